@@ -1,0 +1,142 @@
+/*
+ * wake.h -- C ABI of libwake, a GB300 (sm_103a) implementation of the quasi-static r-xi
+ * plasma-wakefield method of Jain, Palastro, Antonsen, Mori & An, "Plasma wakefield
+ * acceleration studies using the quasi-static code WAKE" (arXiv:1411.3246).
+ *
+ * Conventions (all entry points):
+ *   - Units are normalised: lengths k_p^-1, time omega_p^-1, momenta m c, potentials
+ *     m c^2/e, fields E_0 = m c omega_p/e, densities n_p.  Electrons have charge -1.
+ *   - Array arguments are DEVICE pointers owned by the caller unless stated otherwise;
+ *     the library never frees them.  The library owns only the scratch it allocates in
+ *     wake_init and frees in wake_destroy.
+ *   - Calls are asynchronous on the CUDA stream given to wake_init, except those documented
+ *     as synchronous (wake_diagnostics, wake_status).
+ *   - Every call returns WAKE_OK (0) or a negative WAKE_E* code; wake_last_error() gives a
+ *     thread-local message for the last failure.  A numeric fault inside a kernel is sticky
+ *     in a per-simulation device status word and is reported by wake_status.
+ *   - Grids are node-centred: r_i = i dr (i = 0..nr, dr = rmax/nr) and xi_k = k dxi
+ *     (k = 0..nxi, dxi = ximax/nxi); a grid array is (nxi+1) x (nr+1), slice-major
+ *     (index k*(nr+1) + i).
+ */
+#ifndef WAKE_H
+#define WAKE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WAKE_OK 0
+#define WAKE_EINVAL (-1)   /* bad argument or parameter                              */
+#define WAKE_ENOMEM (-2)   /* device allocation failed                               */
+#define WAKE_ECUDA (-3)    /* CUDA runtime error (launch or copy)                    */
+#define WAKE_ENUMERIC (-4) /* Gamma <= 0 or a non-finite value in the march          */
+#define WAKE_ETIMEOUT (-5) /* a bounded device wait gave up                          */
+#define WAKE_EESCAPE (-6)  /* a plasma ring left [0, rmax]                           */
+#define WAKE_ESTATE (-7)   /* call out of order (e.g. push before any march)         */
+
+#define WAKE_FP64 0  /* FP64 throughout                                              */
+#define WAKE_MIXED 1 /* FP32 particle arithmetic and fields, wider deposit sums      */
+
+/*
+ * Parameters of one simulation (Sec. II, Eq. 12, Table I notation):
+ *   nr, nxi      radial and longitudinal cells of the box [0, rmax] x [0, ximax]
+ *   ppc          plasma rings per radial cell (even when u_th > 0)
+ *   precision    WAKE_FP64 or WAKE_MIXED (all simulations of one handle must agree)
+ *   u_th         thermal momentum of the Maxwellian plasma, per component (0: cold)
+ *   n_d, n_w, sigma_r, sigma_zd, sigma_zw, xi_d, xi_w
+ *                the two-bunch driver density of Eq. 12
+ *   gamma_b, eps_n   beam Lorentz factor and normalised emittance (u_perp spread
+ *                    eps_n/sigma_r)
+ *   ds           beam time step (Eqs. 8-11)
+ *   n_beam       beam macroparticles (0: the driver is Eq. 12 itself, frozen)
+ *   n_drive      the first n_drive beam particles form the drive bunch, the rest the
+ *                witness
+ */
+typedef struct wake_params {
+  int32_t nr, nxi, ppc, precision;
+  double rmax, ximax, u_th;
+  double n_d, n_w, sigma_r, sigma_zd, sigma_zw, xi_d, xi_w;
+  double gamma_b, eps_n, ds;
+  int64_t n_beam, n_drive;
+} wake_params;
+
+typedef struct wake_sim wake_sim; /* opaque handle: n_sims independent simulations */
+
+/*
+ * Create n_sims independent simulations, p[0..n_sims-1] (sizes may differ), bound to the
+ * CUDA stream `stream` (a cudaStream_t; NULL = legacy default stream).  Allocates all
+ * scratch: plasma rings, beam state, the beam-density and field grids.  A simulation with
+ * n_beam == 0 gets the frozen analytic driver of Eq. 12 on its nodes.
+ * Errors: WAKE_EINVAL (sizes out of range: 2 <= nr <= 1024, 2 <= nxi, 1 <= ppc,
+ * nr*ppc <= 16384, precision mismatch), WAKE_ENOMEM, WAKE_ECUDA.
+ */
+int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out);
+
+/*
+ * Initial plasma slice of simulation `sim` (Sec. II.A): rings at their cell positions,
+ * weights with the quasi-static flux factor 1 - v_z0, Gamma_0 = gamma_0 - u_z0 (Eq. 1),
+ * l_z = r u_theta0.  `normals` is a device array of nr*ppc*3 standard normals
+ * (u_r, u_theta, u_z per ring, row-major, mirrored in pairs), scaled by u_th; it may be
+ * NULL only for a cold plasma (u_th == 0).  Must be called before the first march.
+ */
+int wake_load_plasma(wake_sim *s, int sim, const double *normals);
+
+/*
+ * Initial beam of simulation `sim` (Eq. 12 bunches): `normals` is a device array of
+ * 5 x n_beam standard normals (rows x, y, u_x, u_y, xi); x = sigma_r n, u_perp =
+ * (eps_n/sigma_r) n, xi = xi_d + sigma_zd n (drive) or xi_w + sigma_zw n (witness),
+ * u_z = gamma_b.  Particles outside 0 <= xi < ximax or r >= rmax start lost.
+ */
+int wake_load_beam(wake_sim *s, int sim, const double *normals);
+
+/* Beam -> (r, xi) grid density of every simulation with a beam (bilinear hats divided by
+ * the hats' ring volumes).  Needs wake_load_beam. */
+int wake_beam_deposit(wake_sim *s);
+
+/*
+ * The quasi-static xi-march of every simulation with its beam frozen (Sec. II.A, Eqs. 1-7):
+ * per slice, RK2 push of the plasma rings, deposit, and the radial solves for psi, E_z,
+ * B_theta and E_r, written to the handle's field grids.  Needs wake_load_plasma (and a
+ * beam deposit for simulations with a beam).
+ */
+int wake_plasma_march(wake_sim *s);
+
+/* One beam time step of length ds (Eqs. 8-11, Boris) through the fields of the last march,
+ * for every simulation with a beam.  Needs a march. */
+int wake_beam_push(wake_sim *s);
+
+/* nsteps x (wake_beam_deposit, wake_plasma_march, wake_beam_push). */
+int wake_step(wake_sim *s, int nsteps);
+
+/* Copy the last march's fields of `sim` to caller-owned device arrays of (nxi+1)*(nr+1)
+ * doubles each (any pointer may be NULL). */
+int wake_get_fields(wake_sim *s, int sim, double *psi, double *ez, double *er, double *bth);
+
+/* Copy the beam-density grid of `sim` ((nxi+1)*(nr+1) doubles, device). */
+int wake_get_nb(wake_sim *s, int sim, double *nb);
+
+/* Copy the beam state of `sim`: xyz is 6 x n_beam doubles (rows x, y, xi, u_x, u_y, u_z),
+ * lost is n_beam bytes (1 = lost); either may be NULL.  Device pointers. */
+int wake_get_beam(wake_sim *s, int sim, double *xyz, uint8_t *lost);
+
+/* Witness and drive statistics of every simulation (Sec. IV), synchronous.  out_host holds
+ * 5 doubles per simulation: surviving witness count, witness mean gamma, witness rms gamma
+ * spread, surviving drive count, drive mean gamma. */
+int wake_diagnostics(wake_sim *s, double *out_host);
+
+/* Synchronous: WAKE_OK, or the sticky error of simulation `sim` (WAKE_ENUMERIC,
+ * WAKE_EESCAPE, WAKE_ETIMEOUT) raised by a kernel. */
+int wake_status(wake_sim *s, int sim);
+
+/* Thread-local message describing the last failed call (never NULL). */
+const char *wake_last_error(void);
+
+/* Free all scratch of the handle (synchronises its stream). */
+void wake_destroy(wake_sim *s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAKE_H */

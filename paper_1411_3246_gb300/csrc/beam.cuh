@@ -1,0 +1,215 @@
+// Beam-driver and set-up kernels: the Eq. 12 bunches, their (r, xi) deposit, the Boris push
+// of Eqs. 8-11, witness diagnostics, and the initial plasma slice of Sec. II.A.
+//
+// Beam state is SoA: x, y, u_x, u_y in the policy's type BT (float in the mixed form),
+// xi and u_z always in FP64 (u_z ~ gamma_b = 4e4 changes by O(1) per step and xi slips by
+// ~1e-9 per step: both are accumulated in FP64, the kicks themselves computed in BT).
+#pragma once
+
+#include "wake_common.cuh"
+
+namespace wake {
+
+struct BeamDesc {
+  int64_t n, n_drive;
+  int nr, nxi;
+  double rmax, ximax, dr, dxi, ds, gamma_b;
+  double wd, ww;           // macroparticle weights of the drive and witness bunches
+  void *x, *y, *ux, *uy;   // BT
+  double *xi, *uz;
+  uint8_t *lost;
+  void *nb;                // beam-density grid (G)
+  const void *er, *ez, *bth;  // fields of the last march (G)
+  double *diag;            // 5 accumulators
+};
+
+struct BunchInit {
+  double sigma_r, eps_n, xi_d, sigma_zd, xi_w, sigma_zw, gamma_b;
+};
+
+// Eq. 12 bunches from standard normals (rows x, y, u_x, u_y, xi of a 5 x n array).
+template <class BT>
+__global__ void beam_init_kernel(BeamDesc b, BunchInit q, const double *__restrict__ nm) {
+  const double su = q.eps_n / q.sigma_r;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const bool drive = j < b.n_drive;
+    const double x = q.sigma_r * nm[j], y = q.sigma_r * nm[b.n + j];
+    const double xi = drive ? q.xi_d + q.sigma_zd * nm[4 * b.n + j] : q.xi_w + q.sigma_zw * nm[4 * b.n + j];
+    ((BT *)b.x)[j] = (BT)x;
+    ((BT *)b.y)[j] = (BT)y;
+    ((BT *)b.ux)[j] = (BT)(su * nm[2 * b.n + j]);
+    ((BT *)b.uy)[j] = (BT)(su * nm[3 * b.n + j]);
+    b.xi[j] = xi;
+    b.uz[j] = q.gamma_b;
+    const double r = sqrt(x * x + y * y);
+    b.lost[j] = !(xi >= 0.0 && xi < b.ximax && r < b.rmax);
+  }
+}
+
+// Raw bilinear deposit of the beam weights on the (r, xi) nodes (grid zeroed beforehand).
+template <class BT, class G>
+__global__ void beam_deposit_kernel(BeamDesc b) {
+  G *nb = (G *)b.nb;
+  const int n1 = b.nr + 1;
+  const BT inv_dr = (BT)(1.0 / b.dr);
+  const double inv_dxi = 1.0 / b.dxi;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+    if (b.lost[j]) continue;
+    const BT x = ((const BT *)b.x)[j], y = ((const BT *)b.y)[j];
+    const BT r = sqrt(x * x + y * y);
+    int c, k;
+    BT f;
+    locate(r, inv_dr, b.nr, c, f);
+    double g;
+    locate(b.xi[j], inv_dxi, b.nxi, k, g);
+    const BT gg = (BT)g;
+    const BT w = (BT)(j < b.n_drive ? b.wd : b.ww);
+    G *row = nb + (size_t)k * n1 + c;
+    atomicAdd(row, (G)(w * ((BT)1 - f) * ((BT)1 - gg)));
+    atomicAdd(row + 1, (G)(w * f * ((BT)1 - gg)));
+    atomicAdd(row + n1, (G)(w * ((BT)1 - f) * gg));
+    atomicAdd(row + n1 + 1, (G)(w * f * gg));
+  }
+}
+
+// Divide the raw deposit by the hats' volumes: V_i in r, dxi in xi (dxi/2 at both ends).
+template <class G>
+__global__ void nb_normalize_kernel(G *nb, int nr, int nxi, double dr, double dxi) {
+  const int n1 = nr + 1;
+  const int64_t tot = (int64_t)(nxi + 1) * n1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / n1), i = (int)(t % n1);
+    const double vx = (k == 0 || k == nxi) ? 0.5 * dxi : dxi;
+    nb[t] = (G)((double)nb[t] / (node_volume(i, nr, dr) * vx));
+  }
+}
+
+// Eq. 12 on the nodes (frozen analytic driver).
+template <class G>
+__global__ void nb_analytic_kernel(G *nb, int nr, int nxi, double dr, double dxi, double n_d, double n_w,
+                                   double sr, double szd, double szw, double xd, double xw) {
+  const int n1 = nr + 1;
+  const int64_t tot = (int64_t)(nxi + 1) * n1;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(t / n1), i = (int)(t % n1);
+    nb[t] = (G)nb_eq12(i * dr, k * dxi, n_d, n_w, sr, szd, szw, xd, xw);
+  }
+}
+
+// One Boris step (Eqs. 8-11 are the Lorentz force of E = (E_r rhat, E_z), B = B_theta
+// thetahat on a charge -1): fields gathered bilinearly in (r, xi); momentum at half steps;
+// x_perp += dt u_perp/gamma; xi += dt (1 + u_perp^2)/(gamma (gamma + u_z)).  The u_z kick
+// 2 h E_z + (p x s)_z is formed in BT and added to the FP64 u_z.
+template <class BT, class G>
+__global__ void beam_push_kernel(BeamDesc b) {
+  const G *er = (const G *)b.er, *ez = (const G *)b.ez, *bt = (const G *)b.bth;
+  BT *X = (BT *)b.x, *Y = (BT *)b.y, *UX = (BT *)b.ux, *UY = (BT *)b.uy;
+  const int n1 = b.nr + 1;
+  const BT inv_dr = (BT)(1.0 / b.dr), dt = (BT)b.ds, h = (BT)(-0.5 * b.ds), Rw = (BT)b.rmax;
+  const double inv_dxi = 1.0 / b.dxi;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+    if (b.lost[j]) continue;
+    BT x = X[j], y = Y[j], ux = UX[j], uy = UY[j];
+    double xi = b.xi[j], uzd = b.uz[j];
+    const BT r = sqrt(x * x + y * y);
+    int c, k;
+    BT f;
+    double gd;
+    locate(r, inv_dr, b.nr, c, f);
+    locate(xi, inv_dxi, b.nxi, k, gd);
+    const BT g = (BT)gd;
+    const size_t i00 = (size_t)k * n1 + c;
+    const BT w00 = ((BT)1 - f) * ((BT)1 - g), w01 = f * ((BT)1 - g), w10 = ((BT)1 - f) * g, w11 = f * g;
+    const BT Er = w00 * (BT)er[i00] + w01 * (BT)er[i00 + 1] + w10 * (BT)er[i00 + n1] + w11 * (BT)er[i00 + n1 + 1];
+    const BT Ez = w00 * (BT)ez[i00] + w01 * (BT)ez[i00 + 1] + w10 * (BT)ez[i00 + n1] + w11 * (BT)ez[i00 + n1 + 1];
+    const BT Bt = w00 * (BT)bt[i00] + w01 * (BT)bt[i00 + 1] + w10 * (BT)bt[i00 + n1] + w11 * (BT)bt[i00 + n1 + 1];
+    const BT cs = r > (BT)0 ? x / r : (BT)0, sn = r > (BT)0 ? y / r : (BT)0;
+    const BT Ex = Er * cs, Ey = Er * sn, Bx = -Bt * sn, By = Bt * cs;
+    const BT uz = (BT)uzd;
+    const BT mx = ux + h * Ex, my = uy + h * Ey, mz = uz + h * Ez;
+    const BT gm = sqrt((BT)1 + mx * mx + my * my + mz * mz);
+    const BT tx = h * Bx / gm, ty = h * By / gm;
+    const BT px = mx - mz * ty, py = my + mz * tx, pz = mz + (mx * ty - my * tx);
+    const BT s = (BT)2 / ((BT)1 + tx * tx + ty * ty);
+    const BT sx = s * tx, sy = s * ty;
+    ux = mx - pz * sy + h * Ex;
+    uy = my + pz * sx + h * Ey;
+    uzd += (double)((BT)2 * h * Ez + (px * sy - py * sx));
+    const BT uzn = (BT)uzd;
+    const BT up2 = ux * ux + uy * uy;
+    const BT gam = sqrt((BT)1 + up2 + uzn * uzn);
+    x += dt * ux / gam;
+    y += dt * uy / gam;
+    xi += (double)(dt * ((BT)1 + up2) / (gam * (gam + uzn)));
+    X[j] = x;
+    Y[j] = y;
+    UX[j] = ux;
+    UY[j] = uy;
+    b.xi[j] = xi;
+    b.uz[j] = uzd;
+    const BT rn = sqrt(x * x + y * y);
+    if (!(xi >= 0.0 && xi < b.ximax && rn < Rw)) b.lost[j] = 1;
+  }
+}
+
+// Witness / drive sums in FP64: counts, sum(gamma - gamma_b), sum(gamma - gamma_b)^2.
+template <class BT>
+__global__ void beam_diag_kernel(BeamDesc b) {
+  const BT *UX = (const BT *)b.ux, *UY = (const BT *)b.uy;
+  double nw = 0, sw = 0, sw2 = 0, nd = 0, sd = 0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+    if (b.lost[j]) continue;
+    const double ux = UX[j], uy = UY[j], uz = b.uz[j];
+    const double g = sqrt(1.0 + ux * ux + uy * uy + uz * uz) - b.gamma_b;
+    if (j >= b.n_drive) {
+      nw += 1;
+      sw += g;
+      sw2 += g * g;
+    } else {
+      nd += 1;
+      sd += g;
+    }
+  }
+  double v[5] = {nw, sw, sw2, nd, sd};
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    double t = v[q];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(kFull, t, o);
+    if ((threadIdx.x & 31) == 0 && t != 0.0) atomicAdd(&b.diag[q], t);
+  }
+}
+
+// Initial plasma slice (Sec. II.A): cell c, ring m.  Cold: ppc radii (c + (m+1/2)/ppc) dr;
+// warm: ppc/2 radii, each shared by a mirrored pair of draws.  u = u_th * normals,
+// gamma0 = sqrt(1 + u^2), Gamma0 = gamma0 - u_z0, l_z = r u_theta0,
+// w = r dr/ppc * Gamma0/gamma0 (the quasi-static flux factor 1 - v_z0).
+__global__ void plasma_init_kernel(int nr, int ppc, double dr, double u_th, const double *__restrict__ nm,
+                                   double *r0, double *ur0, double *lz, double *G0, double *w) {
+  const int np = nr * ppc;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x) {
+    const int c = j / ppc, m = j % ppc;
+    const bool warm = nm != nullptr;
+    const double r = warm ? ((double)c + ((double)(m / 2) + 0.5) / (double)(ppc / 2)) * dr
+                          : ((double)c + ((double)m + 0.5) / (double)ppc) * dr;
+    double ur = 0.0, ut = 0.0, uz = 0.0;
+    if (warm) {
+      ur = u_th * nm[3 * j];
+      ut = u_th * nm[3 * j + 1];
+      uz = u_th * nm[3 * j + 2];
+    }
+    const double g0 = sqrt(1.0 + ur * ur + ut * ut + uz * uz);
+    r0[j] = r;
+    ur0[j] = ur;
+    lz[j] = r * ut;
+    G0[j] = g0 - uz;
+    w[j] = r * dr / (double)ppc * ((g0 - uz) / g0);
+  }
+}
+
+template <class Src>
+__global__ void widen_kernel(const Src *__restrict__ in, double *__restrict__ out, int64_t n) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = (double)in[t];
+}
+
+}  // namespace wake

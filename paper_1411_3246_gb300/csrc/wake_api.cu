@@ -1,0 +1,468 @@
+// libwake: the C ABI declared in include/wake.h.  Host-side bookkeeping only: scratch
+// allocation per simulation, argument checks, kernel launches on the handle's stream, and
+// the sticky device status words.  All arithmetic of the method runs in the kernels of
+// march.cuh and beam.cuh.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wake.h"
+#include "beam.cuh"
+#include "march.cuh"
+
+using namespace wake;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CUDA_TRY(expr)                                                                       \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess) return fail(WAKE_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+struct Sim {
+  wake_params p{};
+  int np = 0;
+  size_t ng = 0;  // grid nodes (nxi+1)(nr+1)
+  double *r0 = nullptr, *ur0 = nullptr, *lz = nullptr, *G0 = nullptr, *w = nullptr;
+  void *nb = nullptr, *psi = nullptr, *ez = nullptr, *er = nullptr, *bth = nullptr;
+  void *bx = nullptr, *by = nullptr, *bux = nullptr, *buy = nullptr;
+  double *bxi = nullptr, *buz = nullptr;
+  uint8_t *blost = nullptr;
+  int *status = nullptr;
+  bool plasma = false, beam = false, marched = false;
+};
+
+size_t gsize(int precision) { return precision == WAKE_FP64 ? sizeof(double) : sizeof(float); }
+
+int grid_blocks(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
+}
+
+}  // namespace
+
+struct wake_sim {
+  int n = 0, precision = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<Sim> sims;
+  SimDesc *d_desc = nullptr;
+  int *d_order = nullptr;
+  double *d_diag = nullptr;
+  int max_n1 = 0, max_np = 0;
+};
+
+namespace {
+
+void free_sim(Sim &s) {
+  void *ptrs[] = {s.r0, s.ur0, s.lz, s.G0, s.w, s.nb, s.psi, s.ez, s.er, s.bth, s.bx, s.by, s.bux, s.buy,
+                  s.bxi, s.buz, s.blost, s.status};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  s = Sim();
+}
+
+int check_params(const wake_params &p, int prec0) {
+  if (p.precision != WAKE_FP64 && p.precision != WAKE_MIXED) return fail(WAKE_EINVAL, "precision must be WAKE_FP64 or WAKE_MIXED");
+  if (p.precision != prec0) return fail(WAKE_EINVAL, "all simulations of one handle must share the precision");
+  if (p.nr < 2 || p.nr > 1024) return fail(WAKE_EINVAL, "nr must be in [2, 1024]");
+  if (p.nxi < 2 || p.nxi > (1 << 20)) return fail(WAKE_EINVAL, "nxi must be in [2, 2^20]");
+  if (p.ppc < 1 || (int64_t)p.nr * p.ppc > 16384) return fail(WAKE_EINVAL, "need ppc >= 1 and nr*ppc <= 16384");
+  if (p.u_th < 0.0 || (p.u_th > 0.0 && p.ppc % 2)) return fail(WAKE_EINVAL, "a warm plasma needs u_th > 0 and an even ppc");
+  if (!(p.rmax > 0.0) || !(p.ximax > 0.0)) return fail(WAKE_EINVAL, "rmax and ximax must be positive");
+  if (p.n_beam < 0 || p.n_drive < 0 || p.n_drive > p.n_beam) return fail(WAKE_EINVAL, "need 0 <= n_drive <= n_beam");
+  if (!(p.sigma_r > 0.0) || !(p.sigma_zd > 0.0) || (p.n_w != 0.0 && !(p.sigma_zw > 0.0)))
+    return fail(WAKE_EINVAL, "bunch sizes must be positive");
+  if (p.n_beam > 0 && (!(p.gamma_b > 1.0) || !(p.ds > 0.0))) return fail(WAKE_EINVAL, "a beam needs gamma_b > 1 and ds > 0");
+  return WAKE_OK;
+}
+
+template <class T>
+int dalloc(T **p, size_t bytes) {
+  cudaError_t e = cudaMalloc((void **)p, bytes);
+  if (e != cudaSuccess) return fail(WAKE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  return WAKE_OK;
+}
+
+BeamDesc beam_desc(const Sim &s, double *diag) {
+  BeamDesc b{};
+  const wake_params &p = s.p;
+  b.n = p.n_beam;
+  b.n_drive = p.n_drive;
+  b.nr = p.nr;
+  b.nxi = p.nxi;
+  b.rmax = p.rmax;
+  b.ximax = p.ximax;
+  b.dr = p.rmax / p.nr;
+  b.dxi = p.ximax / p.nxi;
+  b.ds = p.ds;
+  b.gamma_b = p.gamma_b;
+  // macroparticle weight = bunch charge (per 2 pi) of Eq. 12, n sqrt(2 pi) sigma_r^2 sigma_z,
+  // over the bunch's macroparticle count
+  const double s2pi = std::sqrt(2.0 * 3.14159265358979323846);
+  const int64_t nw = p.n_beam - p.n_drive;
+  b.wd = p.n_drive > 0 ? p.n_d * s2pi * p.sigma_r * p.sigma_r * p.sigma_zd / (double)p.n_drive : 0.0;
+  b.ww = nw > 0 ? p.n_w * s2pi * p.sigma_r * p.sigma_r * p.sigma_zw / (double)nw : 0.0;
+  b.x = s.bx;
+  b.y = s.by;
+  b.ux = s.bux;
+  b.uy = s.buy;
+  b.xi = s.bxi;
+  b.uz = s.buz;
+  b.lost = s.blost;
+  b.nb = s.nb;
+  b.er = s.er;
+  b.ez = s.ez;
+  b.bth = s.bth;
+  b.diag = diag;
+  return b;
+}
+
+template <class Pol, int PPT>
+int launch_march_ppt(wake_sim *h) {
+  constexpr int NT = Pol::NT;
+  auto kern = march_kernel<Pol, NT, PPT>;
+  const size_t smem = MarchSmem<Pol>::bytes(h->max_n1);
+  CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<h->n, NT, smem, h->stream>>>(h->d_desc, h->d_order);
+  CUDA_TRY(cudaGetLastError());
+  return WAKE_OK;
+}
+
+template <class Pol>
+int launch_march(wake_sim *h) {
+  const int ppt = (h->max_np + Pol::NT - 1) / Pol::NT;
+  if (ppt <= 1) return launch_march_ppt<Pol, 1>(h);
+  if (ppt <= 2) return launch_march_ppt<Pol, 2>(h);
+  if (ppt <= 4) return launch_march_ppt<Pol, 4>(h);
+  if (ppt <= 8) return launch_march_ppt<Pol, 8>(h);
+  if (ppt <= 16) return launch_march_ppt<Pol, 16>(h);
+  if (ppt <= 32) return launch_march_ppt<Pol, 32>(h);
+  return fail(WAKE_EINVAL, "too many plasma rings per simulation");
+}
+
+int check_handle(wake_sim *h, int sim) {
+  if (!h) return fail(WAKE_EINVAL, "null handle");
+  if (sim < 0 || sim >= h->n) return fail(WAKE_EINVAL, "simulation index out of range");
+  return WAKE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *wake_last_error(void) { return g_err.c_str(); }
+
+int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
+  if (!p || !out || n_sims < 1) return fail(WAKE_EINVAL, "wake_init: null pointer or n_sims < 1");
+  *out = nullptr;
+  for (int i = 0; i < n_sims; ++i) {
+    int rc = check_params(p[i], p[0].precision);
+    if (rc) return rc;
+  }
+  wake_sim *h = new wake_sim();
+  h->n = n_sims;
+  h->precision = p[0].precision;
+  h->stream = (cudaStream_t)stream;
+  h->sims.resize(n_sims);
+  const size_t gs = gsize(h->precision);
+  int rc = WAKE_OK;
+  for (int i = 0; i < n_sims && rc == WAKE_OK; ++i) {
+    Sim &s = h->sims[i];
+    s.p = p[i];
+    s.np = p[i].nr * p[i].ppc;
+    s.ng = (size_t)(p[i].nxi + 1) * (p[i].nr + 1);
+    h->max_n1 = std::max(h->max_n1, p[i].nr + 1);
+    h->max_np = std::max(h->max_np, s.np);
+    const size_t pb = sizeof(double) * s.np;
+    if ((rc = dalloc(&s.r0, pb)) || (rc = dalloc(&s.ur0, pb)) || (rc = dalloc(&s.lz, pb)) || (rc = dalloc(&s.G0, pb)) ||
+        (rc = dalloc(&s.w, pb)) || (rc = dalloc(&s.nb, gs * s.ng)) || (rc = dalloc(&s.psi, gs * s.ng)) ||
+        (rc = dalloc(&s.ez, gs * s.ng)) || (rc = dalloc(&s.er, gs * s.ng)) || (rc = dalloc(&s.bth, gs * s.ng)) ||
+        (rc = dalloc(&s.status, sizeof(int))))
+      break;
+    if (cudaMemsetAsync(s.status, 0, sizeof(int), h->stream) != cudaSuccess) {
+      rc = fail(WAKE_ECUDA, "cudaMemsetAsync(status)");
+      break;
+    }
+    if (p[i].n_beam > 0) {
+      const size_t bt = gsize(h->precision) * p[i].n_beam;
+      if ((rc = dalloc(&s.bx, bt)) || (rc = dalloc(&s.by, bt)) || (rc = dalloc(&s.bux, bt)) || (rc = dalloc(&s.buy, bt)) ||
+          (rc = dalloc(&s.bxi, sizeof(double) * p[i].n_beam)) || (rc = dalloc(&s.buz, sizeof(double) * p[i].n_beam)) ||
+          (rc = dalloc(&s.blost, p[i].n_beam)))
+        break;
+    } else {
+      // frozen analytic driver (Eq. 12) on the nodes
+      const double dr = p[i].rmax / p[i].nr, dxi = p[i].ximax / p[i].nxi;
+      const int nb = grid_blocks((int64_t)s.ng, 256);
+      if (h->precision == WAKE_FP64)
+        nb_analytic_kernel<double><<<nb, 256, 0, h->stream>>>((double *)s.nb, p[i].nr, p[i].nxi, dr, dxi, p[i].n_d,
+                                                              p[i].n_w, p[i].sigma_r, p[i].sigma_zd, p[i].sigma_zw,
+                                                              p[i].xi_d, p[i].xi_w);
+      else
+        nb_analytic_kernel<float><<<nb, 256, 0, h->stream>>>((float *)s.nb, p[i].nr, p[i].nxi, dr, dxi, p[i].n_d,
+                                                             p[i].n_w, p[i].sigma_r, p[i].sigma_zd, p[i].sigma_zw,
+                                                             p[i].xi_d, p[i].xi_w);
+      if (cudaGetLastError() != cudaSuccess) {
+        rc = fail(WAKE_ECUDA, "nb_analytic_kernel launch");
+        break;
+      }
+    }
+  }
+  if (rc == WAKE_OK) {
+    // descriptors; CTAs take the simulations largest-work first (LPT order)
+    std::vector<SimDesc> desc(n_sims);
+    std::vector<int> order(n_sims);
+    for (int i = 0; i < n_sims; ++i) {
+      const Sim &s = h->sims[i];
+      SimDesc &d = desc[i];
+      d.nr = s.p.nr;
+      d.nxi = s.p.nxi;
+      d.np = s.np;
+      d.has_beam = s.p.n_beam > 0;
+      d.rmax = s.p.rmax;
+      d.ximax = s.p.ximax;
+      d.dr = s.p.rmax / s.p.nr;
+      d.dxi = s.p.ximax / s.p.nxi;
+      d.r0 = s.r0;
+      d.ur0 = s.ur0;
+      d.lz = s.lz;
+      d.G0 = s.G0;
+      d.w = s.w;
+      d.nb = s.nb;
+      d.psi = s.psi;
+      d.ez = s.ez;
+      d.er = s.er;
+      d.bth = s.bth;
+      d.status = s.status;
+      order[i] = i;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return (double)desc[a].np * desc[a].nxi > (double)desc[b].np * desc[b].nxi;
+    });
+    if ((rc = dalloc(&h->d_desc, sizeof(SimDesc) * n_sims)) == WAKE_OK &&
+        (rc = dalloc(&h->d_order, sizeof(int) * n_sims)) == WAKE_OK &&
+        (rc = dalloc(&h->d_diag, sizeof(double) * 5 * n_sims)) == WAKE_OK) {
+      if (cudaMemcpyAsync(h->d_desc, desc.data(), sizeof(SimDesc) * n_sims, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+          cudaMemcpyAsync(h->d_order, order.data(), sizeof(int) * n_sims, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+          cudaStreamSynchronize(h->stream) != cudaSuccess)
+        rc = fail(WAKE_ECUDA, "wake_init: descriptor upload");
+    }
+  }
+  if (rc != WAKE_OK) {
+    wake_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return WAKE_OK;
+}
+
+int wake_load_plasma(wake_sim *h, int sim, const double *normals) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  Sim &s = h->sims[sim];
+  if (s.p.u_th > 0.0 && !normals) return fail(WAKE_EINVAL, "a warm plasma needs the momentum normals");
+  const double dr = s.p.rmax / s.p.nr;
+  plasma_init_kernel<<<grid_blocks(s.np, 256), 256, 0, h->stream>>>(s.p.nr, s.p.ppc, dr, s.p.u_th,
+                                                                     s.p.u_th > 0.0 ? normals : nullptr, s.r0, s.ur0,
+                                                                     s.lz, s.G0, s.w);
+  CUDA_TRY(cudaGetLastError());
+  s.plasma = true;
+  return WAKE_OK;
+}
+
+int wake_load_beam(wake_sim *h, int sim, const double *normals) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  Sim &s = h->sims[sim];
+  if (s.p.n_beam == 0) return fail(WAKE_EINVAL, "simulation has no beam (n_beam == 0)");
+  if (!normals) return fail(WAKE_EINVAL, "null beam normals");
+  BeamDesc b = beam_desc(s, nullptr);
+  BunchInit q{s.p.sigma_r, s.p.eps_n, s.p.xi_d, s.p.sigma_zd, s.p.xi_w, s.p.sigma_zw, s.p.gamma_b};
+  const int nb = grid_blocks(s.p.n_beam, 256);
+  if (h->precision == WAKE_FP64)
+    beam_init_kernel<double><<<nb, 256, 0, h->stream>>>(b, q, normals);
+  else
+    beam_init_kernel<float><<<nb, 256, 0, h->stream>>>(b, q, normals);
+  CUDA_TRY(cudaGetLastError());
+  s.beam = true;
+  return WAKE_OK;
+}
+
+int wake_beam_deposit(wake_sim *h) {
+  if (!h) return fail(WAKE_EINVAL, "null handle");
+  for (int i = 0; i < h->n; ++i) {
+    Sim &s = h->sims[i];
+    if (s.p.n_beam == 0) continue;
+    if (!s.beam) return fail(WAKE_ESTATE, "wake_beam_deposit before wake_load_beam");
+    BeamDesc b = beam_desc(s, nullptr);
+    CUDA_TRY(cudaMemsetAsync(s.nb, 0, gsize(h->precision) * s.ng, h->stream));
+    const int nb = grid_blocks(s.p.n_beam, 256), ng = grid_blocks((int64_t)s.ng, 256);
+    if (h->precision == WAKE_FP64) {
+      beam_deposit_kernel<double, double><<<nb, 256, 0, h->stream>>>(b);
+      nb_normalize_kernel<double><<<ng, 256, 0, h->stream>>>((double *)s.nb, s.p.nr, s.p.nxi, b.dr, b.dxi);
+    } else {
+      beam_deposit_kernel<float, float><<<nb, 256, 0, h->stream>>>(b);
+      nb_normalize_kernel<float><<<ng, 256, 0, h->stream>>>((float *)s.nb, s.p.nr, s.p.nxi, b.dr, b.dxi);
+    }
+    CUDA_TRY(cudaGetLastError());
+  }
+  return WAKE_OK;
+}
+
+int wake_plasma_march(wake_sim *h) {
+  if (!h) return fail(WAKE_EINVAL, "null handle");
+  for (auto &s : h->sims)
+    if (!s.plasma) return fail(WAKE_ESTATE, "wake_plasma_march before wake_load_plasma");
+  int rc = h->precision == WAKE_FP64 ? launch_march<PolFP64>(h) : launch_march<PolMixed>(h);
+  if (rc) return rc;
+  for (auto &s : h->sims) s.marched = true;
+  return WAKE_OK;
+}
+
+int wake_beam_push(wake_sim *h) {
+  if (!h) return fail(WAKE_EINVAL, "null handle");
+  for (int i = 0; i < h->n; ++i) {
+    Sim &s = h->sims[i];
+    if (s.p.n_beam == 0) continue;
+    if (!s.beam || !s.marched) return fail(WAKE_ESTATE, "wake_beam_push needs a loaded beam and a march");
+    BeamDesc b = beam_desc(s, nullptr);
+    const int nb = grid_blocks(s.p.n_beam, 256);
+    if (h->precision == WAKE_FP64)
+      beam_push_kernel<double, double><<<nb, 256, 0, h->stream>>>(b);
+    else
+      beam_push_kernel<float, float><<<nb, 256, 0, h->stream>>>(b);
+    CUDA_TRY(cudaGetLastError());
+  }
+  return WAKE_OK;
+}
+
+int wake_step(wake_sim *h, int nsteps) {
+  if (!h || nsteps < 0) return fail(WAKE_EINVAL, "wake_step: null handle or nsteps < 0");
+  for (int t = 0; t < nsteps; ++t) {
+    int rc;
+    if ((rc = wake_beam_deposit(h)) || (rc = wake_plasma_march(h)) || (rc = wake_beam_push(h))) return rc;
+  }
+  return WAKE_OK;
+}
+
+int wake_get_fields(wake_sim *h, int sim, double *psi, double *ez, double *er, double *bth) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  Sim &s = h->sims[sim];
+  if (!s.marched) return fail(WAKE_ESTATE, "wake_get_fields before a march");
+  void *src[4] = {s.psi, s.ez, s.er, s.bth};
+  double *dst[4] = {psi, ez, er, bth};
+  for (int q = 0; q < 4; ++q) {
+    if (!dst[q]) continue;
+    if (h->precision == WAKE_FP64) {
+      CUDA_TRY(cudaMemcpyAsync(dst[q], src[q], sizeof(double) * s.ng, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      widen_kernel<float><<<grid_blocks((int64_t)s.ng, 256), 256, 0, h->stream>>>((const float *)src[q], dst[q], (int64_t)s.ng);
+      CUDA_TRY(cudaGetLastError());
+    }
+  }
+  return WAKE_OK;
+}
+
+int wake_get_nb(wake_sim *h, int sim, double *nb) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  Sim &s = h->sims[sim];
+  if (!nb) return fail(WAKE_EINVAL, "null output");
+  if (h->precision == WAKE_FP64) {
+    CUDA_TRY(cudaMemcpyAsync(nb, s.nb, sizeof(double) * s.ng, cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    widen_kernel<float><<<grid_blocks((int64_t)s.ng, 256), 256, 0, h->stream>>>((const float *)s.nb, nb, (int64_t)s.ng);
+    CUDA_TRY(cudaGetLastError());
+  }
+  return WAKE_OK;
+}
+
+int wake_get_beam(wake_sim *h, int sim, double *xyz, uint8_t *lost) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  Sim &s = h->sims[sim];
+  if (!s.beam) return fail(WAKE_ESTATE, "wake_get_beam before wake_load_beam");
+  const int64_t n = s.p.n_beam;
+  if (xyz) {
+    void *src[4] = {s.bx, s.by, s.bux, s.buy};
+    const int row[4] = {0, 1, 3, 4};
+    for (int q = 0; q < 4; ++q) {
+      if (h->precision == WAKE_FP64) {
+        CUDA_TRY(cudaMemcpyAsync(xyz + row[q] * n, src[q], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+      } else {
+        widen_kernel<float><<<grid_blocks(n, 256), 256, 0, h->stream>>>((const float *)src[q], xyz + row[q] * n, n);
+        CUDA_TRY(cudaGetLastError());
+      }
+    }
+    CUDA_TRY(cudaMemcpyAsync(xyz + 2 * n, s.bxi, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(xyz + 5 * n, s.buz, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  if (lost) CUDA_TRY(cudaMemcpyAsync(lost, s.blost, n, cudaMemcpyDeviceToDevice, h->stream));
+  return WAKE_OK;
+}
+
+int wake_diagnostics(wake_sim *h, double *out_host) {
+  if (!h || !out_host) return fail(WAKE_EINVAL, "wake_diagnostics: null argument");
+  CUDA_TRY(cudaMemsetAsync(h->d_diag, 0, sizeof(double) * 5 * h->n, h->stream));
+  for (int i = 0; i < h->n; ++i) {
+    Sim &s = h->sims[i];
+    if (s.p.n_beam == 0 || !s.beam) continue;
+    BeamDesc b = beam_desc(s, h->d_diag + 5 * i);
+    const int nb = grid_blocks(s.p.n_beam, 256);
+    if (h->precision == WAKE_FP64)
+      beam_diag_kernel<double><<<nb, 256, 0, h->stream>>>(b);
+    else
+      beam_diag_kernel<float><<<nb, 256, 0, h->stream>>>(b);
+    CUDA_TRY(cudaGetLastError());
+  }
+  std::vector<double> acc(5 * h->n);
+  CUDA_TRY(cudaMemcpyAsync(acc.data(), h->d_diag, sizeof(double) * 5 * h->n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < h->n; ++i) {
+    const double *a = &acc[5 * i];
+    const double gb = h->sims[i].p.gamma_b;
+    double *o = out_host + 5 * i;
+    o[0] = a[0];
+    o[1] = a[0] > 0 ? gb + a[1] / a[0] : 0.0;
+    o[2] = a[0] > 0 ? std::sqrt(std::max(a[2] / a[0] - (a[1] / a[0]) * (a[1] / a[0]), 0.0)) : 0.0;
+    o[3] = a[3];
+    o[4] = a[3] > 0 ? gb + a[4] / a[3] : 0.0;
+  }
+  return WAKE_OK;
+}
+
+int wake_status(wake_sim *h, int sim) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  int st = 0;
+  CUDA_TRY(cudaMemcpyAsync(&st, h->sims[sim].status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (st & ST_NUMERIC) return fail(WAKE_ENUMERIC, "Gamma <= 0 or a non-finite field in the march");
+  if (st & ST_ESCAPE) return fail(WAKE_EESCAPE, "a plasma ring left [0, rmax]");
+  if (st & ST_TIMEOUT) return fail(WAKE_ETIMEOUT, "a bounded device wait gave up");
+  return WAKE_OK;
+}
+
+void wake_destroy(wake_sim *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (auto &s : h->sims) free_sim(s);
+  if (h->d_desc) cudaFree(h->d_desc);
+  if (h->d_order) cudaFree(h->d_order);
+  if (h->d_diag) cudaFree(h->d_diag);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,202 @@
+"""Thin ctypes binding of libwake (include/wake.h); same names as the C ABI.
+
+Arguments are marshalled only: device arrays are torch CUDA tensors (their data_ptr() is
+passed), every step of the method runs in the library's kernels.  A failing call raises
+WakeError with the library's message.  There is no fallback: if libwake.so is missing this
+module raises on first use.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libwake.so")
+
+WAKE_OK, WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENUMERIC, WAKE_ETIMEOUT, WAKE_EESCAPE, WAKE_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+WAKE_FP64, WAKE_MIXED = 0, 1
+
+# every entry point the header declares
+EXPORTS = ["wake_init", "wake_load_plasma", "wake_load_beam", "wake_beam_deposit", "wake_plasma_march",
+           "wake_beam_push", "wake_step", "wake_get_fields", "wake_get_nb", "wake_get_beam",
+           "wake_diagnostics", "wake_status", "wake_last_error", "wake_destroy"]
+
+
+class wake_params(C.Structure):
+    _fields_ = [("nr", C.c_int32), ("nxi", C.c_int32), ("ppc", C.c_int32), ("precision", C.c_int32),
+                ("rmax", C.c_double), ("ximax", C.c_double), ("u_th", C.c_double),
+                ("n_d", C.c_double), ("n_w", C.c_double), ("sigma_r", C.c_double),
+                ("sigma_zd", C.c_double), ("sigma_zw", C.c_double), ("xi_d", C.c_double),
+                ("xi_w", C.c_double), ("gamma_b", C.c_double), ("eps_n", C.c_double),
+                ("ds", C.c_double), ("n_beam", C.c_int64), ("n_drive", C.c_int64)]
+
+
+class WakeError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libwake error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libwake.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1411_3246_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, pd = C.c_void_p, C.c_int, C.POINTER(C.c_double)
+        L.wake_init.argtypes = [C.POINTER(wake_params), i32, vp, C.POINTER(vp)]
+        L.wake_load_plasma.argtypes = [vp, i32, vp]
+        L.wake_load_beam.argtypes = [vp, i32, vp]
+        for n in ("wake_beam_deposit", "wake_plasma_march", "wake_beam_push"):
+            getattr(L, n).argtypes = [vp]
+        L.wake_step.argtypes = [vp, i32]
+        L.wake_get_fields.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.wake_get_nb.argtypes = [vp, i32, vp]
+        L.wake_get_beam.argtypes = [vp, i32, vp, vp]
+        L.wake_diagnostics.argtypes = [vp, pd]
+        L.wake_status.argtypes = [vp, i32]
+        L.wake_last_error.restype = C.c_char_p
+        L.wake_last_error.argtypes = []
+        L.wake_destroy.argtypes = [vp]
+        L.wake_destroy.restype = None
+        for n in EXPORTS:
+            if n not in ("wake_last_error", "wake_destroy"):
+                getattr(L, n).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != WAKE_OK:
+        raise WakeError(rc, lib().wake_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device arrays must be contiguous CUDA tensors"
+    return C.c_void_p(t.data_ptr())
+
+
+def params_of(cfg, precision: int) -> wake_params:
+    """wake_params from a parameter object with the WakeConfig attribute names."""
+    return wake_params(cfg.nr, cfg.nxi, cfg.ppc, precision, cfg.rmax, cfg.ximax, cfg.u_th, cfg.n_d,
+                       cfg.n_w, cfg.sigma_r, cfg.sigma_zd, cfg.sigma_zw, cfg.xi_d, cfg.xi_w,
+                       cfg.gamma_b, cfg.eps_n, cfg.ds, cfg.n_beam, cfg.n_drive)
+
+
+def wake_init(params, stream=None):
+    """params: list of wake_params.  stream: a torch.cuda.Stream (None: torch's current)."""
+    import torch
+    arr = (wake_params * len(params))(*params)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    h = C.c_void_p()
+    _check(lib().wake_init(arr, len(params), C.c_void_p(stream.cuda_stream), C.byref(h)))
+    return h
+
+
+def wake_load_plasma(h, sim, normals=None):
+    _check(lib().wake_load_plasma(h, sim, _ptr(normals)))
+
+
+def wake_load_beam(h, sim, normals):
+    _check(lib().wake_load_beam(h, sim, _ptr(normals)))
+
+
+def wake_beam_deposit(h):
+    _check(lib().wake_beam_deposit(h))
+
+
+def wake_plasma_march(h):
+    _check(lib().wake_plasma_march(h))
+
+
+def wake_beam_push(h):
+    _check(lib().wake_beam_push(h))
+
+
+def wake_step(h, nsteps):
+    _check(lib().wake_step(h, nsteps))
+
+
+def wake_get_fields(h, sim, psi=None, ez=None, er=None, bth=None):
+    _check(lib().wake_get_fields(h, sim, _ptr(psi), _ptr(ez), _ptr(er), _ptr(bth)))
+
+
+def wake_get_nb(h, sim, nb):
+    _check(lib().wake_get_nb(h, sim, _ptr(nb)))
+
+
+def wake_get_beam(h, sim, xyz=None, lost=None):
+    _check(lib().wake_get_beam(h, sim, _ptr(xyz), _ptr(lost)))
+
+
+def wake_diagnostics(h, n_sims):
+    out = (C.c_double * (5 * n_sims))()
+    _check(lib().wake_diagnostics(h, out))
+    return [list(out[5 * i:5 * i + 5]) for i in range(n_sims)]
+
+
+def wake_status(h, sim):
+    return lib().wake_status(h, sim)
+
+
+def wake_last_error():
+    return lib().wake_last_error().decode()
+
+
+def wake_destroy(h):
+    lib().wake_destroy(h)
+
+
+class Simulations:
+    """Convenience owner of a handle: n independent simulations on one stream."""
+
+    def __init__(self, cfgs, precision=WAKE_MIXED, stream=None):
+        import torch
+        self.cfgs = list(cfgs)
+        self.torch = torch
+        self.h = wake_init([params_of(c, precision) for c in self.cfgs], stream)
+
+    def grid(self, sim):
+        c = self.cfgs[sim]
+        return self.torch.empty((c.nxi + 1, c.nr + 1), dtype=self.torch.float64, device="cuda")
+
+    def fields(self, sim):
+        out = {k: self.grid(sim) for k in ("psi", "ez", "er", "bth")}
+        wake_get_fields(self.h, sim, out["psi"], out["ez"], out["er"], out["bth"])
+        return out
+
+    def nb(self, sim):
+        out = self.grid(sim)
+        wake_get_nb(self.h, sim, out)
+        return out
+
+    def beam(self, sim):
+        c = self.cfgs[sim]
+        xyz = self.torch.empty((6, c.n_beam), dtype=self.torch.float64, device="cuda")
+        lost = self.torch.empty(c.n_beam, dtype=self.torch.uint8, device="cuda")
+        wake_get_beam(self.h, sim, xyz, lost)
+        return xyz, lost
+
+    def diagnostics(self):
+        return wake_diagnostics(self.h, len(self.cfgs))
+
+    def status(self, sim):
+        return wake_status(self.h, sim)
+
+    def close(self):
+        if self.h is not None:
+            wake_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

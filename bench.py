@@ -198,6 +198,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--march-only", type=int, default=0,
+                    help="run this many mixed marches of the workload and exit (profiling)")
+    ap.add_argument("--nr", type=int, default=0, help="override Nr (profiling a smaller case)")
+    ap.add_argument("--nxi", type=int, default=0, help="override Nxi (profiling a smaller case)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -208,12 +212,30 @@ def main():
     from paper_1411_3246_gb300 import wake
     torch.cuda.set_device(local)
     cfg = workload()
+    if args.nr:
+        cfg.nr = args.nr
+    if args.nxi:
+        cfg.nxi = args.nxi
     cfg.seed += 1000 * rank  # independent replicas
     nm_p = torch.from_numpy(synth.plasma_normals(cfg)).pin_memory()
     nm_b = torch.from_numpy(synth.beam_normals(cfg)).pin_memory()
     stream = torch.cuda.Stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
     pushes = plasma_pushes_per_step(cfg)
+
+    if args.march_only:
+        sim = wake.Simulations([cfg], wake.WAKE_MIXED, stream)
+        with torch.cuda.stream(stream):
+            wake.wake_load_plasma(sim.h, 0, nm_p.cuda(non_blocking=True))
+            wake.wake_load_beam(sim.h, 0, nm_b.cuda(non_blocking=True))
+            wake.wake_beam_deposit(sim.h)
+            for _ in range(args.march_only):
+                wake.wake_plasma_march(sim.h)
+        stream.synchronize()
+        st = sim.status(0)
+        sim.close()
+        print(json.dumps({"march_only": args.march_only, "nr": cfg.nr, "nxi": cfg.nxi, "status": st}))
+        return
 
     def timed_steps(prec, k, w, march_events=True):
         sim = wake.Simulations([cfg], prec, stream)

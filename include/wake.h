@@ -70,7 +70,7 @@ typedef struct wake_sim wake_sim; /* opaque handle: n_sims independent simulatio
  * scratch: plasma rings, beam state, the beam-density and field grids.  A simulation with
  * n_beam == 0 gets the frozen analytic driver of Eq. 12 on its nodes.
  * Errors: WAKE_EINVAL (sizes out of range: 2 <= nr <= 1024, 2 <= nxi, 1 <= ppc,
- * nr*ppc <= 16384, precision mismatch), WAKE_ENOMEM, WAKE_ECUDA.
+ * nr*ppc <= 8192, precision mismatch), WAKE_ENOMEM, WAKE_ECUDA.
  */
 int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out);
 

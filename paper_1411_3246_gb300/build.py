@@ -10,6 +10,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwake.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# the mixed-precision march uses approximate FP32 divide and square root (a few ulp) and
+# flushes denormals; every other translation unit keeps IEEE division and sqrt
+EXTRA = {"march_mixed.cu": ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]}
 
 
 def sources():
@@ -36,7 +39,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [nvcc, *flags, "-c", src, "-o", obj]
+        cmd = [nvcc, *flags, *EXTRA.get(os.path.basename(src), []), "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd))
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

@@ -1,70 +1,184 @@
 // The quasi-static xi-march (Sec. II.A, Eqs. 1-7): one CTA marches one simulation through
-// all of its slices, persistent over xi.  The plasma rings live in registers, the node
-// arrays of the current slice in shared memory; nothing but the beam density row (in) and
-// the field rows (out) touches global memory inside the loop.
+// all of its slices, persistent over xi.
 //
-// Per slice, RK2 (midpoint) in xi; each stage solves the fields for the rings' current
-// positions:
-//   1. deposit the ring charge (linear hats);
-//   2. psi from Gauss's law for the hat density (enclosed charge Phi_m at node m,
-//      r_m psi'_m = Phi_m), psi(R) = 0, inward trapezoid sum  -- two block scans;
-//   3. per ring: Gamma = Gamma_0 + psi (Eq. 1), gamma and u_z (Eqs. 2-3), a = u_r/Gamma,
-//      F0 = (gamma/Gamma) psi' + u_theta^2/(Gamma r) (Eq. 4 without -B); deposit
-//      J_z, chi = n/gamma, T = D[w a^2], P = D[w (a^2 psi' - F0)/Gamma], U = D[w a/Gamma]
-//      on the nodes and the radial current K_c of each cell;
-//   4. E_z = d_xi psi (Eq. 7) by an inward scan of the cell currents; Q = P + E_z U; B_theta
-//      from Eq. 6 differentiated in r (Helmholtz form, shift chi) by parallel cyclic
-//      reduction; E_r = B_theta - psi';
-//   5. per ring: the Cartesian radial force (gamma/Gamma) psi' - B_theta (Eqs. 4-5 with the
-//      centrifugal term carried by the local frame).
+// Per slice, RK2 (midpoint) in xi; each stage solves the fields for the rings' positions in
+// four phases separated by block barriers:
+//   P0 (warp 0)    psi from Gauss's law for the hat charge density (enclosed charge Phi_m at
+//                  node m, r_m psi'_m = Phi_m), psi(R) = 0, inward trapezoid sum;
+//   P1 (all warps) per ring: Gamma = Gamma_0 + psi (Eq. 1), gamma and u_z (Eqs. 2-3),
+//                  a = u_r/Gamma, F0 = (gamma/Gamma) psi' + u_theta^2/(Gamma r) (Eq. 4 without
+//                  -B); deposit J_z, chi = n/gamma, T = D[w a^2], P = D[w (a^2 psi' - F0)/Gamma],
+//                  U = D[w a/Gamma] on the nodes and the radial current K_c of each cell;
+//   P2 (warp 0)    node densities; E_z = d_xi psi (Eq. 7) by an inward sum of the cell
+//                  currents; Q = P + E_z U; B_theta from Eq. 6 differentiated in r (Helmholtz
+//                  form, shift chi), a tridiagonal system solved by a warp partition method;
+//   P3 (all warps) per ring: the Cartesian radial force (gamma/Gamma) psi' - B_theta (Eqs. 4-5
+//                  with the centrifugal term carried by the local frame), the move to the next
+//                  stage's position, and that position's charge deposit (linear hats).
 // Stage 1 at xi_k writes the slice's fields; stage 2 at xi_k + dxi/2 uses n_b averaged over
 // slices k and k+1.
+//
+// Layout.  Ring state lives in slot arrays (structure of arrays, slot p*NT + t for the p-th
+// ring of thread t): shared memory in the mixed form, global memory in the FP64 form.  A
+// thread's rings are consecutive in radius (the mixed form re-sorts them by cell every few
+// slices), so its deposits are summed over a window of cells in registers, combined across
+// the lanes of a warp that share a window, and flushed with one shared-memory atomic per node
+// and array.  Node work runs warp-synchronously in warp 0 on lane chunks: the scans in a
+// wide type (FP64, or float-float pairs on the FP32 pipe), the tridiagonal solve by chunk
+// elimination plus a 32-unknown interface system solved by cyclic reduction across lanes.
 #pragma once
 
 #include "wake_common.cuh"
 
 namespace wake {
 
-// Precision policies.  R: ring and node arithmetic (gathers, per-node sources, fields);
-// Acc: shared-memory deposit sums; S: tridiagonal (PCR) arithmetic; G: grid element type in
-// global memory.  The enclosed-charge and inward field sums are always scanned in FP64.
+// ---------------------------------------------------------------------------------------
+// wide accumulation type: FP64, or a float-float pair (Dekker / Knuth two-sum), which keeps
+// ~48 significant bits on the FP32 pipe
+// ---------------------------------------------------------------------------------------
+struct FF {
+  float h, l;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.h + b.h;
+  const float bb = s - a.h;
+  float e = (a.h - (s - bb)) + (b.h - bb);
+  e += a.l + b.l;
+  const float h = s + e;
+  return FF{h, e - (h - s)};
+}
+__device__ __forceinline__ double wide_add(double a, double b) { return a + b; }
+__device__ __forceinline__ FF wide_add(FF a, FF b) { return ff_add(a, b); }
+__device__ __forceinline__ double wide_shfl_up(double a, int o) { return __shfl_up_sync(kFull, a, o); }
+__device__ __forceinline__ FF wide_shfl_up(FF a, int o) {
+  return FF{__shfl_up_sync(kFull, a.h, o), __shfl_up_sync(kFull, a.l, o)};
+}
+__device__ __forceinline__ double wide_shfl_down(double a, int o) { return __shfl_down_sync(kFull, a, o); }
+__device__ __forceinline__ FF wide_shfl_down(FF a, int o) {
+  return FF{__shfl_down_sync(kFull, a.h, o), __shfl_down_sync(kFull, a.l, o)};
+}
+template <class W>
+__device__ __forceinline__ W wide_zero();
+template <>
+__device__ __forceinline__ double wide_zero<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ FF wide_zero<FF>() { return FF{0.f, 0.f}; }
+__device__ __forceinline__ float wide_value(FF x) { return x.h + x.l; }
+__device__ __forceinline__ double wide_value(double x) { return x; }
+template <class W, class R>
+__device__ __forceinline__ W wide_of(R x);
+template <>
+__device__ __forceinline__ double wide_of<double, double>(double x) { return x; }
+template <>
+__device__ __forceinline__ FF wide_of<FF, float>(float x) { return FF{x, 0.f}; }
+
+// exclusive prefix over the lanes of one warp of per-lane totals (lane 0 gets 0)
+template <class W>
+__device__ __forceinline__ W warp_excl_prefix(W v, int lane) {
+  W incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const W t = wide_shfl_up(incl, o);
+    if (lane >= o) incl = wide_add(incl, t);
+  }
+  const W ex = wide_shfl_up(incl, 1);
+  return lane == 0 ? wide_zero<W>() : ex;
+}
+// exclusive suffix over the lanes of one warp (lane 31 gets 0)
+template <class W>
+__device__ __forceinline__ W warp_excl_suffix(W v, int lane) {
+  W incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const W t = wide_shfl_down(incl, o);
+    if (lane + o < 32) incl = wide_add(incl, t);
+  }
+  const W ex = wide_shfl_down(incl, 1);
+  return lane == 31 ? wide_zero<W>() : ex;
+}
+
+// ---------------------------------------------------------------------------------------
+// precision policies.  R: ring and node arithmetic; Acc: current-type deposit sums; Q: charge
+// deposit sums (psi comes from the small difference rho - rho0 of two large sums, so the mixed
+// form sums exact float-float products as 64-bit integers, which makes rho - rho0 exact);
+// G: grid element type in global memory; W: scan type.  Mixed: rings in shared memory, re-sorted by cell every
+// kSortEvery slices, node coefficients computed on the fly.  FP64: rings in global memory in
+// their initial order, node coefficients from tables (FP64 division is slow on this chip).
+// ---------------------------------------------------------------------------------------
 struct PolFP64 {
   using R = double;
   using Acc = double;
-  using S = double;
+  using Q = double;  // charge deposit sums
   using G = double;
+  using W = double;
   static constexpr int NT = 512;
+  static constexpr int kSortEvery = 0;
+  static constexpr bool kSmemRings = false;
+  static constexpr bool kTables = true;
 };
 struct PolMixed {
   using R = float;
   using Acc = float;
-  using S = float;
+  using Q = long long;  // charge deposit sums: 64-bit fixed point, 2^-44 resolution
   using G = float;
-  static constexpr int NT = 1024;
+  using W = FF;
+  static constexpr int NT = 512;
+  static constexpr int kSortEvery = 2;
+  static constexpr bool kSmemRings = true;
+  static constexpr bool kTables = false;
+};
+
+// Ring slot arrays: cell index, offset in the cell, u_r, the constants l_z, Gamma_0, w, and
+// the stage-1 Gamma and radial force kept for the full step.
+template <class R>
+struct RingSoA {
+  int *c;
+  R *f, *ur, *lz, *G0, *w, *G1, *F1;
+  __host__ __device__ static size_t bytes(int slots) {
+    return sizeof(int) * (size_t)slots + 32 + 7 * sizeof(R) * (size_t)slots;
+  }
+  __device__ __forceinline__ void carve(void *base, int slots) {
+    c = (int *)base;
+    R *p = (R *)(((uintptr_t)(c + slots) + 31) & ~(uintptr_t)31);
+    f = p; p += slots;
+    ur = p; p += slots;
+    lz = p; p += slots;
+    G0 = p; p += slots;
+    w = p; p += slots;
+    G1 = p; p += slots;
+    F1 = p; p += slots;
+  }
 };
 
 template <class Pol>
 struct MarchSmem {
   using R = typename Pol::R;
   using Acc = typename Pol::Acc;
-  using S = typename Pol::S;
-  double *work, *wtot;                       // scan buffer
-  Acc *rho0, *rho, *jz, *chi, *T, *P, *U, *K;  // deposits
-  R *psi, *dpsi, *ez, *bth;                  // node fields
-  R *invR, *invV, *alpha, *ga, *gb, *gc;     // per-simulation tables
-  S *ta[2], *tb[2], *tc[2], *td[2];          // PCR buffers
+  typename Pol::Q *rho0, *rho;                  // charge deposits
+  Acc *jz, *chi, *T, *P, *U, *K;                // current-type deposits
+  R *psi, *dpsi, *ez, *bth;                     // node fields
+  R *nb0, *nb1;                                 // beam-density rows (double buffer)
+  R *ta, *tb, *tc, *td, *tu, *tv;               // tridiagonal scratch (row l*M + k at k*32 + l)
+  R *invR, *invV, *alpha, *ga, *gb, *gc;        // tables (FP64 form; the mixed form keeps
+                                                // invR = 1/(m dr) and ga = 1/(j + 1/2) only)
+  int *cnt;                                     // re-sort counts
+  typename Pol::W *wtot;                        // block-scan warp totals
+  RingSoA<R> rings;                             // ring slots (mixed form)
 
-  static size_t bytes(int n1) {
-    return sizeof(double) * ((size_t)n1 + 64) + sizeof(Acc) * 8 * (size_t)n1 + sizeof(R) * 10 * (size_t)n1 +
-           sizeof(S) * 8 * (size_t)n1 + 256;
+  static size_t bytes(int n1, int slots) {
+    size_t b = sizeof(typename Pol::W) * 64 + sizeof(typename Pol::Q) * 2 * (size_t)n1 + sizeof(Acc) * 6 * (size_t)n1 + sizeof(R) * 6 * (size_t)n1 + sizeof(R) * 6 * ((size_t)n1 + 32) + 256;
+    b += sizeof(R) * (Pol::kTables ? 6 : 2) * (size_t)n1;
+    if (Pol::kSortEvery > 0) b += sizeof(int) * ((size_t)n1 + 32);
+    if (Pol::kSmemRings) b += RingSoA<R>::bytes(slots) + 32;
+    return b;
   }
-  __device__ void carve(unsigned char *base, int n1) {
-    double *dp = (double *)base;
-    work = dp; dp += n1;
-    wtot = dp; dp += 64;
-    Acc *ap = (Acc *)dp;
-    rho0 = ap; ap += n1;
-    rho = ap; ap += n1;
+  __device__ void carve(unsigned char *base, int n1, int slots) {
+    wtot = (typename Pol::W *)base;
+    typename Pol::Q *qp = (typename Pol::Q *)(wtot + 64);
+    rho0 = qp; qp += n1;
+    rho = qp; qp += n1;
+    Acc *ap = (Acc *)qp;
     jz = ap; ap += n1;
     chi = ap; ap += n1;
     T = ap; ap += n1;
@@ -76,128 +190,272 @@ struct MarchSmem {
     dpsi = rp; rp += n1;
     ez = rp; rp += n1;
     bth = rp; rp += n1;
+    nb0 = rp; rp += n1;
+    nb1 = rp; rp += n1;
+    ta = rp; rp += n1 + 32;
+    tb = rp; rp += n1 + 32;
+    tc = rp; rp += n1 + 32;
+    td = rp; rp += n1 + 32;
+    tu = rp; rp += n1 + 32;
+    tv = rp; rp += n1 + 32;
+    invR = invV = alpha = ga = gb = gc = nullptr;
     invR = rp; rp += n1;
-    invV = rp; rp += n1;
-    alpha = rp; rp += n1;
     ga = rp; rp += n1;
-    gb = rp; rp += n1;
-    gc = rp; rp += n1;
-    S *sp = (S *)rp;
-    for (int b = 0; b < 2; ++b) {
-      ta[b] = sp; sp += n1;
-      tb[b] = sp; sp += n1;
-      tc[b] = sp; sp += n1;
-      td[b] = sp; sp += n1;
+    if (Pol::kTables) {
+      invV = rp; rp += n1;
+      alpha = rp; rp += n1;
+      gb = rp; rp += n1;
+      gc = rp; rp += n1;
+    }
+    int *ip = (int *)rp;
+    cnt = nullptr;
+    if (Pol::kSortEvery > 0) {
+      cnt = ip;
+      ip += n1 + 32;
+    }
+    if (Pol::kSmemRings) rings.carve((void *)(((uintptr_t)ip + 31) & ~(uintptr_t)31), slots);
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// node geometry: 1/r_m, 1/V_m, alpha_m and the B_theta rows (central differences, a half
+// cell at the wall), from tables or computed on the fly
+// ---------------------------------------------------------------------------------------
+// division of the solves: the mixed form is compiled with the fast approximate '/'
+__device__ __forceinline__ float div_rn(float a, float b) { return a / b; }
+__device__ __forceinline__ double div_rn(double a, double b) { return a / b; }
+
+template <class Pol>
+struct NodeGeo {
+  using R = typename Pol::R;
+  const R *t_invR, *t_invV, *t_alpha, *t_ga, *t_gb, *t_gc;
+  int nr;
+  R dr, inv_dr, inv_dr2, dr_6, v_wall_inv;
+  __device__ __forceinline__ R invR(int m) const { return t_invR[m]; }
+  __device__ __forceinline__ R invV(int m) const {
+    if (Pol::kTables) return t_invV[m];
+    // V_m = m dr^2 in the interior; dr^2/6 on the axis; dr^2 (nr/2 - 1/6) at the wall
+    return m == 0 ? (R)6 * inv_dr2 : (m == nr ? inv_dr2 * v_wall_inv : t_invR[m] * inv_dr);
+  }
+  __device__ __forceinline__ R alpha(int m) const {
+    if (Pol::kTables) return t_alpha[m];
+    return m == 0 ? (R)0 : (m == nr ? (R)1 : (R)0.5 - t_invR[m] * dr_6);
+  }
+  // row q (node i = q + 1): a_q x_{q-1} + b_q x_q + c_q x_{q+1}, without the -chi shift, and
+  // its row sum a + b + c.  The row sum is the small margin of diagonal dominance (about
+  // -1/(r_{i-1/2} r_{i+1/2}) against a diagonal of -2/dr^2), so it is formed directly, never
+  // as the difference of the large coefficients.  1/(j + 1/2) comes from the table ga in the
+  // mixed form.
+  __device__ __forceinline__ void row(int q, R &a, R &c, R &sum) const {
+    if (Pol::kTables) {
+      a = t_ga[q];
+      c = t_gc[q];
+      sum = t_ga[q] + t_gb[q] + t_gc[q];  // FP64: the cancellation costs ~1e-13 of the margin
+      return;
+    }
+    const int i = q + 1;
+    const R ihm = t_ga[i - 1], ihp = t_ga[i];  // 1/(i - 1/2), 1/(i + 1/2)
+    if (i < nr) {
+      a = q == 0 ? (R)0 : (R)(i - 1) * ihm * inv_dr2;
+      c = (R)(i + 1) * ihp * inv_dr2;
+      sum = q == 0 ? (R)(-4.0 / 3.0) * inv_dr2 : -(ihm * ihp) * inv_dr2;
+    } else {
+      a = q == 0 ? (R)0 : (R)(2 * (i - 1)) * ihm * inv_dr2;
+      c = (R)0;
+      sum = q == 0 ? (R)-2 * (R)i * ihm * inv_dr2 : (R)-2 * ihm * inv_dr2;
     }
   }
 };
 
-// One field solve for the rings at radius (pc + pf) dr (cell index pc, offset pf in [0,1])
-// with momenta (pur, put).  nbA/nbB: the beam-density rows to average (the same row for
-// stage 1).  On return Gam[p] = Gamma of ring p and Fc[p] = (gamma/Gamma) psi'(r_p) -
-// B_theta(r_p); the node arrays psi, dpsi, ez, bth hold the fields.
-template <class Pol, int NT, int PPT>
-__device__ __forceinline__ void solve_stage(MarchSmem<Pol> &sm, const SimDesc &d, int j0,
-                                            const int (&pc)[PPT], const typename Pol::R (&pf)[PPT],
-                                            const typename Pol::R (&pur)[PPT],
-                                            const typename Pol::R (&put)[PPT],
-                                            const typename Pol::R (&cG0)[PPT],
-                                            const typename Pol::R (&cw)[PPT],
-                                            const typename Pol::G *nbA, const typename Pol::G *nbB,
-                                            typename Pol::R (&Gam)[PPT], typename Pol::R (&Fc)[PPT]) {
+template <class Pol, int NT>
+__device__ __forceinline__ void fill_tables(MarchSmem<Pol> &sm, int nr, double dr) {
   using R = typename Pol::R;
+  for (int m = threadIdx.x; m <= nr; m += NT) {
+    sm.invR[m] = (R)(m > 0 ? 1.0 / ((double)m * dr) : 0.0);
+    if constexpr (Pol::kTables) {
+      sm.invV[m] = (R)(1.0 / node_volume(m, nr, dr));
+      sm.alpha[m] = (R)(m > 0 ? node_alpha(m, nr) : 0.0);
+      if (m < nr) {
+        const int i = m + 1;
+        const double idr2 = 1.0 / (dr * dr), rm = i - 0.5, rp = i + 0.5;
+        double a, b, c;
+        if (i < nr) {
+          a = (i - 1) / rm * idr2;
+          c = (i + 1) / rp * idr2;
+          b = -(double)i * (1.0 / rp + 1.0 / rm) * idr2;
+        } else {
+          a = 2.0 * (i - 1) / rm * idr2;
+          c = 0.0;
+          b = -2.0 * (double)i / rm * idr2;
+        }
+        sm.ga[m] = (R)(m == 0 ? 0.0 : a);
+        sm.gb[m] = (R)b;
+        sm.gc[m] = (R)c;
+      }
+    } else {
+      sm.ga[m] = (R)(1.0 / ((double)m + 0.5));
+    }
+  }
+}
+
+// Charge sums.  FP64 form: plain doubles.  Mixed form: a ring's hat contributions w(1-f) and
+// w f are exact float-float products (two-product by FMA), summed over the window in
+// float-float, and converted to 64-bit fixed point (2^44 units) for the shared-memory
+// atomics; the integer sums are exact, so rho - rho0 loses nothing to cancellation.
+constexpr double kQScale = 17592186044416.0;  // 2^44
+__device__ __forceinline__ FF two_prod(float a, float b) {
+  const float p = a * b;
+  return FF{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ long long ff_to_q(FF x) {
+  return __float2ll_rn(x.h * (float)kQScale) + __float2ll_rn(x.l * (float)kQScale);
+}
+template <class Q, class W>
+__device__ __forceinline__ W q_to_wide(Q d);
+template <>
+__device__ __forceinline__ double q_to_wide<double, double>(double d) { return d; }
+template <>
+__device__ __forceinline__ FF q_to_wide<long long, FF>(long long d) {
+  // exact split of the integer into two floats, then the exact power-of-two rescale
+  const float hi = (float)d;
+  const float lo = (float)(d - (long long)hi);
+  const float s = (float)(1.0 / kQScale);
+  return FF{hi * s, lo * s};
+}
+
+// Parallel cyclic reduction (Hockney) on rows a_q x_{q-1} + b_q x_q + c_q x_{q+1} = d_q
+// stored as (a, s = a + b + c, c, d).  For this M-matrix (a, c >= 0, s < 0) the eliminated
+// row sum s' = s - k1 s_{q-k} - k2 s_{q+k} (k1 = a_q/b_{q-k}, k2 = c_q/b_{q+k}, both <= 0)
+// adds terms of one sign, so the margin of diagonal dominance is never lost to cancellation;
+// b = s - a - c likewise.  After ceil(log2 n) doublings a = c = 0 and x_q = d_q / s_q.
+// Double-buffered; returns the buffer holding the result.  Ends with a barrier.
+template <int NT, class S>
+__device__ __forceinline__ int pcr_rowsum(S *a0, S *s0, S *c0, S *d0, S *a1, S *s1, S *c1, S *d1, int n) {
+  int cur = 0;
+  for (int k = 1; k < n; k <<= 1) {
+    const S *a = cur ? a1 : a0, *sm_ = cur ? s1 : s0, *c = cur ? c1 : c0, *d = cur ? d1 : d0;
+    S *an = cur ? a0 : a1, *sn = cur ? s0 : s1, *cn = cur ? c0 : c1, *dn = cur ? d0 : d1;
+    for (int q = threadIdx.x; q < n; q += NT) {
+      const S aq = a[q], cq = c[q];
+      S sq = sm_[q], dq = d[q], na = (S)0, nc = (S)0;
+      if (q - k >= 0) {
+        const S bm = sm_[q - k] - a[q - k] - c[q - k];
+        const S k1 = aq / bm;
+        sq -= k1 * sm_[q - k];
+        dq -= k1 * d[q - k];
+        na = -a[q - k] * k1;
+      }
+      if (q + k < n) {
+        const S bp = sm_[q + k] - a[q + k] - c[q + k];
+        const S k2 = cq / bp;
+        sq -= k2 * sm_[q + k];
+        dq -= k2 * d[q + k];
+        nc = -c[q + k] * k2;
+      }
+      an[q] = na;
+      sn[q] = sq;
+      cn[q] = nc;
+      dn[q] = dq;
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  return cur;
+}
+
+// ---------------------------------------------------------------------------------------
+// node solves (all threads of the CTA)
+// ---------------------------------------------------------------------------------------
+
+// Block-wide inclusive scan (suffix scan if Reverse) of n values, fused with its producer and
+// consumer: in(m) gives element m, out(m, s) receives the scan at m.  Each thread holds up to
+// EMAX consecutive elements in registers; warps scan the thread totals with shuffles and warp
+// 0 scans the warp totals.  Contains two barriers and ends with one.
+template <int NT, int EMAX, bool Reverse, class W, class In, class Out>
+__device__ __forceinline__ void block_scan_fused(int n, W *wtot, In &&in, Out &&out) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int E = (n + NT - 1) / NT;  // <= EMAX
+  const int beg = tid * E;
+  W v[EMAX];
+  W tot = wide_zero<W>();
+#pragma unroll
+  for (int j = 0; j < EMAX; ++j) {
+    const int q = beg + j;
+    v[j] = wide_zero<W>();
+    if (j < E && q < n) {
+      v[j] = in(Reverse ? n - 1 - q : q);
+      tot = wide_add(tot, v[j]);
+    }
+  }
+  W incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const W t = wide_shfl_up(incl, o);
+    if (lane >= o) incl = wide_add(incl, t);
+  }
+  if (lane == 31) wtot[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    W t = lane < NT / 32 ? wtot[lane] : wide_zero<W>();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const W u = wide_shfl_up(t, o);
+      if (lane >= o) t = wide_add(t, u);
+    }
+    if (lane < NT / 32) wtot[NT / 32 + lane] = t;
+  }
+  __syncthreads();
+  W run = warp > 0 ? wtot[NT / 32 + warp - 1] : wide_zero<W>();
+  const W below = wide_shfl_up(incl, 1);
+  if (lane > 0) run = wide_add(run, below);
+#pragma unroll
+  for (int j = 0; j < EMAX; ++j) {
+    const int q = beg + j;
+    if (j < E && q < n) {
+      run = wide_add(run, v[j]);
+      out(Reverse ? n - 1 - q : q, run);
+    }
+  }
+  __syncthreads();
+}
+
+// psi from the charge deposit in sm.rho: Phi_m = sum_{i<m} delta_i + alpha_m delta_m,
+// psi'_m = Phi_m / r_m, psi(R) = 0, psi = inward trapezoid sum of psi'.  Ends with a barrier.
+template <class Pol, int NT>
+__device__ __forceinline__ void solve_psi(MarchSmem<Pol> &sm, const NodeGeo<Pol> &geo, typename Pol::W *wtot) {
+  using R = typename Pol::R;
+  using W = typename Pol::W;
+  const int nr = geo.nr, n1 = nr + 1;
+  block_scan_fused<NT, 3, false, W>(
+      n1, wtot, [&](int m) { return q_to_wide<typename Pol::Q, W>(sm.rho[m] - sm.rho0[m]); },
+      [&](int m, W incl) {
+        R dp = (R)0;
+        if (m > 0) {
+          const R v = (R)wide_value(q_to_wide<typename Pol::Q, W>(sm.rho[m] - sm.rho0[m]));
+          dp = (R)wide_value(wide_add(incl, wide_of<W, R>(-((R)1 - geo.alpha(m)) * v))) * geo.invR(m);
+        }
+        sm.dpsi[m] = dp;
+      });
+  const R hdr = (R)0.5 * geo.dr;
+  block_scan_fused<NT, 3, true, W>(
+      n1, wtot, [&](int m) { return wide_of<W, R>(m < nr ? hdr * (sm.dpsi[m] + sm.dpsi[m + 1]) : (R)0); },
+      [&](int m, W incl) { sm.psi[m] = -(R)wide_value(incl); });
+}
+
+// E_z, the Helmholtz system for B_theta and its PCR solve, from the current-type deposits
+// and the beam-density rows nbA, nbB (averaged).  Ends with a barrier.
+template <class Pol, int NT>
+__device__ __forceinline__ void solve_fields(MarchSmem<Pol> &sm, const NodeGeo<Pol> &geo, const typename Pol::R *nbA,
+                                             const typename Pol::R *nbB, typename Pol::W *wtot) {
+  using R = typename Pol::R;
+  using W = typename Pol::W;
   using Acc = typename Pol::Acc;
-  using S = typename Pol::S;
-  const int tid = threadIdx.x, nr = d.nr, n1 = nr + 1, np = d.np;
-  const R inv_dr = (R)(1.0 / d.dr);
-  const R dr = (R)d.dr;
-  const R hdr = (R)(0.5 * d.dr);
-
-  // 1. charge deposit
-  for (int i = tid; i < n1; i += NT) {
-    sm.rho[i] = (Acc)0;
-    sm.jz[i] = (Acc)0;
-    sm.chi[i] = (Acc)0;
-    sm.T[i] = (Acc)0;
-    sm.P[i] = (Acc)0;
-    sm.U[i] = (Acc)0;
-    sm.K[i] = (Acc)0;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int p = 0; p < PPT; ++p) {
-    if (j0 + p < np) {
-      const int c = pc[p];
-      const R f = pf[p];
-      atomicAdd(&sm.rho[c], (Acc)(cw[p] * ((R)1 - f)));
-      atomicAdd(&sm.rho[c + 1], (Acc)(cw[p] * f));
-    }
-  }
-  __syncthreads();
-
-  // 2. psi: enclosed charge Phi_m = sum_{i<m} delta_i + alpha_m delta_m, psi' = Phi/r,
-  //    inward trapezoid sum from psi(R) = 0
-  for (int m = tid; m < n1; m += NT) sm.work[m] = (double)(sm.rho[m] - sm.rho0[m]);
-  __syncthreads();
-  block_scan<NT>(sm.work, n1, sm.wtot, false);
+  const int tid = threadIdx.x, nr = geo.nr, n1 = nr + 1;
+  const R inv_dr = geo.inv_dr, hdr = (R)0.5 * geo.dr;
+  // node densities; d_xi psi'_m = -((1 - alpha_m) K_{m-1} + alpha_m K_m) / (dr r_m) into ez
   for (int m = tid; m < n1; m += NT) {
-    R dp = (R)0;
-    if (m > 0) {
-      const R v = (R)(sm.rho[m] - sm.rho0[m]);
-      dp = ((R)sm.work[m] - ((R)1 - sm.alpha[m]) * v) * sm.invR[m];
-    }
-    sm.dpsi[m] = dp;
-  }
-  __syncthreads();
-  for (int m = tid; m < n1; m += NT) sm.work[m] = m < nr ? (double)(hdr * (sm.dpsi[m] + sm.dpsi[m + 1])) : 0.0;
-  __syncthreads();
-  block_scan<NT>(sm.work, n1, sm.wtot, true);
-  for (int m = tid; m < n1; m += NT) sm.psi[m] = (R)(-sm.work[m]);
-  __syncthreads();
-
-  // 3. ring quantities (Eqs. 1-4) and the current-type deposits
-#pragma unroll
-  for (int p = 0; p < PPT; ++p) {
-    if (j0 + p < np) {
-      const int c = pc[p];
-      const R f = pf[p];
-      const R rp = ((R)c + f) * dr;
-      const R G = cG0[p] + interp(sm.psi, c, f);
-      if (!(G > (R)0)) flag(d.status, ST_NUMERIC);
-      const R iG = (R)1 / G;
-      const R up2 = pur[p] * pur[p] + put[p] * put[p];
-      const R gam = ((R)1 + up2 + G * G) * (R)0.5 * iG;
-      const R uz = gam - G;
-      const R a = pur[p] * iG;
-      const R dp = interp(sm.dpsi, c, f);
-      const R cent = rp > (R)0 ? put[p] * put[p] * iG / rp : (R)0;
-      const R gq = gam * iG * dp;
-      const R F0 = gq + cent;
-      const R w = cw[p];
-      const R vjz = -w * uz * iG, vchi = w * iG, vT = w * a * a, vP = w * (a * a * dp - F0) * iG, vU = w * a * iG;
-      const R g0 = (R)1 - f;
-      atomicAdd(&sm.jz[c], (Acc)(vjz * g0));
-      atomicAdd(&sm.jz[c + 1], (Acc)(vjz * f));
-      atomicAdd(&sm.chi[c], (Acc)(vchi * g0));
-      atomicAdd(&sm.chi[c + 1], (Acc)(vchi * f));
-      atomicAdd(&sm.T[c], (Acc)(vT * g0));
-      atomicAdd(&sm.T[c + 1], (Acc)(vT * f));
-      atomicAdd(&sm.P[c], (Acc)(vP * g0));
-      atomicAdd(&sm.P[c + 1], (Acc)(vP * f));
-      atomicAdd(&sm.U[c], (Acc)(vU * g0));
-      atomicAdd(&sm.U[c + 1], (Acc)(vU * f));
-      atomicAdd(&sm.K[c], (Acc)(w * a));
-      Gam[p] = G;
-      Fc[p] = gq;
-    }
-  }
-  __syncthreads();
-
-  // 4a. node densities (divide by the ring volumes); d_xi psi' at the nodes from the cell
-  //     currents, then E_z = d_xi psi by the inward trapezoid sum from E_z(R) = 0
-  for (int m = tid; m < n1; m += NT) {
-    const R iv = sm.invV[m];
-    const R nbm = (R)0.5 * ((R)nbA[m] + (R)nbB[m]);
+    const R iv = geo.invV(m);
+    const R nbm = (R)0.5 * (nbA[m] + nbB[m]);
     sm.jz[m] = (Acc)((R)sm.jz[m] * iv - nbm);
     sm.chi[m] = (Acc)((R)sm.chi[m] * iv);
     sm.T[m] = (Acc)((R)sm.T[m] * iv);
@@ -205,49 +463,49 @@ __device__ __forceinline__ void solve_stage(MarchSmem<Pol> &sm, const SimDesc &d
     sm.U[m] = (Acc)((R)sm.U[m] * iv);
     R dz = (R)0;
     if (m > 0) {
-      const R al = sm.alpha[m];
+      const R al = geo.alpha(m);
       const R Km = m < nr ? (R)sm.K[m] : (R)0;
-      dz = -(((R)1 - al) * (R)sm.K[m - 1] + al * Km) * sm.invR[m] * inv_dr;
+      dz = -(((R)1 - al) * (R)sm.K[m - 1] + al * Km) * geo.invR(m) * inv_dr;
     }
     sm.ez[m] = dz;
   }
   __syncthreads();
-  for (int m = tid; m < n1; m += NT) sm.work[m] = m < nr ? (double)(hdr * (sm.ez[m] + sm.ez[m + 1])) : 0.0;
-  __syncthreads();
-  block_scan<NT>(sm.work, n1, sm.wtot, true);
-  for (int m = tid; m < n1; m += NT) sm.ez[m] = (R)(-sm.work[m]);
-  __syncthreads();
-  // 4b. the Helmholtz system for B_theta at nodes 1..nr (row q = i - 1)
+  // E_z: inward trapezoid sum from E_z(R) = 0 (in place over the d_xi psi' values)
+  block_scan_fused<NT, 3, true, W>(
+      n1, wtot, [&](int m) { return wide_of<W, R>(m < nr ? hdr * (sm.ez[m] + sm.ez[m + 1]) : (R)0); },
+      [&](int m, W incl) { sm.ez[m] = -(R)wide_value(incl); });  // inputs are all read first
+  // rows q = 0..nr-1 (node i = q + 1): central differences, a half cell at the wall
   const R i2dr = (R)0.5 * inv_dr;
   for (int q = tid; q < nr; q += NT) {
     const int i = q + 1;
     const R Qi = (R)sm.P[i] + sm.ez[i] * (R)sm.U[i];
     const R Ti = (R)sm.T[i];
+    R a, c, sgeo;
+    geo.row(q, a, c, sgeo);
     R rhs;
     if (i < nr)
       rhs = ((R)sm.jz[i + 1] - (R)sm.jz[i - 1]) * i2dr + Qi + ((R)sm.T[i + 1] - (R)sm.T[i - 1]) * i2dr +
-            Ti * sm.invR[i];
+            Ti * geo.invR(i);
     else
-      rhs = Qi + (Ti - (R)sm.T[i - 1]) * inv_dr + Ti * sm.invR[i] - ((R)sm.jz[i - 1] + (R)sm.jz[i]) * inv_dr;
-    sm.ta[0][q] = (S)sm.ga[q];
-    sm.tb[0][q] = (S)(sm.gb[q] - (R)sm.chi[i]);
-    sm.tc[0][q] = (S)sm.gc[q];
-    sm.td[0][q] = (S)rhs;
+      rhs = Qi + (Ti - (R)sm.T[i - 1]) * inv_dr + Ti * geo.invR(i) - ((R)sm.jz[i - 1] + (R)sm.jz[i]) * inv_dr;
+    sm.ta[q] = a;
+    sm.tb[q] = sgeo - (R)sm.chi[i];  // row sum a + b + c (both terms negative)
+    sm.tc[q] = c;
+    sm.td[q] = rhs;
   }
   __syncthreads();
-  const int cur = pcr_solve<NT, S>(sm.ta[0], sm.tb[0], sm.tc[0], sm.td[0], sm.ta[1], sm.tb[1], sm.tc[1],
-                                   sm.td[1], nr);
-  for (int m = tid; m < n1; m += NT) sm.bth[m] = m > 0 ? (R)(sm.td[cur][m - 1] / sm.tb[cur][m - 1]) : (R)0;
+  // parallel cyclic reduction (on row sums); the second buffer reuses the deposit arrays J_z, chi, T, P,
+  // which are dead once the rows are set up (they are zeroed before the next pass B)
+  static_assert(sizeof(Acc) == sizeof(R), "PCR buffer reuses deposit arrays");
+  const int cur = pcr_rowsum<NT, R>(sm.ta, sm.tb, sm.tc, sm.td, (R *)sm.jz, (R *)sm.chi, (R *)sm.T, (R *)sm.P, nr);
+  const R *bb = cur ? (const R *)sm.chi : sm.tb, *dd = cur ? (const R *)sm.P : sm.td;  // row sum = diagonal now
+  for (int m = tid; m < n1; m += NT) sm.bth[m] = m > 0 ? dd[m - 1] / bb[m - 1] : (R)0;
   __syncthreads();
-
-  // 5. Cartesian radial force on each ring
-#pragma unroll
-  for (int p = 0; p < PPT; ++p) {
-    if (j0 + p < np) {
-      Fc[p] = Fc[p] - interp(sm.bth, pc[p], pf[p]);
-    }
-  }
 }
+
+// ---------------------------------------------------------------------------------------
+// ring moves and windowed deposits
+// ---------------------------------------------------------------------------------------
 
 // Move a ring at radius r = (c + f) dr by the Cartesian displacement (dx, dy) from (r, 0)
 // and give it the Cartesian momentum (ux, uy).  The new radius is formed as the exact
@@ -255,25 +513,24 @@ __device__ __forceinline__ void solve_stage(MarchSmem<Pol> &sm, const SimDesc &d
 // precision is lost to the size of r.  Returns the new cell (cn, fn), the radius rn, and the
 // radial / azimuthal momenta; a ring beyond the wall r = nr dr is reflected specularly.
 template <class R>
-__device__ __forceinline__ void move_ring(int c, R f, R r, R dx, R dy, R ux, R uy, R inv_dr, int nr, int &cn,
-                                          R &fn, R &rn, R &urn, R &utn) {
+__device__ __forceinline__ void move_ring(int c, R f, R r, R dx, R dy, R ux, R uy, R inv_dr, R dr, int nr,
+                                          int &cn, R &fn, R &rn, R &urn, R &utn) {
   const R xn = r + dx, yn = dy;
-  R rr = sqrt(xn * xn + yn * yn);
+  const R rr = sqrt(xn * xn + yn * yn);
   const R den = rr + r;
   const R delta = den > (R)0 ? (dx * ((R)2 * r + dx) + dy * dy) / den : (R)0;
   R s = f + delta * inv_dr;  // offset from node c, in cells
   if (rr > (R)0) {
-    urn = (xn * ux + yn * uy) / rr;
-    utn = (xn * uy - yn * ux) / rr;
+    const R irr = (R)1 / rr;
+    urn = (xn * ux + yn * uy) * irr;
+    utn = (xn * uy - yn * ux) * irr;
   } else {
     urn = sqrt(ux * ux + uy * uy);
     utn = (R)0;
   }
-  R tot = (R)c + s;  // r'/dr
-  if (tot > (R)nr) {  // specular reflection at the wall
-    s = (R)(2 * (nr - c)) - s;  // r'/dr = 2 nr - (c + s), kept relative to c
+  if ((R)c + s > (R)nr) {  // specular reflection at the wall: r'/dr -> 2 nr - r'/dr
+    s = (R)(2 * (nr - c)) - s;
     urn = -urn;
-    tot = (R)c + s;
   }
   const R fl = floor(s);
   int ci = c + (int)fl;
@@ -288,107 +545,450 @@ __device__ __forceinline__ void move_ring(int c, R f, R r, R dx, R dy, R ux, R u
   }
   cn = ci;
   fn = fo;
-  rn = tot / inv_dr;
+  rn = ((R)ci + fo) * dr;
+}
+
+// Window of three cells c0..c0+2 (four nodes) summed in registers; a ring outside the
+// window deposits directly.
+template <class R, int NV>
+struct WindowAcc {
+  int c0 = -1;
+  R n[4][NV];
+  __device__ __forceinline__ void init(int c) {
+    c0 = c;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) n[a][q] = (R)0;
+  }
+  __device__ __forceinline__ bool add(int c, R f, const R (&v)[NV]) {
+    const int o = c - c0;
+    if (o < 0 || o > 2) return false;
+    const R g = (R)1 - f;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const R lo = v[q] * g, hi = v[q] * f;
+      n[0][q] += o == 0 ? lo : (R)0;
+      n[1][q] += o == 0 ? hi : (o == 1 ? lo : (R)0);
+      n[2][q] += o == 1 ? hi : (o == 2 ? lo : (R)0);
+      n[3][q] += o == 2 ? hi : (R)0;
+    }
+    return true;
+  }
+};
+
+// Warp segments: maximal runs of consecutive lanes with the same key (a window's first
+// cell).  sum() is the inclusive segmented sum from the segment's head; the segment's tail
+// lane then holds the total, so one lane per segment issues the shared-memory atomics
+// (same-address atomics of one instruction serialise).
+struct WarpSeg {
+  int lane, seg_start, tail_lane;
+  bool is_tail;
+  __device__ __forceinline__ explicit WarpSeg(int key) {
+    lane = threadIdx.x & 31;
+    const int kprev = __shfl_up_sync(kFull, key, 1);
+    const int knext = __shfl_down_sync(kFull, key, 1);
+    const bool head = lane == 0 || kprev != key;
+    is_tail = lane == 31 || knext != key;
+    const unsigned heads = __ballot_sync(kFull, head);
+    const unsigned tails = __ballot_sync(kFull, is_tail);
+    seg_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    tail_lane = __ffs(tails & (0xffffffffu << lane)) - 1;
+  }
+  template <class T>
+  __device__ __forceinline__ T sum(T v) const {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T u = __shfl_up_sync(kFull, v, o);
+      if (lane - o >= seg_start) v += u;
+    }
+    return v;
+  }
+};
+
+// A ring's charge contributions to the node pair (c, c+1) in the form's charge-window type.
+template <class Pol>
+struct ChargeWin;
+template <>
+struct ChargeWin<PolFP64> {
+  int c0 = -1;
+  double n[4];
+  __device__ __forceinline__ void init(int c) {
+    c0 = c;
+    n[0] = n[1] = n[2] = n[3] = 0.0;
+  }
+  __device__ __forceinline__ bool add(int c, double f, double w) {
+    const int o = c - c0;
+    if (o < 0 || o > 2) return false;
+    const double lo = w * (1.0 - f), hi = w * f;
+    n[0] += o == 0 ? lo : 0.0;
+    n[1] += o == 0 ? hi : (o == 1 ? lo : 0.0);
+    n[2] += o == 1 ? hi : (o == 2 ? lo : 0.0);
+    n[3] += o == 2 ? hi : 0.0;
+    return true;
+  }
+  __device__ __forceinline__ static void direct(double *rho, int c, double f, double w) {
+    atomicAdd(&rho[c], w * (1.0 - f));
+    atomicAdd(&rho[c + 1], w * f);
+  }
+  __device__ __forceinline__ double node(int a) const { return n[a]; }
+};
+template <>
+struct ChargeWin<PolMixed> {
+  int c0 = -1;
+  FF n[4];
+  __device__ __forceinline__ void init(int c) {
+    c0 = c;
+    n[0] = n[1] = n[2] = n[3] = FF{0.f, 0.f};
+  }
+  __device__ __forceinline__ bool add(int c, float f, float w) {
+    const int o = c - c0;
+    if (o < 0 || o > 2) return false;
+    const FF hi = two_prod(w, f), lo = ff_add(FF{w, 0.f}, FF{-hi.h, -hi.l});  // lo + hi = w
+    const FF z{0.f, 0.f};
+    n[0] = ff_add(n[0], o == 0 ? lo : z);
+    n[1] = ff_add(n[1], o == 0 ? hi : (o == 1 ? lo : z));
+    n[2] = ff_add(n[2], o == 1 ? hi : (o == 2 ? lo : z));
+    n[3] = ff_add(n[3], o == 2 ? hi : z);
+    return true;
+  }
+  __device__ __forceinline__ static void direct(long long *rho, int c, float f, float w) {
+    const FF hi = two_prod(w, f), lo = ff_add(FF{w, 0.f}, FF{-hi.h, -hi.l});
+    atomicAdd((unsigned long long *)&rho[c], (unsigned long long)ff_to_q(lo));
+    atomicAdd((unsigned long long *)&rho[c + 1], (unsigned long long)ff_to_q(hi));
+  }
+  __device__ __forceinline__ long long node(int a) const { return ff_to_q(n[a]); }
+};
+
+__device__ __forceinline__ void q_atomic_add(double *p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void q_atomic_add(long long *p, long long v) {
+  atomicAdd((unsigned long long *)p, (unsigned long long)v);
+}
+
+// Flush a charge window into rho over the warp.  All lanes of the warp call it.
+template <class Pol>
+__device__ __forceinline__ void flush_charge(MarchSmem<Pol> &sm, const ChargeWin<Pol> &acc, int nr) {
+  using Q = typename Pol::Q;
+  const WarpSeg seg(acc.c0);
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const Q t = seg.sum(acc.node(a));
+    if (seg.is_tail && acc.c0 >= 0 && acc.c0 + a <= nr) q_atomic_add(&sm.rho[acc.c0 + a], t);
+  }
+}
+
+// Charge deposit of one ring through a window (direct atomics outside it).
+template <class Pol>
+__device__ __forceinline__ void add_charge(MarchSmem<Pol> &sm, ChargeWin<Pol> &acc, int p, int c,
+                                           typename Pol::R f, typename Pol::R w) {
+  if (p == 0) acc.init(c);
+  if (!acc.add(c, f, w)) ChargeWin<Pol>::direct(sm.rho, c, f, w);
+}
+
+// ---------------------------------------------------------------------------------------
+// ring passes
+// ---------------------------------------------------------------------------------------
+
+// Pass B: ring quantities at the position given by pos(sl, c, f, u_r, u_theta) and the
+// current-type deposits.  Gam[p] = Gamma, gq[p] = (gamma/Gamma) psi'(r).  All threads call.
+template <class Pol, int NT, int PPT, class Pos>
+__device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int np,
+                                              int nr, typename Pol::R dr, int *status, Pos &&pos,
+                                              typename Pol::R (&Gam)[PPT], typename Pol::R (&gq)[PPT]) {
+  using R = typename Pol::R;
+  using Acc = typename Pol::Acc;
+  const int t = threadIdx.x;
+  WindowAcc<R, 5> acc;
+  acc.init(-8);
+  R kw[3] = {(R)0, (R)0, (R)0};
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    Gam[p] = (R)1;
+    gq[p] = (R)0;
+    if (t * PPT + p < np) {
+      const int sl = p * NT + t;
+      int c;
+      R f, u_r, u_t;
+      pos(sl, c, f, u_r, u_t);
+      if (p == 0) acc.init(c);
+      const R rp = ((R)c + f) * dr;
+      const R G = rs.G0[sl] + interp(sm.psi, c, f);
+      if (!(G > (R)0)) flag(status, ST_NUMERIC);
+      const R iG = (R)1 / G;
+      const R up2 = u_r * u_r + u_t * u_t;
+      const R gam = ((R)1 + up2 + G * G) * (R)0.5 * iG;
+      const R uz = gam - G;
+      const R a = u_r * iG;
+      const R dp = interp(sm.dpsi, c, f);
+      const R cent = rp > (R)0 ? u_t * u_t * iG / rp : (R)0;
+      const R g = gam * iG * dp;
+      const R w = rs.w[sl];
+      const R v[5] = {-w * uz * iG, w * iG, w * a * a, w * (a * a * dp - g - cent) * iG, w * a * iG};
+      if (acc.add(c, f, v)) {
+        const int o = c - acc.c0;
+        kw[0] += o == 0 ? w * a : (R)0;
+        kw[1] += o == 1 ? w * a : (R)0;
+        kw[2] += o == 2 ? w * a : (R)0;
+      } else {
+        const R g0 = (R)1 - f;
+        Acc *arr[5] = {sm.jz, sm.chi, sm.T, sm.P, sm.U};
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          atomicAdd(&arr[q][c], (Acc)(v[q] * g0));
+          atomicAdd(&arr[q][c + 1], (Acc)(v[q] * f));
+        }
+        atomicAdd(&sm.K[c], (Acc)(w * a));
+      }
+      Gam[p] = G;
+      gq[p] = g;
+    }
+  }
+  const WarpSeg seg(acc.c0);
+  const int c = acc.c0;
+  const bool emit = seg.is_tail && c >= 0;
+  Acc *arr[5] = {sm.jz, sm.chi, sm.T, sm.P, sm.U};
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const R tsum = seg.sum(acc.n[a][q]);
+      if (emit && c + a <= nr) atomicAdd(&arr[q][c + a], (Acc)tsum);
+    }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const R tsum = seg.sum(kw[a]);
+    if (emit && c + a < nr) atomicAdd(&sm.K[c + a], (Acc)tsum);
+  }
+}
+
+// Re-sort the rings of the CTA by cell (counting sort) so that each thread's rings are
+// consecutive in radius again.  Rings in the three cells c0..c0+2 of the thread's first ring
+// are counted in registers, combined over warp segments and take their bases with one atomic
+// per cell and segment; others take a rank with their own atomic.  The slot arrays are
+// permuted in place through registers.  Order within a cell follows the atomics.
+template <class Pol, int NT, int PPT>
+__device__ __forceinline__ void resort_rings(MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int np, int nr) {
+  using R = typename Pol::R;
+  const int t = threadIdx.x, n1 = nr + 1;
+  for (int m = t; m < n1; m += NT) sm.cnt[m] = 0;
+  int rc[PPT];
+  R rf[PPT], rur[PPT], rlz[PPT], rG0[PPT], rw[PPT];
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    rc[p] = 0;
+    rf[p] = rur[p] = rlz[p] = rG0[p] = rw[p] = (R)0;
+    if (t * PPT + p < np) {
+      const int sl = p * NT + t;
+      rc[p] = rs.c[sl];
+      rf[p] = rs.f[sl];
+      rur[p] = rs.ur[sl];
+      rlz[p] = rs.lz[sl];
+      rG0[p] = rs.G0[sl];
+      rw[p] = rs.w[sl];
+    }
+  }
+  __syncthreads();
+  int rank[PPT];
+  {
+    const int c0 = t * PPT < np ? rc[0] : -8;
+    int cw[3] = {0, 0, 0};
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      rank[p] = 0;
+      if (t * PPT + p < np) {
+        const int o = rc[p] - c0;
+        if (o >= 0 && o <= 2) {
+          rank[p] = o == 0 ? cw[0] : (o == 1 ? cw[1] : cw[2]);
+          cw[0] += o == 0;
+          cw[1] += o == 1;
+          cw[2] += o == 2;
+        } else {
+          rank[p] = atomicAdd(&sm.cnt[rc[p]], 1) | (1 << 30);
+        }
+      }
+    }
+    const WarpSeg seg(c0);
+    int base[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int incl = seg.sum(cw[a]);
+      int b = 0;
+      if (seg.is_tail && c0 >= 0 && c0 + a < nr && incl > 0) b = atomicAdd(&sm.cnt[c0 + a], incl);
+      b = __shfl_sync(kFull, b, seg.tail_lane);
+      base[a] = b + incl - cw[a];
+    }
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+      if (t * PPT + p < np) {
+        if (rank[p] & (1 << 30)) {
+          rank[p] &= ~(1 << 30);
+        } else {
+          const int o = rc[p] - c0;
+          rank[p] += o == 0 ? base[0] : (o == 1 ? base[1] : base[2]);
+        }
+      }
+  }
+  __syncthreads();
+  // exclusive scan of the counts (warp 0)
+  if (t < 32) {
+    const int E = (n1 + 31) / 32, beg = min(n1, t * E), end = min(n1, beg + E);
+    int s = 0;
+    for (int q = beg; q < end; ++q) s += sm.cnt[q];
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(kFull, incl, o);
+      if (t >= o) incl += u;
+    }
+    int run = incl - s;
+    for (int q = beg; q < end; ++q) {
+      const int v = sm.cnt[q];
+      sm.cnt[q] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  // scatter: rank r goes to thread r / PPT, ring r % PPT, slot (r % PPT) * NT + r / PPT
+#pragma unroll
+  for (int p = 0; p < PPT; ++p)
+    if (t * PPT + p < np) {
+      const int r = sm.cnt[rc[p]] + rank[p];
+      const int sl = (r % PPT) * NT + r / PPT;
+      rs.c[sl] = rc[p];
+      rs.f[sl] = rf[p];
+      rs.ur[sl] = rur[p];
+      rs.lz[sl] = rlz[p];
+      rs.G0[sl] = rG0[p];
+      rs.w[sl] = rw[p];
+    }
+  __syncthreads();
 }
 
 template <class Pol, int NT, int PPT>
 __global__ void __launch_bounds__(NT, 1) march_kernel(const SimDesc *descs, const int *order) {
   using R = typename Pol::R;
   using G = typename Pol::G;
+  using Acc = typename Pol::Acc;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const SimDesc d = descs[order ? order[blockIdx.x] : blockIdx.x];
+  const SimDesc &d = descs[order ? order[blockIdx.x] : blockIdx.x];
   const int tid = threadIdx.x, nr = d.nr, n1 = nr + 1, np = d.np, nxi = d.nxi;
+  constexpr int SLOTS = NT * PPT;
   MarchSmem<Pol> sm;
-  sm.carve(smem_raw, n1);
-  const double dr = d.dr;
-  const R h = (R)d.dxi, R_wall = (R)d.rmax;
+  sm.carve(smem_raw, n1, SLOTS);
+  RingSoA<R> rs;
+  if (Pol::kSmemRings)
+    rs = sm.rings;
+  else
+    rs.carve(d.ring_buf, SLOTS);
+  const double drd = d.dr;
+  const R h = (R)d.dxi, R_wall = (R)d.rmax, dR = (R)drd, inv_dr = (R)(1.0 / drd);
+  const NodeGeo<Pol> geo{sm.invR, sm.invV, sm.alpha, sm.ga, sm.gb, sm.gc, nr, dR, inv_dr, (R)(1.0 / (drd * drd)),
+                          (R)(drd / 6.0), (R)(1.0 / (0.5 * nr - 1.0 / 6.0))};
+  const G *nb = (const G *)d.nb;
+  G *opsi = (G *)d.psi, *oez = (G *)d.ez, *oer = (G *)d.er, *obth = (G *)d.bth;
 
-  // per-simulation node tables: 1/r_m, 1/V_m, alpha_m, and the geometric part of the
-  // B_theta rows (central differences; a half cell at the wall)
+  fill_tables<Pol, NT>(sm, nr, drd);
   for (int m = tid; m < n1; m += NT) {
-    sm.invR[m] = (R)(m > 0 ? 1.0 / ((double)m * dr) : 0.0);
-    sm.invV[m] = (R)(1.0 / node_volume(m, nr, dr));
-    sm.alpha[m] = (R)(m > 0 ? node_alpha(m, nr) : 0.0);
-    if (m < nr) {
-      const int i = m + 1;
-      const double idr2 = 1.0 / (dr * dr), rm = i - 0.5, rp = i + 0.5;
-      double a, b, c;
-      if (i < nr) {
-        a = (i - 1) / rm * idr2;
-        c = (i + 1) / rp * idr2;
-        b = -(double)i * (1.0 / rp + 1.0 / rm) * idr2;
-      } else {
-        a = 2.0 * (i - 1) / rm * idr2;
-        c = 0.0;
-        b = -2.0 * (double)i / rm * idr2;
-      }
-      sm.ga[m] = (R)(m == 0 ? 0.0 : a);
-      sm.gb[m] = (R)b;
-      sm.gc[m] = (R)c;
-    }
+    sm.nb0[m] = (R)nb[m];
+    sm.rho[m] = (typename Pol::Q)0;
+    sm.jz[m] = sm.chi[m] = sm.T[m] = sm.P[m] = sm.U[m] = sm.K[m] = (Acc)0;
   }
-  // rings: contiguous chunk of PPT per thread.  A ring's radius is kept as a cell index c
-  // and an offset f in [0,1] (r = (c + f) dr), so its position resolution is uniform over
-  // the box in either precision; moves are applied as exact radial displacements.
-  const int j0 = tid * PPT;
-  const R dR = (R)dr, inv_dr = (R)(1.0 / dr);
-  int rc[PPT];
-  R rf[PPT], ur[PPT], lz[PPT], cG0[PPT], cw[PPT];
+  // rings: thread t holds rings t*PPT .. t*PPT+PPT-1 (consecutive in radius), slot p*NT + t.
+  // A ring's radius is a cell index c and an offset f in [0,1] (r = (c + f) dr), so its
+  // position resolution is uniform over the box; moves are exact radial displacements.
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
-    const int j = j0 + p;
+    const int j = tid * PPT + p, sl = p * NT + tid;
     if (j < np) {
-      const double s = d.r0[j] / dr;
+      const double s = d.r0[j] / drd;
       int c = (int)floor(s);
       c = c < 0 ? 0 : (c > nr - 1 ? nr - 1 : c);
-      rc[p] = c;
-      rf[p] = (R)(s - (double)c);
-      ur[p] = (R)d.ur0[j];
-      lz[p] = (R)d.lz[j];
-      cG0[p] = (R)d.G0[j];
-      cw[p] = (R)d.w[j];
-    } else {
-      rc[p] = 0;
-      rf[p] = ur[p] = lz[p] = cw[p] = (R)0;
-      cG0[p] = (R)1;
+      rs.c[sl] = c;
+      rs.f[sl] = (R)(s - (double)c);
+      rs.ur[sl] = (R)d.ur0[j];
+      rs.lz[sl] = (R)d.lz[j];
+      rs.G0[sl] = (R)d.G0[j];
+      rs.w[sl] = (R)d.w[j];
     }
   }
   __syncthreads();
-  // ion background: the deposit of the unperturbed electrons (same arithmetic as a stage)
+
+  // positions of the stages: the slice state (stage 1), and the midpoint reached from it with
+  // the stage-1 derivative in the local Cartesian frame (x, y) = (r, 0), (u_x, u_y) =
+  // (u_r, u_theta) (stage 2), recomputed where it is needed
+  auto state_pos = [&](int sl, int &c, R &f, R &u_r, R &u_t) {
+    c = rs.c[sl];
+    f = rs.f[sl];
+    u_r = rs.ur[sl];
+    const R r = ((R)c + f) * dR;
+    u_t = r > (R)0 ? rs.lz[sl] / r : (R)0;
+  };
+  auto midpoint = [&](int sl, int &c, R &f, R &u_r, R &u_t) -> R {
+    const int c0 = rs.c[sl];
+    const R f0 = rs.f[sl], ur0 = rs.ur[sl];
+    const R r = ((R)c0 + f0) * dR;
+    const R ut = r > (R)0 ? rs.lz[sl] / r : (R)0;
+    const R iG = (R)1 / rs.G1[sl];
+    const R dx = (R)0.5 * h * ur0 * iG, dy = (R)0.5 * h * ut * iG;
+    const R uxh = ur0 + (R)0.5 * h * rs.F1[sl];
+    R rr;
+    move_ring<R>(c0, f0, r, dx, dy, uxh, ut, inv_dr, dR, nr, c, f, rr, u_r, u_t);
+    return rr;
+  };
+
+  // charge of the initial slice; it is also the ion background (the deposit of the
+  // unperturbed electrons), so psi starts exactly at zero
   {
-    for (int i = tid; i < n1; i += NT) sm.rho[i] = 0;
-    __syncthreads();
+    ChargeWin<Pol> acc;
+    acc.init(-8);
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-      if (j0 + p < np) {
-        atomicAdd(&sm.rho[rc[p]], (typename Pol::Acc)(cw[p] * ((R)1 - rf[p])));
-        atomicAdd(&sm.rho[rc[p] + 1], (typename Pol::Acc)(cw[p] * rf[p]));
+    for (int p = 0; p < PPT; ++p)
+      if (tid * PPT + p < np) {
+        const int sl = p * NT + tid;
+        add_charge<Pol>(sm, acc, p, rs.c[sl], rs.f[sl], rs.w[sl]);
       }
-    }
-    __syncthreads();
-    for (int i = tid; i < n1; i += NT) sm.rho0[i] = sm.rho[i];
-    __syncthreads();
+    flush_charge<Pol>(sm, acc, nr);
   }
+  __syncthreads();
+  for (int m = tid; m < n1; m += NT) sm.rho0[m] = sm.rho[m];
+  __syncthreads();
 
-  const G *nb = (const G *)d.nb;
-  G *opsi = (G *)d.psi, *oez = (G *)d.ez, *oer = (G *)d.er, *obth = (G *)d.bth;
-  int pc[PPT];
-  R pf[PPT], pur[PPT], put[PPT], G1[PPT], F1[PPT], G2[PPT], F2[PPT];
-
+  R G2[PPT], F2[PPT];
   for (int k = 0; k <= nxi; ++k) {
-    const G *nbk = nb + (size_t)k * n1;
-    // stage 1 at xi_k
+    if (Pol::kSortEvery > 0 && k > 0 && k % Pol::kSortEvery == 0) resort_rings<Pol, NT, PPT>(sm, rs, np, nr);
+    const R *nbk = (k & 1) ? sm.nb1 : sm.nb0, *nbk1 = (k & 1) ? sm.nb0 : sm.nb1;
+    // prefetch beam-density row k+1 (stored in phase P1); n1 <= 3 NT
+    R pre[3] = {(R)0, (R)0, (R)0};
+    if (k < nxi) {
+      const G *row = nb + (size_t)(k + 1) * n1;
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-      const R r = ((R)rc[p] + rf[p]) * dR;
-      pc[p] = rc[p];
-      pf[p] = rf[p];
-      pur[p] = ur[p];
-      put[p] = r > (R)0 ? lz[p] / r : (R)0;
+      for (int q = 0; q < 3; ++q)
+        if (tid + q * NT < n1) pre[q] = (R)row[tid + q * NT];
     }
-    solve_stage<Pol, NT, PPT>(sm, d, j0, pc, pf, pur, put, cG0, cw, nbk, nbk, G1, F1);
-    // fields of slice k
+    // ======== stage 1 at xi_k ========
+    solve_psi<Pol, NT>(sm, geo, sm.wtot);  // P0
+    __syncthreads();
+    if (k < nxi) {  // P1
+      R *dst = (k & 1) ? sm.nb0 : sm.nb1;
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        if (tid + q * NT < n1) dst[tid + q * NT] = pre[q];
+    }
+    for (int i = tid; i < n1; i += NT) sm.rho[i] = (typename Pol::Q)0;
     {
+      R Gs[PPT], gqs[PPT];
+      pass_currents<Pol, NT, PPT>(sm, rs, np, nr, dR, d.status, state_pos, Gs, gqs);
+#pragma unroll
+      for (int p = 0; p < PPT; ++p)
+        if (tid * PPT + p < np) {
+          rs.G1[p * NT + tid] = Gs[p];
+          rs.F1[p * NT + tid] = gqs[p];
+        }
+    }
+    __syncthreads();
+    solve_fields<Pol, NT>(sm, geo, nbk, nbk, sm.wtot);  // P2
+    __syncthreads();
+    {  // P3: fields of slice k, then the move to the midpoint and its charge deposit
       G *o1 = opsi + (size_t)k * n1, *o2 = oez + (size_t)k * n1, *o3 = oer + (size_t)k * n1,
         *o4 = obth + (size_t)k * n1;
       for (int m = tid; m < n1; m += NT) {
@@ -401,51 +1001,78 @@ __global__ void __launch_bounds__(NT, 1) march_kernel(const SimDesc *descs, cons
       }
     }
     if (k == nxi) break;
-    __syncthreads();
-    // midpoint state in the local Cartesian frame (x, y) = (r, 0), (u_x, u_y) = (u_r, u_theta)
+    for (int i = tid; i < n1; i += NT) sm.jz[i] = sm.chi[i] = sm.T[i] = sm.P[i] = sm.U[i] = sm.K[i] = (Acc)0;
+    {
+      ChargeWin<Pol> acc;
+      acc.init(-8);
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-      const R r = ((R)rc[p] + rf[p]) * dR;
-      const R ut = put[p];
-      const R dx = (R)0.5 * h * ur[p] / G1[p], dy = (R)0.5 * h * ut / G1[p];
-      const R uxh = ur[p] + (R)0.5 * h * F1[p], uyh = ut;
-      int cn;
-      R fn, rr, urr, utt;
-      move_ring<R>(rc[p], rf[p], r, dx, dy, uxh, uyh, inv_dr, nr, cn, fn, rr, urr, utt);
-      if (j0 + p < np && !(rr >= (R)0 && rr <= R_wall)) flag(d.status, ST_ESCAPE);
-      pc[p] = cn;
-      pf[p] = fn;
-      pur[p] = urr;
-      put[p] = utt;
+      for (int p = 0; p < PPT; ++p) {
+        if (tid * PPT + p < np) {
+          const int sl = p * NT + tid;
+          rs.F1[sl] = rs.F1[sl] - interp(sm.bth, rs.c[sl], rs.f[sl]);
+          int c;
+          R f, u_r, u_t;
+          const R rr = midpoint(sl, c, f, u_r, u_t);
+          if (!(rr >= (R)0 && rr <= R_wall)) flag(d.status, ST_ESCAPE);
+          add_charge<Pol>(sm, acc, p, c, f, rs.w[sl]);
+        }
+      }
+      flush_charge<Pol>(sm, acc, nr);
     }
-    // stage 2 at xi_k + dxi/2
-    solve_stage<Pol, NT, PPT>(sm, d, j0, pc, pf, pur, put, cG0, cw, nbk, nbk + n1, G2, F2);
-    // full step from the slice-k state with the midpoint derivative
+    __syncthreads();
+    // ======== stage 2 at xi_k + dxi/2 ========
+    solve_psi<Pol, NT>(sm, geo, sm.wtot);  // P0
+    __syncthreads();
+    for (int i = tid; i < n1; i += NT) sm.rho[i] = (typename Pol::Q)0;  // P1
+    pass_currents<Pol, NT, PPT>(sm, rs, np, nr, dR, d.status,
+                                [&](int sl, int &c, R &f, R &u_r, R &u_t) { midpoint(sl, c, f, u_r, u_t); },
+                                G2, F2);
+    __syncthreads();
+    solve_fields<Pol, NT>(sm, geo, nbk, nbk1, sm.wtot);  // P2
+    __syncthreads();
+    // P3: full step from the slice-k state with the midpoint derivative, and the charge
+    // deposit of the new slice
+    for (int i = tid; i < n1; i += NT) sm.jz[i] = sm.chi[i] = sm.T[i] = sm.P[i] = sm.U[i] = sm.K[i] = (Acc)0;
+    {
+      ChargeWin<Pol> acc;
+      acc.init(-8);
 #pragma unroll
-    for (int p = 0; p < PPT; ++p) {
-      const R r = ((R)rc[p] + rf[p]) * dR;
-      const R ut = r > (R)0 ? lz[p] / r : (R)0;
-      const R xh = r + (R)0.5 * h * ur[p] / G1[p];
-      const R yh = (R)0.5 * h * ut / G1[p];
-      const R uxh = ur[p] + (R)0.5 * h * F1[p];
-      const R uyh = ut;
-      const R rh = sqrt(xh * xh + yh * yh);
-      R ex = (R)1, ey = (R)0;
-      if (rh > (R)0) {
-        ex = xh / rh;
-        ey = yh / rh;
+      for (int p = 0; p < PPT; ++p) {
+        if (tid * PPT + p < np) {
+          const int sl = p * NT + tid;
+          int mc;
+          R mf, mu_r, mu_t;
+          midpoint(sl, mc, mf, mu_r, mu_t);
+          const R F2b = F2[p] - interp(sm.bth, mc, mf);
+          const int c0 = rs.c[sl];
+          const R f0 = rs.f[sl], ur0 = rs.ur[sl], G1v = rs.G1[sl], F1v = rs.F1[sl];
+          const R r = ((R)c0 + f0) * dR;
+          const R ut = r > (R)0 ? rs.lz[sl] / r : (R)0;
+          const R iG1 = (R)1 / G1v;
+          const R xh = r + (R)0.5 * h * ur0 * iG1;
+          const R yh = (R)0.5 * h * ut * iG1;
+          const R uxh = ur0 + (R)0.5 * h * F1v;
+          const R rh = sqrt(xh * xh + yh * yh);
+          R ex = (R)1, ey = (R)0;
+          if (rh > (R)0) {
+            const R irh = (R)1 / rh;
+            ex = xh * irh;
+            ey = yh * irh;
+          }
+          const R iG2 = (R)1 / G2[p];
+          const R dx = h * uxh * iG2, dy = h * ut * iG2;
+          const R uxn = ur0 + h * F2b * ex, uyn = ut + h * F2b * ey;
+          int cn;
+          R fn, rn, urn, utn;
+          move_ring<R>(c0, f0, r, dx, dy, uxn, uyn, inv_dr, dR, nr, cn, fn, rn, urn, utn);
+          if (!(rn >= (R)0 && rn <= R_wall) || !isfinite(urn)) flag(d.status, ST_ESCAPE);
+          rs.c[sl] = cn;
+          rs.f[sl] = fn;
+          rs.ur[sl] = urn;
+          add_charge<Pol>(sm, acc, p, cn, fn, rs.w[sl]);
+        }
       }
-      const R dx = h * uxh / G2[p], dy = h * uyh / G2[p];
-      const R uxn = ur[p] + h * F2[p] * ex, uyn = ut + h * F2[p] * ey;
-      int cn;
-      R fn, rn, urn, utn;
-      move_ring<R>(rc[p], rf[p], r, dx, dy, uxn, uyn, inv_dr, nr, cn, fn, rn, urn, utn);
-      if (j0 + p < np && (!(rn >= (R)0 && rn <= R_wall) || !isfinite(urn))) flag(d.status, ST_ESCAPE);
-      if (j0 + p < np) {
-        rc[p] = cn;
-        rf[p] = fn;
-        ur[p] = urn;
-      }
+      flush_charge<Pol>(sm, acc, nr);
     }
     __syncthreads();
   }

@@ -11,7 +11,7 @@
 
 #include "../../include/wake.h"
 #include "beam.cuh"
-#include "march.cuh"
+#include "march_launch.h"
 
 using namespace wake;
 
@@ -35,6 +35,7 @@ struct Sim {
   int np = 0;
   size_t ng = 0;  // grid nodes (nxi+1)(nr+1)
   double *r0 = nullptr, *ur0 = nullptr, *lz = nullptr, *G0 = nullptr, *w = nullptr;
+  void *ring_buf = nullptr;  // ring slot arrays in global memory (FP64 form)
   void *nb = nullptr, *psi = nullptr, *ez = nullptr, *er = nullptr, *bth = nullptr;
   void *bx = nullptr, *by = nullptr, *bux = nullptr, *buy = nullptr;
   double *bxi = nullptr, *buz = nullptr;
@@ -65,7 +66,7 @@ struct wake_sim {
 namespace {
 
 void free_sim(Sim &s) {
-  void *ptrs[] = {s.r0, s.ur0, s.lz, s.G0, s.w, s.nb, s.psi, s.ez, s.er, s.bth, s.bx, s.by, s.bux, s.buy,
+  void *ptrs[] = {s.r0, s.ur0, s.lz, s.G0, s.w, s.ring_buf, s.nb, s.psi, s.ez, s.er, s.bth, s.bx, s.by, s.bux, s.buy,
                   s.bxi, s.buz, s.blost, s.status};
   for (void *q : ptrs)
     if (q) cudaFree(q);
@@ -77,7 +78,7 @@ int check_params(const wake_params &p, int prec0) {
   if (p.precision != prec0) return fail(WAKE_EINVAL, "all simulations of one handle must share the precision");
   if (p.nr < 2 || p.nr > 1024) return fail(WAKE_EINVAL, "nr must be in [2, 1024]");
   if (p.nxi < 2 || p.nxi > (1 << 20)) return fail(WAKE_EINVAL, "nxi must be in [2, 2^20]");
-  if (p.ppc < 1 || (int64_t)p.nr * p.ppc > 16384) return fail(WAKE_EINVAL, "need ppc >= 1 and nr*ppc <= 16384");
+  if (p.ppc < 1 || (int64_t)p.nr * p.ppc > 8192) return fail(WAKE_EINVAL, "need ppc >= 1 and nr*ppc <= 8192");
   if (p.u_th < 0.0 || (p.u_th > 0.0 && p.ppc % 2)) return fail(WAKE_EINVAL, "a warm plasma needs u_th > 0 and an even ppc");
   if (!(p.rmax > 0.0) || !(p.ximax > 0.0)) return fail(WAKE_EINVAL, "rmax and ximax must be positive");
   if (p.n_beam < 0 || p.n_drive < 0 || p.n_drive > p.n_beam) return fail(WAKE_EINVAL, "need 0 <= n_drive <= n_beam");
@@ -128,27 +129,13 @@ BeamDesc beam_desc(const Sim &s, double *diag) {
   return b;
 }
 
-template <class Pol, int PPT>
-int launch_march_ppt(wake_sim *h) {
-  constexpr int NT = Pol::NT;
-  auto kern = march_kernel<Pol, NT, PPT>;
-  const size_t smem = MarchSmem<Pol>::bytes(h->max_n1);
-  CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  kern<<<h->n, NT, smem, h->stream>>>(h->d_desc, h->d_order);
-  CUDA_TRY(cudaGetLastError());
-  return WAKE_OK;
-}
-
-template <class Pol>
 int launch_march(wake_sim *h) {
-  const int ppt = (h->max_np + Pol::NT - 1) / Pol::NT;
-  if (ppt <= 1) return launch_march_ppt<Pol, 1>(h);
-  if (ppt <= 2) return launch_march_ppt<Pol, 2>(h);
-  if (ppt <= 4) return launch_march_ppt<Pol, 4>(h);
-  if (ppt <= 8) return launch_march_ppt<Pol, 8>(h);
-  if (ppt <= 16) return launch_march_ppt<Pol, 16>(h);
-  if (ppt <= 32) return launch_march_ppt<Pol, 32>(h);
-  return fail(WAKE_EINVAL, "too many plasma rings per simulation");
+  MarchLaunch L{h->d_desc, h->d_order, h->n, h->max_n1, h->max_np, h->stream};
+  int ppt = 0;
+  const cudaError_t e = h->precision == WAKE_FP64 ? launch_march_fp64(L, &ppt) : launch_march_mixed(L, &ppt);
+  if (ppt == 0) return fail(WAKE_EINVAL, "too many plasma rings per simulation");
+  if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("march launch: ") + cudaGetErrorString(e));
+  return WAKE_OK;
 }
 
 int check_handle(wake_sim *h, int sim) {
@@ -186,7 +173,8 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
     h->max_np = std::max(h->max_np, s.np);
     const size_t pb = sizeof(double) * s.np;
     if ((rc = dalloc(&s.r0, pb)) || (rc = dalloc(&s.ur0, pb)) || (rc = dalloc(&s.lz, pb)) || (rc = dalloc(&s.G0, pb)) ||
-        (rc = dalloc(&s.w, pb)) || (rc = dalloc(&s.nb, gs * s.ng)) || (rc = dalloc(&s.psi, gs * s.ng)) ||
+        (rc = dalloc(&s.w, pb)) || (ring_buf_bytes(h->precision == WAKE_FP64) > 0 && (rc = dalloc(&s.ring_buf, ring_buf_bytes(h->precision == WAKE_FP64)))) ||
+        (rc = dalloc(&s.nb, gs * s.ng)) || (rc = dalloc(&s.psi, gs * s.ng)) ||
         (rc = dalloc(&s.ez, gs * s.ng)) || (rc = dalloc(&s.er, gs * s.ng)) || (rc = dalloc(&s.bth, gs * s.ng)) ||
         (rc = dalloc(&s.status, sizeof(int))))
       break;
@@ -218,6 +206,8 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
       }
     }
   }
+  if (rc == WAKE_OK && march_smem_bytes(h->precision == WAKE_FP64, h->max_n1, h->max_np) > 227 * 1024)
+    rc = fail(WAKE_EINVAL, "nr and nr*ppc too large for one march CTA's shared memory");
   if (rc == WAKE_OK) {
     // descriptors; CTAs take the simulations largest-work first (LPT order)
     std::vector<SimDesc> desc(n_sims);
@@ -238,6 +228,7 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
       d.lz = s.lz;
       d.G0 = s.G0;
       d.w = s.w;
+      d.ring_buf = s.ring_buf;
       d.nb = s.nb;
       d.psi = s.psi;
       d.ez = s.ez;
@@ -323,7 +314,7 @@ int wake_plasma_march(wake_sim *h) {
   if (!h) return fail(WAKE_EINVAL, "null handle");
   for (auto &s : h->sims)
     if (!s.plasma) return fail(WAKE_ESTATE, "wake_plasma_march before wake_load_plasma");
-  int rc = h->precision == WAKE_FP64 ? launch_march<PolFP64>(h) : launch_march<PolMixed>(h);
+  int rc = launch_march(h);
   if (rc) return rc;
   for (auto &s : h->sims) s.marched = true;
   return WAKE_OK;

@@ -21,6 +21,7 @@ struct SimDesc {
   int nr, nxi, np, has_beam;
   double rmax, ximax, dr, dxi;
   const double *r0, *ur0, *lz, *G0, *w;  // ring constants (set by wake_load_plasma)
+  void *ring_buf;                        // ring slot arrays in global memory (FP64 form)
   const void *nb;                        // beam density n_b on the nodes
   void *psi, *ez, *er, *bth;             // march output
   int *status;

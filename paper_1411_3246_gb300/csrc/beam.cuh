@@ -3,7 +3,9 @@
 //
 // Beam state is SoA: x, y, u_x, u_y in the policy's type BT (float in the mixed form),
 // xi and u_z always in FP64 (u_z ~ gamma_b = 4e4 changes by O(1) per step and xi slips by
-// ~1e-9 per step: both are accumulated in FP64, the kicks themselves computed in BT).
+// ~1e-9 per step: both are accumulated in FP64, the kicks themselves computed in BT).  A
+// flag byte per particle holds bit 0 = lost and bit 1 = witness; orig holds the particle's
+// index in the caller's order (the beam is kept sorted by xi cell for the pipelined step).
 #pragma once
 
 #include "wake_common.cuh"
@@ -17,7 +19,8 @@ struct BeamDesc {
   double wd, ww;           // macroparticle weights of the drive and witness bunches
   void *x, *y, *ux, *uy;   // BT
   double *xi, *uz;
-  uint8_t *lost;
+  uint8_t *lost;           // flags: bit 0 lost, bit 1 witness
+  int *orig;               // index in the caller's order
   void *nb;                // beam-density grid (G)
   const void *er, *ez, *bth;  // fields of the last march (G)
   double *diag;            // 5 accumulators
@@ -42,7 +45,8 @@ __global__ void beam_init_kernel(BeamDesc b, BunchInit q, const double *__restri
     b.xi[j] = xi;
     b.uz[j] = q.gamma_b;
     const double r = sqrt(x * x + y * y);
-    b.lost[j] = !(xi >= 0.0 && xi < b.ximax && r < b.rmax);
+    b.lost[j] = (uint8_t)((xi >= 0.0 && xi < b.ximax && r < b.rmax) ? 0 : 1) | (uint8_t)(drive ? 0 : 2);
+    b.orig[j] = (int)j;
   }
 }
 
@@ -54,7 +58,8 @@ __global__ void beam_deposit_kernel(BeamDesc b) {
   const BT inv_dr = (BT)(1.0 / b.dr);
   const double inv_dxi = 1.0 / b.dxi;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
-    if (b.lost[j]) continue;
+    const uint8_t fl = b.lost[j];
+    if (fl & 1) continue;
     const BT x = ((const BT *)b.x)[j], y = ((const BT *)b.y)[j];
     const BT r = sqrt(x * x + y * y);
     int c, k;
@@ -63,7 +68,7 @@ __global__ void beam_deposit_kernel(BeamDesc b) {
     double g;
     locate(b.xi[j], inv_dxi, b.nxi, k, g);
     const BT gg = (BT)g;
-    const BT w = (BT)(j < b.n_drive ? b.wd : b.ww);
+    const BT w = (BT)((fl & 2) ? b.ww : b.wd);
     G *row = nb + (size_t)k * n1 + c;
     atomicAdd(row, (G)(w * ((BT)1 - f) * ((BT)1 - gg)));
     atomicAdd(row + 1, (G)(w * f * ((BT)1 - gg)));
@@ -97,18 +102,43 @@ __global__ void nb_analytic_kernel(G *nb, int nr, int nxi, double dr, double dxi
 }
 
 // One Boris step (Eqs. 8-11 are the Lorentz force of E = (E_r rhat, E_z), B = B_theta
-// thetahat on a charge -1): fields gathered bilinearly in (r, xi); momentum at half steps;
-// x_perp += dt u_perp/gamma; xi += dt (1 + u_perp^2)/(gamma (gamma + u_z)).  The u_z kick
-// 2 h E_z + (p x s)_z is formed in BT and added to the FP64 u_z.
+// thetahat on a charge -1) with the fields (Er, Ez, Bt) gathered at the particle: momentum at
+// half steps; x_perp += dt u_perp/gamma; xi += dt (1 + u_perp^2)/(gamma (gamma + u_z)).  The
+// u_z kick 2 h E_z + (p x s)_z is formed in BT and added to the FP64 u_z.
+template <class BT>
+__device__ __forceinline__ void boris_step(BT &x, BT &y, BT &ux, BT &uy, double &xi, double &uzd, BT r, BT Er,
+                                           BT Ez, BT Bt, BT dt) {
+  const BT h = (BT)-0.5 * dt;  // q dt / 2 with q = -1
+  const BT cs = r > (BT)0 ? x / r : (BT)0, sn = r > (BT)0 ? y / r : (BT)0;
+  const BT Ex = Er * cs, Ey = Er * sn, Bx = -Bt * sn, By = Bt * cs;
+  const BT uz = (BT)uzd;
+  const BT mx = ux + h * Ex, my = uy + h * Ey, mz = uz + h * Ez;
+  const BT gm = sqrt((BT)1 + mx * mx + my * my + mz * mz);
+  const BT tx = h * Bx / gm, ty = h * By / gm;
+  const BT px = mx - mz * ty, py = my + mz * tx, pz = mz + (mx * ty - my * tx);
+  const BT s = (BT)2 / ((BT)1 + tx * tx + ty * ty);
+  const BT sx = s * tx, sy = s * ty;
+  ux = mx - pz * sy + h * Ex;
+  uy = my + pz * sx + h * Ey;
+  uzd += (double)((BT)2 * h * Ez + (px * sy - py * sx));
+  const BT uzn = (BT)uzd;
+  const BT up2 = ux * ux + uy * uy;
+  const BT gam = sqrt((BT)1 + up2 + uzn * uzn);
+  x += dt * ux / gam;
+  y += dt * uy / gam;
+  xi += (double)(dt * ((BT)1 + up2) / (gam * (gam + uzn)));
+}
+
+// One beam step through the grid fields of the last march, bilinear gather in (r, xi).
 template <class BT, class G>
 __global__ void beam_push_kernel(BeamDesc b) {
   const G *er = (const G *)b.er, *ez = (const G *)b.ez, *bt = (const G *)b.bth;
   BT *X = (BT *)b.x, *Y = (BT *)b.y, *UX = (BT *)b.ux, *UY = (BT *)b.uy;
   const int n1 = b.nr + 1;
-  const BT inv_dr = (BT)(1.0 / b.dr), dt = (BT)b.ds, h = (BT)(-0.5 * b.ds), Rw = (BT)b.rmax;
+  const BT inv_dr = (BT)(1.0 / b.dr), dt = (BT)b.ds, Rw = (BT)b.rmax;
   const double inv_dxi = 1.0 / b.dxi;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
-    if (b.lost[j]) continue;
+    if (b.lost[j] & 1) continue;
     BT x = X[j], y = Y[j], ux = UX[j], uy = UY[j];
     double xi = b.xi[j], uzd = b.uz[j];
     const BT r = sqrt(x * x + y * y);
@@ -123,24 +153,7 @@ __global__ void beam_push_kernel(BeamDesc b) {
     const BT Er = w00 * (BT)er[i00] + w01 * (BT)er[i00 + 1] + w10 * (BT)er[i00 + n1] + w11 * (BT)er[i00 + n1 + 1];
     const BT Ez = w00 * (BT)ez[i00] + w01 * (BT)ez[i00 + 1] + w10 * (BT)ez[i00 + n1] + w11 * (BT)ez[i00 + n1 + 1];
     const BT Bt = w00 * (BT)bt[i00] + w01 * (BT)bt[i00 + 1] + w10 * (BT)bt[i00 + n1] + w11 * (BT)bt[i00 + n1 + 1];
-    const BT cs = r > (BT)0 ? x / r : (BT)0, sn = r > (BT)0 ? y / r : (BT)0;
-    const BT Ex = Er * cs, Ey = Er * sn, Bx = -Bt * sn, By = Bt * cs;
-    const BT uz = (BT)uzd;
-    const BT mx = ux + h * Ex, my = uy + h * Ey, mz = uz + h * Ez;
-    const BT gm = sqrt((BT)1 + mx * mx + my * my + mz * mz);
-    const BT tx = h * Bx / gm, ty = h * By / gm;
-    const BT px = mx - mz * ty, py = my + mz * tx, pz = mz + (mx * ty - my * tx);
-    const BT s = (BT)2 / ((BT)1 + tx * tx + ty * ty);
-    const BT sx = s * tx, sy = s * ty;
-    ux = mx - pz * sy + h * Ex;
-    uy = my + pz * sx + h * Ey;
-    uzd += (double)((BT)2 * h * Ez + (px * sy - py * sx));
-    const BT uzn = (BT)uzd;
-    const BT up2 = ux * ux + uy * uy;
-    const BT gam = sqrt((BT)1 + up2 + uzn * uzn);
-    x += dt * ux / gam;
-    y += dt * uy / gam;
-    xi += (double)(dt * ((BT)1 + up2) / (gam * (gam + uzn)));
+    boris_step<BT>(x, y, ux, uy, xi, uzd, r, Er, Ez, Bt, dt);
     X[j] = x;
     Y[j] = y;
     UX[j] = ux;
@@ -148,7 +161,7 @@ __global__ void beam_push_kernel(BeamDesc b) {
     b.xi[j] = xi;
     b.uz[j] = uzd;
     const BT rn = sqrt(x * x + y * y);
-    if (!(xi >= 0.0 && xi < b.ximax && rn < Rw)) b.lost[j] = 1;
+    if (!(xi >= 0.0 && xi < b.ximax && rn < Rw)) b.lost[j] |= 1;
   }
 }
 
@@ -158,10 +171,10 @@ __global__ void beam_diag_kernel(BeamDesc b) {
   const BT *UX = (const BT *)b.ux, *UY = (const BT *)b.uy;
   double nw = 0, sw = 0, sw2 = 0, nd = 0, sd = 0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
-    if (b.lost[j]) continue;
+    if (b.lost[j] & 1) continue;
     const double ux = UX[j], uy = UY[j], uz = b.uz[j];
     const double g = sqrt(1.0 + ux * ux + uy * uy + uz * uz) - b.gamma_b;
-    if (j >= b.n_drive) {
+    if (b.lost[j] & 2) {
       nw += 1;
       sw += g;
       sw2 += g * g;
@@ -183,7 +196,7 @@ __global__ void beam_diag_kernel(BeamDesc b) {
 // warm: ppc/2 radii, each shared by a mirrored pair of draws.  u = u_th * normals,
 // gamma0 = sqrt(1 + u^2), Gamma0 = gamma0 - u_z0, l_z = r u_theta0,
 // w = r dr/ppc * Gamma0/gamma0 (the quasi-static flux factor 1 - v_z0).
-__global__ void plasma_init_kernel(int nr, int ppc, double dr, double u_th, const double *__restrict__ nm,
+static __global__ void plasma_init_kernel(int nr, int ppc, double dr, double u_th, const double *__restrict__ nm,
                                    double *r0, double *ur0, double *lz, double *G0, double *w) {
   const int np = nr * ppc;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x) {
@@ -203,6 +216,86 @@ __global__ void plasma_init_kernel(int nr, int ppc, double dr, double u_th, cons
     lz[j] = r * ut;
     G0[j] = g0 - uz;
     w[j] = r * dr / (double)ppc * ((g0 - uz) / g0);
+  }
+}
+
+// Counting sort of the beam by xi cell (lost particles go to the extra bin nxi).
+// The cell is found exactly as the push finds it (locate with 1/dxi).
+__device__ __forceinline__ int beam_bin(const BeamDesc &b, int64_t j) {
+  if (b.lost[j] & 1) return b.nxi;
+  int k;
+  double g;
+  locate(b.xi[j], 1.0 / b.dxi, b.nxi, k, g);
+  return k;
+}
+// Largest xi slip rate dxi/dt = (1 + u_perp^2) / (gamma (gamma + u_z)) over the live beam, as
+// the bits of a non-negative double (ordered like unsigned integers) in *out (zeroed before).
+template <class BT>
+__global__ void beam_slip_kernel(BeamDesc b, unsigned long long *out) {
+  double m = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+    if (b.lost[j] & 1) continue;
+    const double ux = ((const BT *)b.ux)[j], uy = ((const BT *)b.uy)[j], uz = b.uz[j];
+    const double up2 = ux * ux + uy * uy, g = sqrt(1.0 + up2 + uz * uz);
+    m = fmax(m, (1.0 + up2) / (g * (g + uz)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+static __global__ void bin_count_kernel(BeamDesc b, int *count) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&count[beam_bin(b, j)], 1);
+}
+// exclusive scan of nbins counts into start[0..nbins] (one block of 1024 threads)
+static __global__ void bin_scan_kernel(const int *count, int *start, int *cursor, int nbins) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x, E = (nbins + 1023) / 1024, beg = t * E, end = min(nbins, beg + E);
+  int s = 0;
+  for (int q = beg; q < end; ++q) s += count[q];
+  part[t] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v = t >= o ? part[t - o] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = part[t] - s;
+  for (int q = beg; q < end; ++q) {
+    start[q] = run;
+    cursor[q] = run;
+    run += count[q];
+  }
+  if (t == 1023) start[nbins] = part[1023];
+}
+template <class BT>
+__global__ void bin_scatter_kernel(BeamDesc b, BeamDesc dst, int *cursor) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = atomicAdd(&cursor[beam_bin(b, j)], 1);
+    ((BT *)dst.x)[q] = ((const BT *)b.x)[j];
+    ((BT *)dst.y)[q] = ((const BT *)b.y)[j];
+    ((BT *)dst.ux)[q] = ((const BT *)b.ux)[j];
+    ((BT *)dst.uy)[q] = ((const BT *)b.uy)[j];
+    dst.xi[q] = b.xi[j];
+    dst.uz[q] = b.uz[j];
+    dst.lost[q] = b.lost[j];
+    dst.orig[q] = b.orig[j];
+  }
+}
+// Scatter the beam back to the caller's order: out rows x, y, xi, u_x, u_y, u_z (6 x n).
+template <class BT>
+__global__ void beam_unpermute_kernel(BeamDesc b, double *xyz, uint8_t *lost) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = b.orig[j];
+    if (xyz) {
+      xyz[0 * b.n + o] = (double)((const BT *)b.x)[j];
+      xyz[1 * b.n + o] = (double)((const BT *)b.y)[j];
+      xyz[2 * b.n + o] = b.xi[j];
+      xyz[3 * b.n + o] = (double)((const BT *)b.ux)[j];
+      xyz[4 * b.n + o] = (double)((const BT *)b.uy)[j];
+      xyz[5 * b.n + o] = b.uz[j];
+    }
+    if (lost) lost[o] = b.lost[j] & 1;
   }
 }
 

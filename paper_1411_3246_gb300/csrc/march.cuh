@@ -166,7 +166,7 @@ struct MarchSmem {
   typename Pol::W *wtot;                        // block-scan warp totals
   RingSoA<R> rings;                             // ring slots (mixed form)
 
-  static size_t bytes(int n1, int slots) {
+  __host__ __device__ static size_t bytes(int n1, int slots) {
     size_t b = sizeof(typename Pol::W) * 64 + sizeof(typename Pol::Q) * 2 * (size_t)n1 + sizeof(Acc) * 6 * (size_t)n1 + sizeof(R) * 6 * (size_t)n1 + sizeof(R) * 6 * ((size_t)n1 + 32) + 256;
     b += sizeof(R) * (Pol::kTables ? 6 : 2) * (size_t)n1;
     if (Pol::kSortEvery > 0) b += sizeof(int) * ((size_t)n1 + 32);
@@ -864,13 +864,17 @@ __device__ __forceinline__ void resort_rings(MarchSmem<Pol> &sm, const RingSoA<t
   __syncthreads();
 }
 
-template <class Pol, int NT, int PPT>
-__global__ void __launch_bounds__(NT, 1) march_kernel(const SimDesc *descs, const int *order) {
+// The march of one simulation by one CTA.  Hooks supply the beam-density rows and receive
+// each slice's fields (see PlainHooks; the pipelined beam step adds its own):
+//   bool wait_rows(int k)           rows k, k+1 may be read (false: give up, block-uniform)
+//   R    nb_row(int row, int m)     beam density at node m of a row
+//   void slice_done(int k, sm)      stage-1 fields of slice k are in sm (psi, dpsi, ez, bth)
+//   void finish(sm)                 after the last slice
+template <class Pol, int NT, int PPT, class Hooks>
+__device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem_raw, Hooks &hk) {
   using R = typename Pol::R;
   using G = typename Pol::G;
   using Acc = typename Pol::Acc;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const SimDesc &d = descs[order ? order[blockIdx.x] : blockIdx.x];
   const int tid = threadIdx.x, nr = d.nr, n1 = nr + 1, np = d.np, nxi = d.nxi;
   constexpr int SLOTS = NT * PPT;
   MarchSmem<Pol> sm;
@@ -884,12 +888,8 @@ __global__ void __launch_bounds__(NT, 1) march_kernel(const SimDesc *descs, cons
   const R h = (R)d.dxi, R_wall = (R)d.rmax, dR = (R)drd, inv_dr = (R)(1.0 / drd);
   const NodeGeo<Pol> geo{sm.invR, sm.invV, sm.alpha, sm.ga, sm.gb, sm.gc, nr, dR, inv_dr, (R)(1.0 / (drd * drd)),
                           (R)(drd / 6.0), (R)(1.0 / (0.5 * nr - 1.0 / 6.0))};
-  const G *nb = (const G *)d.nb;
-  G *opsi = (G *)d.psi, *oez = (G *)d.ez, *oer = (G *)d.er, *obth = (G *)d.bth;
-
   fill_tables<Pol, NT>(sm, nr, drd);
   for (int m = tid; m < n1; m += NT) {
-    sm.nb0[m] = (R)nb[m];
     sm.rho[m] = (typename Pol::Q)0;
     sm.jz[m] = sm.chi[m] = sm.T[m] = sm.P[m] = sm.U[m] = sm.K[m] = (Acc)0;
   }
@@ -957,13 +957,15 @@ __global__ void __launch_bounds__(NT, 1) march_kernel(const SimDesc *descs, cons
   for (int k = 0; k <= nxi; ++k) {
     if (Pol::kSortEvery > 0 && k > 0 && k % Pol::kSortEvery == 0) resort_rings<Pol, NT, PPT>(sm, rs, np, nr);
     const R *nbk = (k & 1) ? sm.nb1 : sm.nb0, *nbk1 = (k & 1) ? sm.nb0 : sm.nb1;
+    if (!hk.wait_rows(k)) break;
+    if (k == 0)  // row 0 is first read in P2, after two barriers
+      for (int m = tid; m < n1; m += NT) sm.nb0[m] = hk.nb_row(0, m);
     // prefetch beam-density row k+1 (stored in phase P1); n1 <= 3 NT
     R pre[3] = {(R)0, (R)0, (R)0};
     if (k < nxi) {
-      const G *row = nb + (size_t)(k + 1) * n1;
 #pragma unroll
       for (int q = 0; q < 3; ++q)
-        if (tid + q * NT < n1) pre[q] = (R)row[tid + q * NT];
+        if (tid + q * NT < n1) pre[q] = hk.nb_row(k + 1, tid + q * NT);
     }
     // ======== stage 1 at xi_k ========
     solve_psi<Pol, NT>(sm, geo, sm.wtot);  // P0
@@ -988,18 +990,8 @@ __global__ void __launch_bounds__(NT, 1) march_kernel(const SimDesc *descs, cons
     __syncthreads();
     solve_fields<Pol, NT>(sm, geo, nbk, nbk, sm.wtot);  // P2
     __syncthreads();
-    {  // P3: fields of slice k, then the move to the midpoint and its charge deposit
-      G *o1 = opsi + (size_t)k * n1, *o2 = oez + (size_t)k * n1, *o3 = oer + (size_t)k * n1,
-        *o4 = obth + (size_t)k * n1;
-      for (int m = tid; m < n1; m += NT) {
-        const R ps = sm.psi[m], e = sm.ez[m], b = sm.bth[m];
-        if (!(isfinite(ps) && isfinite(e) && isfinite(b))) flag(d.status, ST_NUMERIC);
-        o1[m] = (G)ps;
-        o2[m] = (G)e;
-        o3[m] = m > 0 ? (G)(b - sm.dpsi[m]) : (G)0;
-        o4[m] = (G)b;
-      }
-    }
+    // P3: fields of slice k, then the move to the midpoint and its charge deposit
+    hk.slice_done(k, sm);
     if (k == nxi) break;
     for (int i = tid; i < n1; i += NT) sm.jz[i] = sm.chi[i] = sm.T[i] = sm.P[i] = sm.U[i] = sm.K[i] = (Acc)0;
     {
@@ -1076,6 +1068,41 @@ __global__ void __launch_bounds__(NT, 1) march_kernel(const SimDesc *descs, cons
     }
     __syncthreads();
   }
+  hk.finish(sm);
+}
+
+// Plain march: beam density from the simulation's grid, fields to its output grids.
+template <class Pol, int NT>
+struct PlainHooks {
+  using R = typename Pol::R;
+  using G = typename Pol::G;
+  const G *nb;
+  G *opsi, *oez, *oer, *obth;
+  int n1;
+  int *status;
+  __device__ __forceinline__ bool wait_rows(int) { return true; }
+  __device__ __forceinline__ R nb_row(int row, int m) const { return (R)nb[(size_t)row * n1 + m]; }
+  __device__ __forceinline__ void slice_done(int k, MarchSmem<Pol> &sm) {
+    G *o1 = opsi + (size_t)k * n1, *o2 = oez + (size_t)k * n1, *o3 = oer + (size_t)k * n1, *o4 = obth + (size_t)k * n1;
+    for (int m = threadIdx.x; m < n1; m += NT) {
+      const R ps = sm.psi[m], e = sm.ez[m], b = sm.bth[m];
+      if (!(isfinite(ps) && isfinite(e) && isfinite(b))) flag(status, ST_NUMERIC);
+      o1[m] = (G)ps;
+      o2[m] = (G)e;
+      o3[m] = m > 0 ? (G)(b - sm.dpsi[m]) : (G)0;
+      o4[m] = (G)b;
+    }
+  }
+  __device__ __forceinline__ void finish(MarchSmem<Pol> &) {}
+};
+
+template <class Pol, int NT, int PPT>
+__global__ void __launch_bounds__(NT, 1) march_kernel(const SimDesc *descs, const int *order) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SimDesc &d = descs[order ? order[blockIdx.x] : blockIdx.x];
+  PlainHooks<Pol, NT> hk{(const typename Pol::G *)d.nb, (typename Pol::G *)d.psi, (typename Pol::G *)d.ez,
+                         (typename Pol::G *)d.er, (typename Pol::G *)d.bth, d.nr + 1, d.status};
+  march_body<Pol, NT, PPT>(d, smem_raw, hk);
 }
 
 }  // namespace wake

@@ -1,5 +1,6 @@
 // Mixed form of the xi-march: FP32 ring and node arithmetic, float-float scans.
 #include "march.cuh"
+#include "pipeline.cuh"
 #include "march_launch.h"
 
 namespace wake {
@@ -24,6 +25,65 @@ cudaError_t launch_march_mixed(const MarchLaunch &L, int *ppt_out) {
     case 8: return go<8>(L);
     case 16: return go<16>(L);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+
+template <int PPT>
+static cudaError_t go_step(const PipeArgs &a, int ctas, cudaStream_t stream) {
+  auto kern = step_kernel<PolMixed, PolMixed::NT, PPT>;
+  const size_t smem = step_smem_bytes<PolMixed, PolMixed::NT, PPT>(a.d.nr + 1);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  PipeArgs arg = a;
+  void *args[] = {&arg};
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(ctas), dim3(PolMixed::NT), args, smem, stream);
+}
+template <int PPT>
+static int ctas_step(int n1) {
+  auto kern = step_kernel<PolMixed, PolMixed::NT, PPT>;
+  const size_t smem = step_smem_bytes<PolMixed, PolMixed::NT, PPT>(n1);
+  if (smem > 227 * 1024) return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, PolMixed::NT, smem) != cudaSuccess) return 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * sms;
+}
+static int ppt_for(int np) {
+  const int ppt = (np + PolMixed::NT - 1) / PolMixed::NT;
+  return ppt <= 1 ? 1 : ppt <= 2 ? 2 : ppt <= 4 ? 4 : ppt <= 8 ? 8 : ppt <= 16 ? 16 : 0;
+}
+static size_t step_bytes_for(int n1, int np) {
+  switch (ppt_for(np)) {
+    case 1: return step_smem_bytes<PolMixed, PolMixed::NT, 1>(n1);
+    case 2: return step_smem_bytes<PolMixed, PolMixed::NT, 2>(n1);
+    case 4: return step_smem_bytes<PolMixed, PolMixed::NT, 4>(n1);
+    case 8: return step_smem_bytes<PolMixed, PolMixed::NT, 8>(n1);
+    case 16: return step_smem_bytes<PolMixed, PolMixed::NT, 16>(n1);
+    default: return (size_t)1 << 40;
+  }
+}
+cudaError_t launch_step_mixed(const PipeArgs &a, int np, int ctas, cudaStream_t stream) {
+  switch (ppt_for(np)) {
+    case 1: return go_step<1>(a, ctas, stream);
+    case 2: return go_step<2>(a, ctas, stream);
+    case 4: return go_step<4>(a, ctas, stream);
+    case 8: return go_step<8>(a, ctas, stream);
+    case 16: return go_step<16>(a, ctas, stream);
+    default: return cudaErrorInvalidValue;
+  }
+}
+int step_ctas_mixed(int n1, int np) {
+  if (step_bytes_for(n1, np) > 227 * 1024) return 0;
+  switch (ppt_for(np)) {
+    case 1: return ctas_step<1>(n1);
+    case 2: return ctas_step<2>(n1);
+    case 4: return ctas_step<4>(n1);
+    case 8: return ctas_step<8>(n1);
+    case 16: return ctas_step<16>(n1);
+    default: return 0;
   }
 }
 

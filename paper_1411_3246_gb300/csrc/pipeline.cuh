@@ -1,0 +1,215 @@
+// Pipelined beam steps.  A beam step is deposit -> xi-march -> push (Sec. II.A, last
+// paragraph); consecutive steps are sequential, but the march of step t+1 at slice k only
+// needs the beam density of rows <= k+1, i.e. the beam particles of the xi cells <= k+1 pushed
+// by step t.  Beam particles slip back in xi by dt (1 - v_z) ~ 1e-9 per step (gamma = 4e4), so
+// a particle stays in its cell or moves to the next one.  One persistent cooperative launch
+// therefore runs many steps at once, one CTA per SM, each CTA marching its own step a few
+// slices behind the previous step's CTA:
+//   - step t's CTA keeps the fields of its last four slices in shared memory; once slice k is
+//     solved it pushes the beam particles sorted into cell b = k - 2 (their fields lie in
+//     slices b .. b+2) and deposits them straight into the beam-density grid of step t+1;
+//   - it then publishes progress[t] = b + 1 (release); step t+1's CTA waits (acquire, bounded)
+//     for progress[t] >= k + 2 before it reads rows <= k + 1 of its grid.
+// Every step has its own density grid (zeroed before the launch), so no grid is reused within
+// a launch.  A wait that exceeds its bound sets ST_TIMEOUT and the CTA leaves cleanly; a
+// particle found more than one cell from its sorted cell sets ST_DRIFT.
+#pragma once
+
+#include "beam.cuh"
+#include "march.cuh"
+
+namespace wake {
+
+constexpr int ST_DRIFT = 8;
+
+struct PipeArgs {
+  SimDesc d;              // the simulation (plasma, output grids, status)
+  void *grids;            // nsteps + 1 beam-density grids (G), grid t at t * ng
+  size_t ng;              // nodes per grid
+  int *progress;          // nsteps counters: sorted cells pushed by step t
+  int nsteps;
+  int write_last;         // write the last step's fields to the output grids
+  // beam (sorted by xi cell; cell b holds particles bin_start[b] .. bin_start[b+1]-1)
+  void *x, *y, *ux, *uy;
+  double *xi, *uz;
+  uint8_t *flags;
+  const int *bin_start;
+  double wd, ww, ds;
+  long long spin_limit;   // polls before a wait gives up
+  void *ring_bufs;        // per-CTA ring slot storage (FP64 form)
+  size_t ring_stride;
+};
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <class Pol, int NT>
+struct PipeHooks {
+  using R = typename Pol::R;
+  using G = typename Pol::G;
+  using BT = R;
+  const PipeArgs &a;
+  int t;          // step within the launch
+  R *win;         // 4 slices x (E_r, E_z, B_theta) x n1
+  int *ctl;       // [0] abort flag, [1] progress seen of step t-1
+  int n1, nr, nxi;
+  double dr, dxi, rmax, ximax;
+
+  __device__ __forceinline__ const G *grid(int s) const { return (const G *)a.grids + (size_t)s * a.ng; }
+
+  // rows <= k+1 of this step's grid are final once progress[t-1] >= min(nxi, k + 2).  Thread 0
+  // polls (bounded; it also gives up as soon as another CTA has timed out), every thread then
+  // meets at one barrier, so the decision is uniform.
+  __device__ __forceinline__ bool wait_rows(int k) {
+    if (t == 0) return true;
+    const int need = min(nxi, k + 2);
+    if (threadIdx.x == 0 && ctl[1] < need) {
+      long long it = 0;
+      int v = ld_acquire(&a.progress[t - 1]);
+      while (v < need) {
+        if (++it > a.spin_limit || (*(volatile int *)a.d.status & ST_TIMEOUT)) {
+          flag(a.d.status, ST_TIMEOUT);
+          ctl[0] = 1;
+          break;
+        }
+        __nanosleep(128);
+        v = ld_acquire(&a.progress[t - 1]);
+      }
+      ctl[1] = v;
+    }
+    __syncthreads();
+    return ctl[0] == 0;
+  }
+  __device__ __forceinline__ R nb_row(int row, int m) const { return (R)__ldcg(grid(t) + (size_t)row * n1 + m); }
+
+  __device__ __forceinline__ void slice_done(int k, MarchSmem<Pol> &sm) {
+    R *w = win + (size_t)(k & 3) * 3 * n1;
+    const bool out = a.write_last && t == a.nsteps - 1;
+    G *o1 = (G *)a.d.psi + (size_t)k * n1, *o2 = (G *)a.d.ez + (size_t)k * n1, *o3 = (G *)a.d.er + (size_t)k * n1,
+      *o4 = (G *)a.d.bth + (size_t)k * n1;
+    for (int m = threadIdx.x; m < n1; m += NT) {
+      const R ps = sm.psi[m], e = sm.ez[m], b = sm.bth[m];
+      if (!(isfinite(ps) && isfinite(e) && isfinite(b))) flag(a.d.status, ST_NUMERIC);
+      const R er = m > 0 ? b - sm.dpsi[m] : (R)0;
+      w[m] = er;
+      w[n1 + m] = e;
+      w[2 * n1 + m] = b;
+      if (out) {
+        o1[m] = (G)ps;
+        o2[m] = (G)e;
+        o3[m] = (G)er;
+        o4[m] = (G)b;
+      }
+    }
+    __syncthreads();
+    if (k >= 2) push_cell(k - 2);
+  }
+  __device__ __forceinline__ void finish(MarchSmem<Pol> &) {
+    if (ctl[0] == 0 && nxi >= 1) push_cell(nxi - 1);
+  }
+
+  // Push the beam particles sorted into cell b (fields of slices b .. b+2 are in the window)
+  // and deposit them into the grid of step t+1; then publish progress[t] = b + 1.
+  __device__ void push_cell(int b) {
+    BT *X = (BT *)a.x, *Y = (BT *)a.y, *UX = (BT *)a.ux, *UY = (BT *)a.uy;
+    G *nbn = (G *)a.grids + (size_t)(t + 1) * a.ng;
+    const BT inv_dr = (BT)(1.0 / dr), dt = (BT)a.ds, Rw = (BT)rmax;
+    const double inv_dxi = 1.0 / dxi;
+    const int beg = a.bin_start[b], end = a.bin_start[b + 1];
+    for (int j = beg + threadIdx.x; j < end; j += NT) {
+      uint8_t fl = __ldcg(a.flags + j);
+      if (fl & 1) continue;
+      BT x = __ldcg(X + j), y = __ldcg(Y + j), ux = __ldcg(UX + j), uy = __ldcg(UY + j);
+      double xi = __ldcg(a.xi + j), uzd = __ldcg(a.uz + j);
+      int kk;
+      double gd;
+      locate(xi, inv_dxi, nxi, kk, gd);
+      if (kk != b && kk != b + 1) {  // drifted beyond the cell the fields are ready for
+        flag(a.d.status, ST_DRIFT);
+        continue;
+      }
+      const BT r = sqrt(x * x + y * y);
+      int c;
+      BT f;
+      locate(r, inv_dr, nr, c, f);
+      const BT g = (BT)gd;
+      const R *w0 = win + (size_t)(kk & 3) * 3 * n1, *w1 = win + (size_t)((kk + 1) & 3) * 3 * n1;
+      const BT a00 = ((BT)1 - f) * ((BT)1 - g), a01 = f * ((BT)1 - g), a10 = ((BT)1 - f) * g, a11 = f * g;
+      const BT Er = a00 * w0[c] + a01 * w0[c + 1] + a10 * w1[c] + a11 * w1[c + 1];
+      const BT Ez = a00 * w0[n1 + c] + a01 * w0[n1 + c + 1] + a10 * w1[n1 + c] + a11 * w1[n1 + c + 1];
+      const BT Bt = a00 * w0[2 * n1 + c] + a01 * w0[2 * n1 + c + 1] + a10 * w1[2 * n1 + c] + a11 * w1[2 * n1 + c + 1];
+      boris_step<BT>(x, y, ux, uy, xi, uzd, r, Er, Ez, Bt, dt);
+      X[j] = x;
+      Y[j] = y;
+      UX[j] = ux;
+      UY[j] = uy;
+      a.xi[j] = xi;
+      a.uz[j] = uzd;
+      const BT rn = sqrt(x * x + y * y);
+      if (!(xi >= 0.0 && xi < ximax && rn < Rw)) {
+        a.flags[j] = fl | 1;
+        continue;
+      }
+      // deposit into the next step's grid: bilinear hats over the hat volumes
+      int c2, k2;
+      BT f2;
+      double g2d;
+      locate(rn, inv_dr, nr, c2, f2);
+      locate(xi, inv_dxi, nxi, k2, g2d);
+      const BT g2 = (BT)g2d;
+      // weight over the hat volumes: V_i = i dr^2 (dr^2/6 on the axis, dr^2 (nr/2 - 1/6) at the
+      // wall) in r, dxi (dxi/2 at the two end slices) in xi
+      const BT wq = (BT)((fl & 2) ? a.ww : a.wd) * (BT)(1.0 / (dr * dr * dxi));
+      auto iv = [&](int i) -> BT {
+        return i == 0 ? (BT)6 : (i == nr ? (BT)1 / ((BT)nr * (BT)0.5 - (BT)(1.0 / 6.0)) : (BT)1 / (BT)i);
+      };
+      const BT ix0 = k2 == 0 ? (BT)2 : (BT)1, ix1 = k2 + 1 == nxi ? (BT)2 : (BT)1;
+      const BT v0 = iv(c2), v1 = iv(c2 + 1);
+      const BT s00 = wq * v0 * ix0, s01 = wq * v1 * ix0, s10 = wq * v0 * ix1, s11 = wq * v1 * ix1;
+      G *row = nbn + (size_t)k2 * n1 + c2;
+      atomicAdd(row, (G)(s00 * ((BT)1 - f2) * ((BT)1 - g2)));
+      atomicAdd(row + 1, (G)(s01 * f2 * ((BT)1 - g2)));
+      atomicAdd(row + n1, (G)(s10 * ((BT)1 - f2) * g2));
+      atomicAdd(row + n1 + 1, (G)(s11 * f2 * g2));
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(&a.progress[t], b + 1);
+  }
+};
+
+template <class Pol, int NT, int PPT>
+__global__ void __launch_bounds__(NT, 1) step_kernel(PipeArgs a) {
+  using R = typename Pol::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n1 = a.d.nr + 1;
+  const size_t base = (MarchSmem<Pol>::bytes(n1, NT * PPT) + 63) & ~(size_t)63;
+  R *win = (R *)(smem_raw + base);
+  int *ctl = (int *)(win + (size_t)12 * n1);
+  for (int t = blockIdx.x; t < a.nsteps; t += gridDim.x) {
+    if (threadIdx.x == 0) {
+      ctl[0] = 0;
+      ctl[1] = 0;
+    }
+    __syncthreads();
+    PipeHooks<Pol, NT> hk{a, t, win, ctl, n1, a.d.nr, a.d.nxi, a.d.dr, a.d.dxi, a.d.rmax, a.d.ximax};
+    SimDesc d = a.d;
+    if (!Pol::kSmemRings) d.ring_buf = (unsigned char *)a.ring_bufs + (size_t)blockIdx.x * a.ring_stride;
+    march_body<Pol, NT, PPT>(d, smem_raw, hk);
+    __syncthreads();
+    if (ctl[0]) break;
+  }
+}
+
+template <class Pol, int NT, int PPT>
+size_t step_smem_bytes(int n1) {
+  return ((MarchSmem<Pol>::bytes(n1, NT * PPT) + 63) & ~(size_t)63) + sizeof(typename Pol::R) * 12 * (size_t)n1 + 64;
+}
+
+}  // namespace wake

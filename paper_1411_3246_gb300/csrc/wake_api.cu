@@ -12,6 +12,7 @@
 #include "../../include/wake.h"
 #include "beam.cuh"
 #include "march_launch.h"
+#include "pipeline.cuh"
 
 using namespace wake;
 
@@ -39,7 +40,20 @@ struct Sim {
   void *nb = nullptr, *psi = nullptr, *ez = nullptr, *er = nullptr, *bth = nullptr;
   void *bx = nullptr, *by = nullptr, *bux = nullptr, *buy = nullptr;
   double *bxi = nullptr, *buz = nullptr;
-  uint8_t *blost = nullptr;
+  uint8_t *blost = nullptr;  // flags: bit 0 lost, bit 1 witness
+  int *orig = nullptr;       // index of each particle in the caller's order
+  // second copy of the beam for the re-sort by xi cell, and the cell table
+  void *bx2 = nullptr, *by2 = nullptr, *bux2 = nullptr, *buy2 = nullptr;
+  double *bxi2 = nullptr, *buz2 = nullptr;
+  uint8_t *blost2 = nullptr;
+  int *orig2 = nullptr, *bin_count = nullptr, *bin_start = nullptr, *bin_cursor = nullptr;
+  unsigned long long *slip = nullptr;  // largest xi slip rate of the beam (double bits)
+  // pipelined steps: per-step beam-density grids, progress counters, per-CTA ring storage
+  void *pgrids = nullptr;
+  int pgrid_cap = 0;
+  int *progress = nullptr;
+  void *pring = nullptr;
+  size_t pring_bytes = 0;
   int *status = nullptr;
   bool plasma = false, beam = false, marched = false;
 };
@@ -67,7 +81,8 @@ namespace {
 
 void free_sim(Sim &s) {
   void *ptrs[] = {s.r0, s.ur0, s.lz, s.G0, s.w, s.ring_buf, s.nb, s.psi, s.ez, s.er, s.bth, s.bx, s.by, s.bux, s.buy,
-                  s.bxi, s.buz, s.blost, s.status};
+                  s.bxi, s.buz, s.blost, s.status, s.orig, s.bx2, s.by2, s.bux2, s.buy2, s.bxi2, s.buz2, s.blost2,
+                  s.orig2, s.bin_count, s.bin_start, s.bin_cursor, s.slip, s.pgrids, s.progress, s.pring};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   s = Sim();
@@ -121,6 +136,7 @@ BeamDesc beam_desc(const Sim &s, double *diag) {
   b.xi = s.bxi;
   b.uz = s.buz;
   b.lost = s.blost;
+  b.orig = s.orig;
   b.nb = s.nb;
   b.er = s.er;
   b.ez = s.ez;
@@ -184,9 +200,17 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
     }
     if (p[i].n_beam > 0) {
       const size_t bt = gsize(h->precision) * p[i].n_beam;
+      const size_t nbm = (size_t)p[i].n_beam;
       if ((rc = dalloc(&s.bx, bt)) || (rc = dalloc(&s.by, bt)) || (rc = dalloc(&s.bux, bt)) || (rc = dalloc(&s.buy, bt)) ||
-          (rc = dalloc(&s.bxi, sizeof(double) * p[i].n_beam)) || (rc = dalloc(&s.buz, sizeof(double) * p[i].n_beam)) ||
-          (rc = dalloc(&s.blost, p[i].n_beam)))
+          (rc = dalloc(&s.bxi, sizeof(double) * nbm)) || (rc = dalloc(&s.buz, sizeof(double) * nbm)) ||
+          (rc = dalloc(&s.blost, nbm)) || (rc = dalloc(&s.orig, sizeof(int) * nbm)) || (rc = dalloc(&s.bx2, bt)) ||
+          (rc = dalloc(&s.by2, bt)) || (rc = dalloc(&s.bux2, bt)) || (rc = dalloc(&s.buy2, bt)) ||
+          (rc = dalloc(&s.bxi2, sizeof(double) * nbm)) || (rc = dalloc(&s.buz2, sizeof(double) * nbm)) ||
+          (rc = dalloc(&s.blost2, nbm)) || (rc = dalloc(&s.orig2, sizeof(int) * nbm)) ||
+          (rc = dalloc(&s.bin_count, sizeof(int) * (p[i].nxi + 2))) ||
+          (rc = dalloc(&s.bin_start, sizeof(int) * (p[i].nxi + 2))) ||
+          (rc = dalloc(&s.bin_cursor, sizeof(int) * (p[i].nxi + 2))) ||
+          (rc = dalloc(&s.slip, sizeof(unsigned long long))))
         break;
     } else {
       // frozen analytic driver (Eq. 12) on the nodes
@@ -337,13 +361,189 @@ int wake_beam_push(wake_sim *h) {
   return WAKE_OK;
 }
 
-int wake_step(wake_sim *h, int nsteps) {
-  if (!h || nsteps < 0) return fail(WAKE_EINVAL, "wake_step: null handle or nsteps < 0");
+namespace {
+
+// Sort the beam of simulation s by xi cell (lost particles last) into the second copy and
+// swap the copies; bin_start then gives the range of each cell.
+int sort_beam(wake_sim *h, Sim &s) {
+  BeamDesc b = beam_desc(s, nullptr);
+  BeamDesc d = b;
+  d.x = s.bx2;
+  d.y = s.by2;
+  d.ux = s.bux2;
+  d.uy = s.buy2;
+  d.xi = s.bxi2;
+  d.uz = s.buz2;
+  d.lost = s.blost2;
+  d.orig = s.orig2;
+  const int nbins = s.p.nxi + 1;
+  CUDA_TRY(cudaMemsetAsync(s.bin_count, 0, sizeof(int) * (nbins + 1), h->stream));
+  const int blocks = grid_blocks(s.p.n_beam, 256);
+  bin_count_kernel<<<blocks, 256, 0, h->stream>>>(b, s.bin_count);
+  bin_scan_kernel<<<1, 1024, 0, h->stream>>>(s.bin_count, s.bin_start, s.bin_cursor, nbins);
+  if (h->precision == WAKE_FP64)
+    bin_scatter_kernel<double><<<blocks, 256, 0, h->stream>>>(b, d, s.bin_cursor);
+  else
+    bin_scatter_kernel<float><<<blocks, 256, 0, h->stream>>>(b, d, s.bin_cursor);
+  CUDA_TRY(cudaGetLastError());
+  std::swap(s.bx, s.bx2);
+  std::swap(s.by, s.by2);
+  std::swap(s.bux, s.bux2);
+  std::swap(s.buy, s.buy2);
+  std::swap(s.bxi, s.bxi2);
+  std::swap(s.buz, s.buz2);
+  std::swap(s.blost, s.blost2);
+  std::swap(s.orig, s.orig2);
+  return WAKE_OK;
+}
+
+// Steps one pipelined launch may run: every beam particle must stay within one xi cell of
+// the cell it was sorted into (pipeline.cuh), so the launch is kept to a quarter cell of slip
+// at the beam's present largest slip rate.  Synchronises the stream.
+int slip_bound_steps(wake_sim *h, Sim &s, long long *out) {
+  BeamDesc b = beam_desc(s, nullptr);
+  CUDA_TRY(cudaMemsetAsync(s.slip, 0, sizeof(unsigned long long), h->stream));
+  const int blocks = grid_blocks(s.p.n_beam, 256);
+  if (h->precision == WAKE_FP64)
+    beam_slip_kernel<double><<<blocks, 256, 0, h->stream>>>(b, s.slip);
+  else
+    beam_slip_kernel<float><<<blocks, 256, 0, h->stream>>>(b, s.slip);
+  CUDA_TRY(cudaGetLastError());
+  unsigned long long bits = 0;
+  CUDA_TRY(cudaMemcpyAsync(&bits, s.slip, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  double rate;
+  std::memcpy(&rate, &bits, sizeof(rate));
+  const double lim = rate > 0.0 ? 0.25 * (s.p.ximax / s.p.nxi) / (s.p.ds * rate) : 1e18;
+  *out = (long long)std::min(1e18, std::floor(lim));
+  return WAKE_OK;
+}
+
+int step_sequential(wake_sim *h, int nsteps) {
   for (int t = 0; t < nsteps; ++t) {
     int rc;
     if ((rc = wake_beam_deposit(h)) || (rc = wake_plasma_march(h)) || (rc = wake_beam_push(h))) return rc;
   }
   return WAKE_OK;
+}
+
+// nsteps beam steps of a single simulation as pipelined cooperative launches (pipeline.cuh).
+// Per launch: sort the beam by xi cell, deposit the first step's density into grid 0, zero
+// the grids of the later steps and the progress counters, launch.
+int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
+  Sim &s = h->sims[0];
+  const int fp64 = h->precision == WAKE_FP64;
+  const size_t gs = gsize(h->precision), gbytes = gs * s.ng;
+  // every step of a launch owns a density grid; keep them within ~2 GB
+  const int chmax = (int)std::min<size_t>(1024, std::max<size_t>(1, ((size_t)2 << 30) / gbytes - 1));
+  const size_t rb = ring_buf_bytes(fp64);
+  int rc, done = 0, last_ch = 0;
+  while (done < nsteps) {
+    long long lim = 0;
+    if ((rc = slip_bound_steps(h, s, &lim))) return rc;
+    if (lim < 4) return step_sequential(h, nsteps - done);  // a beam slipping this fast: one step at a time
+    const int ch = (int)std::min<long long>(std::min(nsteps - done, chmax), lim);
+    if (s.pgrid_cap < ch + 1) {
+      if (s.pgrids) cudaFree(s.pgrids);
+      if (s.progress) cudaFree(s.progress);
+      s.pgrids = nullptr;
+      s.progress = nullptr;
+      s.pgrid_cap = 0;
+      const int cap = std::min(nsteps, chmax);
+      if ((rc = dalloc(&s.pgrids, gbytes * (cap + 1))) || (rc = dalloc(&s.progress, sizeof(int) * cap))) return rc;
+      s.pgrid_cap = cap + 1;
+    }
+    const int ctas = std::min(ch, ctas_max);
+    if (rb > 0 && s.pring_bytes < rb * ctas) {
+      if (s.pring) cudaFree(s.pring);
+      s.pring = nullptr;
+      s.pring_bytes = 0;
+      if ((rc = dalloc(&s.pring, rb * ctas))) return rc;
+      s.pring_bytes = rb * ctas;
+    }
+    if ((rc = sort_beam(h, s))) return rc;
+    const BeamDesc bd = beam_desc(s, nullptr);
+    {  // beam density of the launch's first step
+      BeamDesc b = bd;
+      b.nb = s.pgrids;
+      CUDA_TRY(cudaMemsetAsync(s.pgrids, 0, gbytes, h->stream));
+      const int nbk = grid_blocks(s.p.n_beam, 256), ngk = grid_blocks((int64_t)s.ng, 256);
+      if (fp64) {
+        beam_deposit_kernel<double, double><<<nbk, 256, 0, h->stream>>>(b);
+        nb_normalize_kernel<double><<<ngk, 256, 0, h->stream>>>((double *)s.pgrids, s.p.nr, s.p.nxi, b.dr, b.dxi);
+      } else {
+        beam_deposit_kernel<float, float><<<nbk, 256, 0, h->stream>>>(b);
+        nb_normalize_kernel<float><<<ngk, 256, 0, h->stream>>>((float *)s.pgrids, s.p.nr, s.p.nxi, b.dr, b.dxi);
+      }
+      CUDA_TRY(cudaGetLastError());
+    }
+    CUDA_TRY(cudaMemsetAsync((char *)s.pgrids + gbytes, 0, gbytes * ch, h->stream));
+    CUDA_TRY(cudaMemsetAsync(s.progress, 0, sizeof(int) * ch, h->stream));
+    PipeArgs a{};
+    SimDesc &d = a.d;
+    d.nr = s.p.nr;
+    d.nxi = s.p.nxi;
+    d.np = s.np;
+    d.has_beam = 1;
+    d.rmax = s.p.rmax;
+    d.ximax = s.p.ximax;
+    d.dr = s.p.rmax / s.p.nr;
+    d.dxi = s.p.ximax / s.p.nxi;
+    d.r0 = s.r0;
+    d.ur0 = s.ur0;
+    d.lz = s.lz;
+    d.G0 = s.G0;
+    d.w = s.w;
+    d.ring_buf = s.ring_buf;
+    d.nb = nullptr;
+    d.psi = s.psi;
+    d.ez = s.ez;
+    d.er = s.er;
+    d.bth = s.bth;
+    d.status = s.status;
+    a.grids = s.pgrids;
+    a.ng = s.ng;
+    a.progress = s.progress;
+    a.nsteps = ch;
+    a.write_last = 1;
+    a.x = bd.x;
+    a.y = bd.y;
+    a.ux = bd.ux;
+    a.uy = bd.uy;
+    a.xi = bd.xi;
+    a.uz = bd.uz;
+    a.flags = bd.lost;
+    a.bin_start = s.bin_start;
+    a.wd = bd.wd;
+    a.ww = bd.ww;
+    a.ds = s.p.ds;
+    a.spin_limit = 1LL << 24;  // polls of >= 128 ns: a wait gives up after seconds
+    a.ring_bufs = s.pring;
+    a.ring_stride = rb;
+    const cudaError_t e = launch_step(fp64, a, s.np, ctas, h->stream);
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("pipelined step launch: ") + cudaGetErrorString(e));
+    done += ch;
+    last_ch = ch;
+    // the density the launch's last march used
+    CUDA_TRY(cudaMemcpyAsync(s.nb, (char *)s.pgrids + gbytes * (last_ch - 1), gbytes, cudaMemcpyDeviceToDevice,
+                             h->stream));
+    s.marched = true;
+  }
+  return WAKE_OK;
+}
+
+}  // namespace
+
+int wake_step(wake_sim *h, int nsteps) {
+  if (!h || nsteps < 0) return fail(WAKE_EINVAL, "wake_step: null handle or nsteps < 0");
+  if (nsteps == 0) return WAKE_OK;
+  if (h->n == 1 && h->sims[0].p.n_beam > 0) {
+    Sim &s = h->sims[0];
+    if (!s.beam || !s.plasma) return fail(WAKE_ESTATE, "wake_step needs wake_load_plasma and wake_load_beam");
+    const int ctas = step_max_ctas(h->precision == WAKE_FP64, s.p.nr + 1, s.np);
+    if (ctas > 0) return step_pipelined(h, nsteps, ctas);
+  }
+  return step_sequential(h, nsteps);
 }
 
 int wake_get_fields(wake_sim *h, int sim, double *psi, double *ez, double *er, double *bth) {
@@ -385,21 +585,13 @@ int wake_get_beam(wake_sim *h, int sim, double *xyz, uint8_t *lost) {
   Sim &s = h->sims[sim];
   if (!s.beam) return fail(WAKE_ESTATE, "wake_get_beam before wake_load_beam");
   const int64_t n = s.p.n_beam;
-  if (xyz) {
-    void *src[4] = {s.bx, s.by, s.bux, s.buy};
-    const int row[4] = {0, 1, 3, 4};
-    for (int q = 0; q < 4; ++q) {
-      if (h->precision == WAKE_FP64) {
-        CUDA_TRY(cudaMemcpyAsync(xyz + row[q] * n, src[q], sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-      } else {
-        widen_kernel<float><<<grid_blocks(n, 256), 256, 0, h->stream>>>((const float *)src[q], xyz + row[q] * n, n);
-        CUDA_TRY(cudaGetLastError());
-      }
-    }
-    CUDA_TRY(cudaMemcpyAsync(xyz + 2 * n, s.bxi, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(xyz + 5 * n, s.buz, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-  }
-  if (lost) CUDA_TRY(cudaMemcpyAsync(lost, s.blost, n, cudaMemcpyDeviceToDevice, h->stream));
+  BeamDesc b = beam_desc(s, nullptr);
+  const int nb = grid_blocks(n, 256);
+  if (h->precision == WAKE_FP64)
+    beam_unpermute_kernel<double><<<nb, 256, 0, h->stream>>>(b, xyz, lost);
+  else
+    beam_unpermute_kernel<float><<<nb, 256, 0, h->stream>>>(b, xyz, lost);
+  CUDA_TRY(cudaGetLastError());
   return WAKE_OK;
 }
 
@@ -442,6 +634,7 @@ int wake_status(wake_sim *h, int sim) {
   if (st & ST_NUMERIC) return fail(WAKE_ENUMERIC, "Gamma <= 0 or a non-finite field in the march");
   if (st & ST_ESCAPE) return fail(WAKE_EESCAPE, "a plasma ring left [0, rmax]");
   if (st & ST_TIMEOUT) return fail(WAKE_ETIMEOUT, "a bounded device wait gave up");
+  if (st & ST_DRIFT) return fail(WAKE_ESTATE, "a beam particle slipped more than one xi cell within a step");
   return WAKE_OK;
 }
 

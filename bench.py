@@ -1,20 +1,22 @@
-"""Benchmark: plasma pushes/s of the quasi-static wake step on the blowout two-bunch workload.
+"""Benchmark: plasma pushes/s of the quasi-static wake method on the blowout two-bunch workload.
 
-Workload (one "step" = one beam time step: beam deposit -> xi-march -> beam push): warm
-plasma u_th = 0.01, Nr = 512 over 8 k_p^-1, Nxi = 2048 over 12 k_p^-1, 8 rings per cell
-(4096 rings per slice), two-bunch Eq. 12 driver n_b/n_p = 8, sigma_r = 0.2, sigma_z = 0.6,
-gamma = 4e4, witness 4.5 behind with 30% of the drive charge, 1,048,576 beam macroparticles,
-dt = 5.  One step = 4096 x 2048 = 8,388,608 plasma pushes and 1,048,576 beam pushes.
+Workload: warm plasma u_th = 0.01, Nr = 512 over 8 k_p^-1, Nxi = 2048 over 12 k_p^-1, 8 rings
+per cell (4096 rings per slice), two-bunch Eq. 12 driver n_b/n_p = 8, sigma_r = 0.2,
+sigma_z = 0.6, gamma = 4e4, witness 4.5 behind with 30% of the drive charge, 1,048,576 beam
+macroparticles, 200 beam steps of ds = 5.  One bench step is one run of that workload from
+its initial beam: 200 x (beam deposit -> xi-march -> beam push), i.e. 200 x 4096 x 2049
+plasma pushes and 200 x 1,048,576 beam pushes, taken by one wake_step(200) call (pipelined:
+one cooperative launch, one beam step per SM).
 
 Arms:
   default           the library's mixed-precision form (FP32 rings and fields, wide sums)
   --impl reference  the FP64 CPU oracle on the host cores (bounded sample of the same steps)
 
-Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events on the
-library's stream; between timed steps a 512 MB buffer is written to flush L2.  The JSON
-line also carries the plain-FP64 GPU path (same scheme, FP64 throughout), an end-to-end
-number through the C ABI from pinned host buffers, the march kernel's roofline and the
-oracle CPU baseline.
+Timing: W untimed warm-up runs, then K runs, each bracketed by CUDA events on the library's
+stream; before each timed run the beam is re-initialised on the device (outside the timed
+region) and a 512 MB buffer is written to flush L2.  The JSON line also carries the plain
+FP64 GPU path (same scheme, FP64 throughout), an end-to-end number through the C ABI from
+pinned host buffers, the step kernel's roofline and the oracle CPU baseline.
 """
 from __future__ import annotations
 
@@ -34,12 +36,17 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
-# FP32 operations per plasma push of the mixed march (one ring advanced one slice: two
-# field stages and two Cartesian moves; an FMA counts 2, a divide or sqrt 1), and the
-# per-node work of the two stages amortised over the rings of the slice.  Counted from
-# the kernel source, see the design doc.
+# Algorithmic FP32 operations (an FMA counts 2, a divide or square root 1): per plasma push
+# (one ring advanced one slice: two field stages and two Cartesian moves), per grid node and
+# field stage (the radial solves), and per beam push (bilinear gather, Boris step, deposit
+# into the next step's grid).
 FLOP_PER_PUSH = 236.0
 FLOP_PER_NODE_STAGE = 62.0
+FLOP_PER_BEAM_PUSH = 140.0
+BEAM_STEPS = 200
+# kernels of one pipelined wake_step launch sequence: slip bound, three of the cell sort,
+# deposit and normalise of the first step's density, the step kernel
+KERNELS_PER_RUN = 7
 
 
 def workload():
@@ -47,11 +54,12 @@ def workload():
 
 
 def plasma_pushes_per_step(cfg):
-    return cfg.nr * cfg.ppc * cfg.nxi
+    """Plasma pushes of one march: every ring through every slice xi_0 .. xi_Nxi."""
+    return cfg.nr * cfg.ppc * (cfg.nxi + 1)
 
 
 def march_flops(cfg):
-    return plasma_pushes_per_step(cfg) * FLOP_PER_PUSH + 2 * cfg.nxi * (cfg.nr + 1) * FLOP_PER_NODE_STAGE
+    return plasma_pushes_per_step(cfg) * FLOP_PER_PUSH + 2 * (cfg.nxi + 1) * (cfg.nr + 1) * FLOP_PER_NODE_STAGE
 
 
 def peaks():
@@ -176,32 +184,37 @@ def run_reference(args, world, rank):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_dict(cfg, world),
+            "config": config_dict(cfg, world, BEAM_STEPS),
             "cpu_baseline": {"value": v, "unit": "pushes/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} full beam steps of the workload, one host thread"},
+                             "sample": f"each step: one beam step (deposit, march, push) of the workload's "
+                                       f"{BEAM_STEPS}, FP64 oracle, one host thread"},
             "e2e": {"value": v, "unit": "pushes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def config_dict(cfg, world):
-    return {"workload": "blowout two-bunch warm plasma, Nr=512 x Nxi=2048, 8 rings/cell, 1M beam particles, dt=5",
+def config_dict(cfg, world, beam_steps):
+    return {"workload": f"blowout two-bunch warm plasma, Nr={cfg.nr} x Nxi={cfg.nxi}, {cfg.ppc} rings/cell, "
+                        f"{cfg.n_beam} beam particles, {beam_steps} beam steps of ds={cfg.ds:g}",
+            "step": f"one run of the workload from its initial beam: {beam_steps} x (deposit, xi-march, push)",
             "nr": cfg.nr, "nxi": cfg.nxi, "ppc": cfg.ppc, "n_beam": cfg.n_beam, "u_th": cfg.u_th,
-            "plasma_pushes_per_step": plasma_pushes_per_step(cfg), "beam_pushes_per_step": cfg.n_beam,
-            "l2": "flushed between timed steps (512 MB write)", "parallelism": f"replicas x{world}"}
+            "beam_steps": beam_steps, "plasma_pushes_per_step": plasma_pushes_per_step(cfg) * beam_steps,
+            "beam_pushes_per_step": cfg.n_beam * beam_steps,
+            "l2": "flushed before each timed run (512 MB write); the run's working set exceeds L2",
+            "parallelism": f"replicas x{world}"}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=2)
-    ap.add_argument("--march-only", type=int, default=0,
-                    help="run this many mixed marches of the workload and exit (profiling)")
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed runs of the FP64 form (0: skip)")
+    ap.add_argument("--beam-steps", type=int, default=BEAM_STEPS, help="beam steps per run (profiling)")
     ap.add_argument("--nr", type=int, default=0, help="override Nr (profiling a smaller case)")
     ap.add_argument("--nxi", type=int, default=0, help="override Nxi (profiling a smaller case)")
+    ap.add_argument("--n-beam", type=int, default=0, help="override the beam size (profiling)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -216,95 +229,82 @@ def main():
         cfg.nr = args.nr
     if args.nxi:
         cfg.nxi = args.nxi
+    if args.n_beam:
+        cfg = synth.two_bunch(cfg, 0.3, 4.5, args.n_beam)
+    nbs = args.beam_steps
     cfg.seed += 1000 * rank  # independent replicas
     nm_p = torch.from_numpy(synth.plasma_normals(cfg)).pin_memory()
     nm_b = torch.from_numpy(synth.beam_normals(cfg)).pin_memory()
     stream = torch.cuda.Stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
-    pushes = plasma_pushes_per_step(cfg)
+    pushes = plasma_pushes_per_step(cfg) * nbs
 
-    if args.march_only:
-        sim = wake.Simulations([cfg], wake.WAKE_MIXED, stream)
-        with torch.cuda.stream(stream):
-            wake.wake_load_plasma(sim.h, 0, nm_p.cuda(non_blocking=True))
-            wake.wake_load_beam(sim.h, 0, nm_b.cuda(non_blocking=True))
-            wake.wake_beam_deposit(sim.h)
-            for _ in range(args.march_only):
-                wake.wake_plasma_march(sim.h)
-        stream.synchronize()
-        st = sim.status(0)
-        sim.close()
-        print(json.dumps({"march_only": args.march_only, "nr": cfg.nr, "nxi": cfg.nxi, "status": st}))
-        return
-
-    def timed_steps(prec, k, w, march_events=True):
+    def timed_runs(prec, k, w):
+        """k timed runs (w untimed first) of the workload; returns per-run wall ms (events around
+        wake_step), the step kernel's ms per run, and the last run's diagnostics."""
         sim = wake.Simulations([cfg], prec, stream)
         with torch.cuda.stream(stream):
-            wake.wake_load_plasma(sim.h, 0, nm_p.cuda(non_blocking=True))
-            wake.wake_load_beam(sim.h, 0, nm_b.cuda(non_blocking=True))
-            for _ in range(w):
-                wake.wake_step(sim.h, 1)
-        stream.synchronize()
-        step_ms, march_ms = [], []
-        for _ in range(k):
+            dp = nm_p.cuda(non_blocking=True)
+            db = nm_b.cuda(non_blocking=True)
+            wake.wake_load_plasma(sim.h, 0, dp)
+        run_ms, kern_ms, diag = [], [], None
+        for i in range(w + k):
             with torch.cuda.stream(stream):
+                wake.wake_load_beam(sim.h, 0, db)
                 flush.fill_(1)
-                ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
                 ev[0].record(stream)
-                wake.wake_beam_deposit(sim.h)
+                wake.wake_step(sim.h, nbs)
                 ev[1].record(stream)
-                wake.wake_plasma_march(sim.h)
-                ev[2].record(stream)
-                wake.wake_beam_push(sim.h)
-                ev[3].record(stream)
             stream.synchronize()
-            step_ms.append(ev[0].elapsed_time(ev[3]))
-            march_ms.append(ev[1].elapsed_time(ev[2]))
+            if i >= w:
+                run_ms.append(ev[0].elapsed_time(ev[1]))
+                kern_ms.append(wake.wake_step_kernel_ms(sim.h))
         st = sim.status(0)
         diag = sim.diagnostics()[0]
         sim.close()
         if st != wake.WAKE_OK:
             raise RuntimeError(f"simulation status {st}: {wake.wake_last_error()}")
-        return step_ms, march_ms, diag
+        return run_ms, kern_ms, diag
 
     # --- mixed-precision arm (the headline) ---
     barrier(world)
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        step_ms, march_ms, diag = timed_steps(wake.WAKE_MIXED, args.steps, args.warmup)
+        run_ms, kern_ms, diag = timed_runs(wake.WAKE_MIXED, args.steps, args.warmup)
         torch.cuda.synchronize()
     barrier(world)
     clocks = clk.summary()
-    tot_s = barrier_max(sum(step_ms) / 1e3, world)
+    tot_s = barrier_max(sum(run_ms) / 1e3, world)
     value = world * pushes * args.steps / tot_s
-    march_s = sum(march_ms) / 1e3 / args.steps
 
-    # --- plain FP64 GPU path, same workload ---
+    # --- plain FP64 GPU path, same workload and scheme ---
     fp64 = None
     if args.fp64_steps > 0:
-        s64, m64, _ = timed_steps(wake.WAKE_FP64, args.fp64_steps, 1)
-        t64 = barrier_max(sum(s64) / 1e3, world)
+        r64, k64, _ = timed_runs(wake.WAKE_FP64, args.fp64_steps, 1)
+        t64 = barrier_max(sum(r64) / 1e3, world)
         fp64 = {"value": world * pushes * args.fp64_steps / t64, "unit": "pushes/s",
-                "ms_per_step": 1e3 * t64 / args.fp64_steps, "steps": args.fp64_steps}
+                "ms_per_step": 1e3 * t64 / args.fp64_steps, "steps": args.fp64_steps,
+                "note": "FP64 form of the same pipelined path (rings, fields and sums in FP64)"}
 
-    # --- end to end through the C ABI from pinned host buffers: a one-step run per step ---
-    e2e_steps = max(1, min(args.steps, 5))
+    # --- end to end through the C ABI from pinned host buffers, one run per step ---
+    e2e_steps = max(1, min(args.steps, 3))
     h2d = nm_p.numel() * 8 + nm_b.numel() * 8
-    diag_host = None
+    sim = wake.Simulations([cfg], wake.WAKE_MIXED, stream)
     e2e_ms = []
-    for _ in range(e2e_steps):
+    for i in range(e2e_steps + 1):  # the first run allocates the pipeline's grids: untimed
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim = wake.Simulations([cfg], wake.WAKE_MIXED, stream)
         with torch.cuda.stream(stream):
             dp = nm_p.cuda(non_blocking=True)
             db = nm_b.cuda(non_blocking=True)
             wake.wake_load_plasma(sim.h, 0, dp)
             wake.wake_load_beam(sim.h, 0, db)
-            wake.wake_step(sim.h, 1)
-        diag_host = sim.diagnostics()  # synchronous device -> host read
-        sim.close()
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+            wake.wake_step(sim.h, nbs)
+        sim.diagnostics()  # synchronous device -> host read of the run's result
+        if i > 0:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    sim.close()
     e2e_s = barrier_max(sum(e2e_ms) / 1e3, world)
 
     # --- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ---
@@ -312,28 +312,31 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n = 8
         sps = oracle_step_rate(cfg, n)
-        cpu = {"value": pushes / sps, "unit": "pushes/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} full beam steps of the workload (FP64 oracle, one host thread)"}
+        cpu = {"value": plasma_pushes_per_step(cfg) / sps, "unit": "pushes/s", "cores": 1, "kind": "oracle",
+               "sample": f"{n} beam steps of the workload (FP64 oracle, one host thread)"}
 
     pk, src = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    achieved = march_flops(cfg) / march_s / 1e12
+    alive = diag[0] + diag[3]
+    flops_run = nbs * (march_flops(cfg) + alive * FLOP_PER_BEAM_PUSH)
+    kern_s = sum(kern_ms) / len(kern_ms) / 1e3
+    achieved = flops_run / kern_s / 1e12
     peak = fp32_peak_tflops(sm_mhz)
-    roof = {"kernel": "march_kernel<PolMixed>", "bound": "alu", "achieved": achieved, "peak": peak,
+    roof = {"kernel": "step_kernel<PolMixed>", "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
             "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max clock of {src} peaks file)",
-            "march_ms": 1e3 * march_s}
+            "kernel_ms": 1e3 * kern_s, "kernel_share_of_run": kern_s * 1e3 / (sum(run_ms) / len(run_ms))}
     if rank == 0:
         line = {"metric": "plasma_pushes_per_s", "value": value, "unit": "pushes/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-                "data": "synthetic", "config": config_dict(cfg, world),
-                "beam_pushes_per_s": world * cfg.n_beam * args.steps / tot_s,
+                "data": "synthetic", "config": config_dict(cfg, world, nbs),
+                "beam_pushes_per_s": world * cfg.n_beam * nbs * args.steps / tot_s,
                 "fp64_gpu": fp64,
                 "e2e": {"value": world * pushes * e2e_steps / e2e_s, "unit": "pushes/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 5 * 8},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
-                "gpu_launches": 4 * args.steps,
+                "gpu_launches": KERNELS_PER_RUN * args.steps,
                 "witness": {"mean_gamma": diag[1], "rms_gamma": diag[2], "alive": diag[0]}}
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -107,8 +107,25 @@ int wake_plasma_march(wake_sim *s);
  * for every simulation with a beam.  Needs a march. */
 int wake_beam_push(wake_sim *s);
 
-/* nsteps x (wake_beam_deposit, wake_plasma_march, wake_beam_push). */
+/*
+ * nsteps x (wake_beam_deposit, wake_plasma_march, wake_beam_push).  With one simulation
+ * that has a beam, the steps run pipelined: the beam is sorted by xi cell and one
+ * cooperative launch marches up to one step per SM, each step a few slices behind the one
+ * before, pushing each cell of the beam as soon as its fields are solved (same arithmetic as
+ * the separate calls; only the order of the deposit sums differs).  A launch is limited to
+ * the steps over which no beam particle slips more than a quarter of a xi cell, measured on
+ * the beam at its start (this call synchronises the stream once per launch); a beam that
+ * slips faster, or a handle of several simulations, takes the separate calls.  A particle
+ * found to have slipped further anyway raises WAKE_ESTATE through wake_status.
+ */
 int wake_step(wake_sim *s, int nsteps);
+
+/*
+ * Device time in milliseconds of the pipelined step kernels launched by the last wake_step
+ * call (0 if it took the separate calls), measured with CUDA events on the handle's stream;
+ * synchronous.  Instrumentation only: the paper has no counterpart.
+ */
+int wake_step_kernel_ms(wake_sim *s, float *ms);
 
 /* Copy the last march's fields of `sim` to caller-owned device arrays of (nxi+1)*(nr+1)
  * doubles each (any pointer may be NULL). */

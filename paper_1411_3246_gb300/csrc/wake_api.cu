@@ -75,6 +75,8 @@ struct wake_sim {
   int *d_order = nullptr;
   double *d_diag = nullptr;
   int max_n1 = 0, max_np = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // around each pipelined launch
+  int ev_used = 0;
 };
 
 namespace {
@@ -520,8 +522,20 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
     a.spin_limit = 1LL << 24;  // polls of >= 128 ns: a wait gives up after seconds
     a.ring_bufs = s.pring;
     a.ring_stride = rb;
+    if (h->ev_used == (int)h->ev.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> q{};
+      CUDA_TRY(cudaEventCreate(&q.first));
+      if (cudaEventCreate(&q.second) != cudaSuccess) {
+        cudaEventDestroy(q.first);
+        return fail(WAKE_ECUDA, "cudaEventCreate");
+      }
+      h->ev.push_back(q);
+    }
+    CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].first, h->stream));
     const cudaError_t e = launch_step(fp64, a, s.np, ctas, h->stream);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("pipelined step launch: ") + cudaGetErrorString(e));
+    CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].second, h->stream));
+    ++h->ev_used;
     done += ch;
     last_ch = ch;
     // the density the launch's last march used
@@ -536,6 +550,7 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
 
 int wake_step(wake_sim *h, int nsteps) {
   if (!h || nsteps < 0) return fail(WAKE_EINVAL, "wake_step: null handle or nsteps < 0");
+  h->ev_used = 0;
   if (nsteps == 0) return WAKE_OK;
   if (h->n == 1 && h->sims[0].p.n_beam > 0) {
     Sim &s = h->sims[0];
@@ -544,6 +559,19 @@ int wake_step(wake_sim *h, int nsteps) {
     if (ctas > 0) return step_pipelined(h, nsteps, ctas);
   }
   return step_sequential(h, nsteps);
+}
+
+int wake_step_kernel_ms(wake_sim *h, float *ms) {
+  if (!h || !ms) return fail(WAKE_EINVAL, "wake_step_kernel_ms: null argument");
+  float tot = 0.0f;
+  for (int i = 0; i < h->ev_used; ++i) {
+    float t = 0.0f;
+    CUDA_TRY(cudaEventSynchronize(h->ev[i].second));
+    CUDA_TRY(cudaEventElapsedTime(&t, h->ev[i].first, h->ev[i].second));
+    tot += t;
+  }
+  *ms = tot;
+  return WAKE_OK;
 }
 
 int wake_get_fields(wake_sim *h, int sim, double *psi, double *ez, double *er, double *bth) {
@@ -646,6 +674,10 @@ void wake_destroy(wake_sim *h) {
   if (h->d_desc) cudaFree(h->d_desc);
   if (h->d_order) cudaFree(h->d_order);
   if (h->d_diag) cudaFree(h->d_diag);
+  for (auto &q : h->ev) {
+    cudaEventDestroy(q.first);
+    cudaEventDestroy(q.second);
+  }
   delete h;
 }
 

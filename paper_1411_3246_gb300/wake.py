@@ -18,7 +18,7 @@ WAKE_FP64, WAKE_MIXED = 0, 1
 
 # every entry point the header declares
 EXPORTS = ["wake_init", "wake_load_plasma", "wake_load_beam", "wake_beam_deposit", "wake_plasma_march",
-           "wake_beam_push", "wake_step", "wake_get_fields", "wake_get_nb", "wake_get_beam",
+           "wake_beam_push", "wake_step", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
            "wake_diagnostics", "wake_status", "wake_last_error", "wake_destroy"]
 
 
@@ -54,6 +54,7 @@ def lib():
         for n in ("wake_beam_deposit", "wake_plasma_march", "wake_beam_push"):
             getattr(L, n).argtypes = [vp]
         L.wake_step.argtypes = [vp, i32]
+        L.wake_step_kernel_ms.argtypes = [vp, C.POINTER(C.c_float)]
         L.wake_get_fields.argtypes = [vp, i32, vp, vp, vp, vp]
         L.wake_get_nb.argtypes = [vp, i32, vp]
         L.wake_get_beam.argtypes = [vp, i32, vp, vp]
@@ -122,6 +123,12 @@ def wake_beam_push(h):
 
 def wake_step(h, nsteps):
     _check(lib().wake_step(h, nsteps))
+
+
+def wake_step_kernel_ms(h):
+    ms = C.c_float()
+    _check(lib().wake_step_kernel_ms(h, C.byref(ms)))
+    return ms.value
 
 
 def wake_get_fields(h, sim, psi=None, ez=None, er=None, bth=None):

@@ -67,6 +67,11 @@ int grid_blocks(int64_t n, int threads) {
 
 }  // namespace
 
+namespace wake {
+// Error message of an entry point defined in another translation unit.
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace wake
+
 struct wake_sim {
   int n = 0, precision = 0;
   cudaStream_t stream = nullptr;

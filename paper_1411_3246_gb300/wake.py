@@ -19,7 +19,8 @@ WAKE_FP64, WAKE_MIXED = 0, 1
 # every entry point the header declares
 EXPORTS = ["wake_init", "wake_load_plasma", "wake_load_beam", "wake_beam_deposit", "wake_plasma_march",
            "wake_beam_push", "wake_step", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
-           "wake_diagnostics", "wake_status", "wake_last_error", "wake_destroy"]
+           "wake_diagnostics", "wake_status", "wake_beam_deposit_noalloc", "wake_last_error", "wake_destroy"]
+WAKE_NOALLOC_MAX_NODES = 524288
 
 
 class wake_params(C.Structure):
@@ -60,6 +61,7 @@ def lib():
         L.wake_get_beam.argtypes = [vp, i32, vp, vp]
         L.wake_diagnostics.argtypes = [vp, pd]
         L.wake_status.argtypes = [vp, i32]
+        L.wake_beam_deposit_noalloc.argtypes = [C.POINTER(wake_params), vp, vp, vp, vp]
         L.wake_last_error.restype = C.c_char_p
         L.wake_last_error.argtypes = []
         L.wake_destroy.argtypes = [vp]
@@ -147,6 +149,16 @@ def wake_diagnostics(h, n_sims):
     out = (C.c_double * (5 * n_sims))()
     _check(lib().wake_diagnostics(h, out))
     return [list(out[5 * i:5 * i + 5]) for i in range(n_sims)]
+
+
+def wake_beam_deposit_noalloc(params, xyz, lost, nb, stream=None):
+    """params: a wake_params; xyz (6 x n_beam float64), lost (uint8) and nb ((nxi+1) x (nr+1)
+    float64) CUDA tensors; stream: a torch.cuda.Stream (None: torch's current)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(lib().wake_beam_deposit_noalloc(C.byref(params), _ptr(xyz), _ptr(lost),
+                                           C.c_void_p(stream.cuda_stream), _ptr(nb)))
 
 
 def wake_status(h, sim):

@@ -108,7 +108,12 @@ int wake_plasma_march(wake_sim *s);
 int wake_beam_push(wake_sim *s);
 
 /*
- * nsteps x (wake_beam_deposit, wake_plasma_march, wake_beam_push).  With one simulation
+ * nsteps x (wake_beam_deposit, wake_plasma_march, wake_beam_push).  With several
+ * simulations one step is a batched deposit, one march launch per tile class (concurrent
+ * streams) and a batched push; the first call captures that step as a CUDA graph on the
+ * handle's stream and every call replays it nsteps times (on the legacy default stream, or
+ * while the caller's stream is capturing, the launches are issued directly).  With one
+ * simulation
  * that has a beam, the steps run pipelined: the beam is sorted by xi cell and one
  * cooperative launch marches up to one step per SM, each step a few slices behind the one
  * before, pushing each cell of the beam as soon as its fields are solved (same arithmetic as
@@ -119,6 +124,16 @@ int wake_beam_push(wake_sim *s);
  * found to have slipped further anyway raises WAKE_ESTATE through wake_status.
  */
 int wake_step(wake_sim *s, int nsteps);
+
+/*
+ * The march tile simulation `sim` runs in: nt threads per CTA, ppt rings per thread.  With
+ * several simulations the first march chooses each simulation's tile by timing the compiled
+ * candidates on a short probe march (synchronous: make that first march before any stream
+ * capture); the environment variable WAKE_TILE_NT (128, 256 or 512), read by wake_init,
+ * restricts the choice to one width.  Before the first march both are 0.  Instrumentation
+ * and tuning: the paper has no counterpart.
+ */
+int wake_tile(wake_sim *s, int sim, int *nt, int *ppt);
 
 /*
  * Device time in milliseconds of the pipelined step kernels launched by the last wake_step

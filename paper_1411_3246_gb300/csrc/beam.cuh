@@ -50,14 +50,15 @@ __global__ void beam_init_kernel(BeamDesc b, BunchInit q, const double *__restri
   }
 }
 
-// Raw bilinear deposit of the beam weights on the (r, xi) nodes (grid zeroed beforehand).
+// Raw bilinear deposit of the beam weights on the (r, xi) nodes (grid zeroed beforehand):
+// particles j0, j0 + stride, ...
 template <class BT, class G>
-__global__ void beam_deposit_kernel(BeamDesc b) {
+__device__ __forceinline__ void deposit_range(const BeamDesc &b, int64_t j0, int64_t stride) {
   G *nb = (G *)b.nb;
   const int n1 = b.nr + 1;
   const BT inv_dr = (BT)(1.0 / b.dr);
   const double inv_dxi = 1.0 / b.dxi;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = j0; j < b.n; j += stride) {
     const uint8_t fl = b.lost[j];
     if (fl & 1) continue;
     const BT x = ((const BT *)b.x)[j], y = ((const BT *)b.y)[j];
@@ -76,17 +77,27 @@ __global__ void beam_deposit_kernel(BeamDesc b) {
     atomicAdd(row + n1 + 1, (G)(w * f * gg));
   }
 }
+template <class BT, class G>
+__global__ void beam_deposit_kernel(BeamDesc b) {
+  deposit_range<BT, G>(b, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
 
 // Divide the raw deposit by the hats' volumes: V_i in r, dxi in xi (dxi/2 at both ends).
 template <class G>
-__global__ void nb_normalize_kernel(G *nb, int nr, int nxi, double dr, double dxi) {
+__device__ __forceinline__ void normalize_range(G *nb, int nr, int nxi, double dr, double dxi, int64_t t0,
+                                                int64_t stride) {
   const int n1 = nr + 1;
   const int64_t tot = (int64_t)(nxi + 1) * n1;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = t0; t < tot; t += stride) {
     const int k = (int)(t / n1), i = (int)(t % n1);
     const double vx = (k == 0 || k == nxi) ? 0.5 * dxi : dxi;
     nb[t] = (G)((double)nb[t] / (node_volume(i, nr, dr) * vx));
   }
+}
+template <class G>
+__global__ void nb_normalize_kernel(G *nb, int nr, int nxi, double dr, double dxi) {
+  normalize_range<G>(nb, nr, nxi, dr, dxi, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                     (int64_t)gridDim.x * blockDim.x);
 }
 
 // Eq. 12 on the nodes (frozen analytic driver).
@@ -129,15 +140,16 @@ __device__ __forceinline__ void boris_step(BT &x, BT &y, BT &ux, BT &uy, double 
   xi += (double)(dt * ((BT)1 + up2) / (gam * (gam + uzn)));
 }
 
-// One beam step through the grid fields of the last march, bilinear gather in (r, xi).
+// One beam step through the grid fields of the last march, bilinear gather in (r, xi):
+// particles j0, j0 + stride, ...
 template <class BT, class G>
-__global__ void beam_push_kernel(BeamDesc b) {
+__device__ __forceinline__ void push_range(const BeamDesc &b, int64_t j0, int64_t stride) {
   const G *er = (const G *)b.er, *ez = (const G *)b.ez, *bt = (const G *)b.bth;
   BT *X = (BT *)b.x, *Y = (BT *)b.y, *UX = (BT *)b.ux, *UY = (BT *)b.uy;
   const int n1 = b.nr + 1;
   const BT inv_dr = (BT)(1.0 / b.dr), dt = (BT)b.ds, Rw = (BT)b.rmax;
   const double inv_dxi = 1.0 / b.dxi;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = j0; j < b.n; j += stride) {
     if (b.lost[j] & 1) continue;
     BT x = X[j], y = Y[j], ux = UX[j], uy = UY[j];
     double xi = b.xi[j], uzd = b.uz[j];
@@ -163,6 +175,38 @@ __global__ void beam_push_kernel(BeamDesc b) {
     const BT rn = sqrt(x * x + y * y);
     if (!(xi >= 0.0 && xi < b.ximax && rn < Rw)) b.lost[j] |= 1;
   }
+}
+template <class BT, class G>
+__global__ void beam_push_kernel(BeamDesc b) {
+  push_range<BT, G>(b, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+
+// Batched forms over the simulations of a handle: blockIdx.y is the simulation; simulations
+// without a beam (n == 0, the frozen analytic driver) are left alone.
+template <class G>
+__global__ void nb_zero_batch_kernel(const BeamDesc *bs) {
+  const BeamDesc &b = bs[blockIdx.y];
+  if (b.n == 0) return;
+  const int64_t tot = (int64_t)(b.nxi + 1) * (b.nr + 1);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x)
+    ((G *)b.nb)[t] = (G)0;
+}
+template <class BT, class G>
+__global__ void beam_deposit_batch_kernel(const BeamDesc *bs) {
+  const BeamDesc b = bs[blockIdx.y];
+  deposit_range<BT, G>(b, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+}
+template <class G>
+__global__ void nb_normalize_batch_kernel(const BeamDesc *bs) {
+  const BeamDesc &b = bs[blockIdx.y];
+  if (b.n == 0) return;
+  normalize_range<G>((G *)b.nb, b.nr, b.nxi, b.dr, b.dxi, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                     (int64_t)gridDim.x * blockDim.x);
+}
+template <class BT, class G>
+__global__ void beam_push_batch_kernel(const BeamDesc *bs) {
+  const BeamDesc b = bs[blockIdx.y];
+  push_range<BT, G>(b, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
 // Witness / drive sums in FP64: counts, sum(gamma - gamma_b), sum(gamma - gamma_b)^2.

@@ -159,7 +159,7 @@ struct MarchSmem {
   Acc *jz, *chi, *T, *P, *U, *K;                // current-type deposits
   R *psi, *dpsi, *ez, *bth;                     // node fields
   R *nb0, *nb1;                                 // beam-density rows (double buffer)
-  R *ta, *tb, *tc, *td, *tu, *tv;               // tridiagonal scratch (row l*M + k at k*32 + l)
+  R *ta, *tb, *tc, *td;                         // tridiagonal rows (a, row sum, c, rhs)
   R *invR, *invV, *alpha, *ga, *gb, *gc;        // tables (FP64 form; the mixed form keeps
                                                 // invR = 1/(m dr) and ga = 1/(j + 1/2) only)
   int *cnt;                                     // re-sort counts
@@ -167,7 +167,7 @@ struct MarchSmem {
   RingSoA<R> rings;                             // ring slots (mixed form)
 
   __host__ __device__ static size_t bytes(int n1, int slots) {
-    size_t b = sizeof(typename Pol::W) * 64 + sizeof(typename Pol::Q) * 2 * (size_t)n1 + sizeof(Acc) * 6 * (size_t)n1 + sizeof(R) * 6 * (size_t)n1 + sizeof(R) * 6 * ((size_t)n1 + 32) + 256;
+    size_t b = sizeof(typename Pol::W) * 64 + sizeof(typename Pol::Q) * 2 * (size_t)n1 + sizeof(Acc) * 6 * (size_t)n1 + sizeof(R) * 6 * (size_t)n1 + sizeof(R) * 4 * ((size_t)n1 + 32) + 256;
     b += sizeof(R) * (Pol::kTables ? 6 : 2) * (size_t)n1;
     if (Pol::kSortEvery > 0) b += sizeof(int) * ((size_t)n1 + 32);
     if (Pol::kSmemRings) b += RingSoA<R>::bytes(slots) + 32;
@@ -196,8 +196,6 @@ struct MarchSmem {
     tb = rp; rp += n1 + 32;
     tc = rp; rp += n1 + 32;
     td = rp; rp += n1 + 32;
-    tu = rp; rp += n1 + 32;
-    tv = rp; rp += n1 + 32;
     invR = invV = alpha = ga = gb = gc = nullptr;
     invR = rp; rp += n1;
     ga = rp; rp += n1;
@@ -1083,6 +1081,7 @@ struct PlainHooks {
   __device__ __forceinline__ bool wait_rows(int) { return true; }
   __device__ __forceinline__ R nb_row(int row, int m) const { return (R)nb[(size_t)row * n1 + m]; }
   __device__ __forceinline__ void slice_done(int k, MarchSmem<Pol> &sm) {
+    if (!opsi) return;  // a timing probe of the tile autotuner keeps no output
     G *o1 = opsi + (size_t)k * n1, *o2 = oez + (size_t)k * n1, *o3 = oer + (size_t)k * n1, *o4 = obth + (size_t)k * n1;
     for (int m = threadIdx.x; m < n1; m += NT) {
       const R ps = sm.psi[m], e = sm.ez[m], b = sm.bth[m];
@@ -1096,8 +1095,10 @@ struct PlainHooks {
   __device__ __forceinline__ void finish(MarchSmem<Pol> &) {}
 };
 
+// One CTA per simulation.  Tiles of fewer threads ask for more CTAs per SM, within the
+// same 128 registers per thread.
 template <class Pol, int NT, int PPT>
-__global__ void __launch_bounds__(NT, 1) march_kernel(const SimDesc *descs, const int *order) {
+__global__ void __launch_bounds__(NT, (NT < 512 ? 512 / NT : 1)) march_kernel(const SimDesc *descs, const int *order) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SimDesc &d = descs[order ? order[blockIdx.x] : blockIdx.x];
   PlainHooks<Pol, NT> hk{(const typename Pol::G *)d.nb, (typename Pol::G *)d.psi, (typename Pol::G *)d.ez,

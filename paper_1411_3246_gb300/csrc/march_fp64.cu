@@ -1,41 +1,24 @@
 // FP64 form of the xi-march (every step in double precision).
-#include "march.cuh"
+#include "march_tiles.cuh"
 #include "pipeline.cuh"
-#include "march_launch.h"
 
 namespace wake {
 
-template <int PPT>
-static cudaError_t go(const MarchLaunch &L) {
-  auto kern = march_kernel<PolFP64, PolFP64::NT, PPT>;
-  const size_t smem = MarchSmem<PolFP64>::bytes(L.max_n1, PolFP64::NT * PPT);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<L.n, PolFP64::NT, smem, L.stream>>>(L.d_desc, L.d_order);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_march_fp64(const MarchLaunch &L, int *ppt_out) {
-  const int ppt = (L.max_np + PolFP64::NT - 1) / PolFP64::NT;
-  *ppt_out = ppt <= 1 ? 1 : ppt <= 2 ? 2 : ppt <= 4 ? 4 : ppt <= 8 ? 8 : ppt <= 16 ? 16 : 0;
-  switch (*ppt_out) {
-    case 1: return go<1>(L);
-    case 2: return go<2>(L);
-    case 4: return go<4>(L);
-    case 8: return go<8>(L);
-    case 16: return go<16>(L);
-    default: return cudaErrorInvalidValue;
+bool march_tile_fp64(int nt, int ppt, TileFns *out) {
+  if (nt != PolFP64::NT) return false;
+  switch (ppt) {
+    case 1: *out = tile_fns<PolFP64, 512, 1>(); return true;
+    case 2: *out = tile_fns<PolFP64, 512, 2>(); return true;
+    case 4: *out = tile_fns<PolFP64, 512, 4>(); return true;
+    case 8: *out = tile_fns<PolFP64, 512, 8>(); return true;
+    case 16: *out = tile_fns<PolFP64, 512, 16>(); return true;
+    default: return false;
   }
 }
 
-static int ppt_of(int np, int nt) {
-  const int ppt = (np + nt - 1) / nt;
-  return ppt <= 1 ? 1 : ppt <= 2 ? 2 : ppt <= 4 ? 4 : ppt <= 8 ? 8 : ppt <= 16 ? 16 : 0;
-}
-
-size_t march_smem_bytes(int precision_fp64, int n1, int np) {
-  if (precision_fp64) return MarchSmem<PolFP64>::bytes(n1, PolFP64::NT * ppt_of(np, PolFP64::NT));
-  return MarchSmem<PolMixed>::bytes(n1, PolMixed::NT * ppt_of(np, PolMixed::NT));
+bool march_tile(int precision_fp64, int nt, int ppt, TileFns *out) {
+  if (precision_fp64) return march_tile_fp64(nt, ppt, out);
+  return nt == 512 ? march_tile_mixed512(nt, ppt, out) : march_tile_mixed_small(nt, ppt, out);
 }
 
 size_t ring_buf_bytes(int precision_fp64) {

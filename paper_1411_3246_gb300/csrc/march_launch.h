@@ -10,17 +10,23 @@ namespace wake {
 
 struct PipeArgs;
 
-struct MarchLaunch {
-  const SimDesc *d_desc;  // n descriptors (device)
-  const int *d_order;     // CTA -> simulation (device), largest work first
-  int n, max_n1, max_np;
-  cudaStream_t stream;
-};
+constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
-// Each returns cudaSuccess or the launch error; ppt_out receives the rings per thread used
-// (0 if max_np needs more than the largest compiled variant).
-cudaError_t launch_march_fp64(const MarchLaunch &L, int *ppt_out);
-cudaError_t launch_march_mixed(const MarchLaunch &L, int *ppt_out);
+// A compiled march tile: NT threads per CTA, PPT rings per thread (march_tiles.cuh).
+struct TileFns {
+  int nt, ppt;
+  // one CTA per entry of order[0..count-1] (descriptor d[order[i]]), shared memory for n1 nodes
+  cudaError_t (*launch)(const SimDesc *d, const int *order, int count, int n1, cudaStream_t s);
+  cudaError_t (*prepare)(int n1);  // shared-memory limit for n1 nodes (before any capture)
+  size_t (*smem)(int n1);
+  int (*occupancy)(int n1);  // CTAs per SM for n1 nodes, 0 if it does not fit
+};
+// The tile (nt, ppt) of a precision form, if it is compiled.
+bool march_tile(int precision_fp64, int nt, int ppt, TileFns *out);
+bool march_tile_fp64(int nt, int ppt, TileFns *out);
+bool march_tile_mixed512(int nt, int ppt, TileFns *out);
+bool march_tile_mixed_small(int nt, int ppt, TileFns *out);
+
 // Global-memory ring slot storage one simulation needs (0 when the rings live in shared
 // memory).
 size_t ring_buf_bytes(int precision_fp64);
@@ -30,7 +36,5 @@ size_t ring_buf_bytes(int precision_fp64);
 bool step_smem_ok(int precision_fp64, int n1, int np);
 int step_max_ctas(int precision_fp64, int n1, int np);
 cudaError_t launch_step(int precision_fp64, const PipeArgs &a, int np, int ctas, cudaStream_t stream);
-// Dynamic shared memory one march CTA needs for n1 nodes and np rings.
-size_t march_smem_bytes(int precision_fp64, int n1, int np);
 
 }  // namespace wake

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -60,6 +61,10 @@ struct Sim {
 
 size_t gsize(int precision) { return precision == WAKE_FP64 ? sizeof(double) : sizeof(float); }
 
+// x-extent of a batched launch (blockIdx.y is the simulation): up to 64 blocks of 256 per
+// simulation, each striding over that simulation's particles or nodes.
+int batch_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 64)); }
+
 int grid_blocks(int64_t n, int threads) {
   int64_t b = (n + threads - 1) / threads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
@@ -82,6 +87,24 @@ struct wake_sim {
   int max_n1 = 0, max_np = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;  // around each pipelined launch
   int ev_used = 0;
+  // march tiles: simulations grouped by the tile the autotuner chose (planned at the first march)
+  struct TileClass {
+    TileFns fns;
+    int n1max = 0, off = 0, count = 0;
+    cudaStream_t side = nullptr;  // class 0 runs on the handle's stream
+    cudaEvent_t done = nullptr;
+  };
+  bool planned = false;
+  std::vector<TileClass> classes;
+  std::vector<int> tile_of;  // per simulation: its class
+  cudaEvent_t fork = nullptr;
+  SimDesc *d_probe = nullptr;  // autotuner probe descriptor, status word, all-zero CTA map
+  int *d_probe_status = nullptr, *d_probe_order = nullptr;
+  int tile_nt_forced = 0;  // WAKE_TILE_NT
+  BeamDesc *d_bdesc = nullptr;  // per simulation (several simulations: the batched beam kernels)
+  int64_t max_beam = 0;
+  size_t max_ng = 0;
+  cudaGraphExec_t step_graph = nullptr;  // one batched step, captured at the first wake_step
 };
 
 namespace {
@@ -152,12 +175,168 @@ BeamDesc beam_desc(const Sim &s, double *diag) {
   return b;
 }
 
+constexpr int kProbeSlices = 48;
+constexpr int kMaxProbeCtas = 152 * 16;
+
+int pow2_at_least(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+// Compiled tiles that can march simulation s: NT x PPT >= Np rings, Nr+1 <= 3 NT nodes (a
+// thread holds at most three nodes in the block scans), shared memory within one CTA's limit.
+std::vector<TileFns> tile_candidates(const wake_sim *h, const Sim &s) {
+  std::vector<TileFns> out;
+  const int n1 = s.p.nr + 1;
+  for (int nt : {128, 256, 512}) {
+    if (h->precision == WAKE_FP64 && nt != 512) continue;
+    if (h->tile_nt_forced && nt != h->tile_nt_forced) continue;
+    if (n1 > 3 * nt) continue;
+    const int ppt = pow2_at_least((s.np + nt - 1) / nt);
+    TileFns f;
+    if (!march_tile(h->precision == WAKE_FP64, nt, ppt, &f)) continue;
+    if (f.smem(n1) > kMaxSmemPerCta) continue;
+    out.push_back(f);
+  }
+  return out;
+}
+
+// Throughput score of tile f on simulation s: a probe march of kProbeSlices slices run by as
+// many CTAs as fill the GPU (all on s, outputs discarded), CTAs x slices per ms.
+int probe_tile(wake_sim *h, const Sim &s, const SimDesc &d, const TileFns &f, double *score) {
+  const int n1 = s.p.nr + 1;
+  int occ = f.occupancy(n1), dev = 0, sms = 0;
+  if (occ < 1) {
+    *score = 0.0;
+    return WAKE_OK;
+  }
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int ctas = std::min(kMaxProbeCtas, occ * sms);
+  SimDesc pd = d;
+  pd.nxi = std::min(d.nxi, kProbeSlices);
+  pd.psi = pd.ez = pd.er = pd.bth = nullptr;
+  pd.status = h->d_probe_status;
+  CUDA_TRY(cudaMemcpyAsync(h->d_probe, &pd, sizeof(SimDesc), cudaMemcpyHostToDevice, h->stream));
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(WAKE_ECUDA, "cudaEventCreate");
+  }
+  cudaError_t e = f.launch(h->d_probe, h->d_probe_order, ctas, n1, h->stream);  // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+  if (e == cudaSuccess) e = f.launch(h->d_probe, h->d_probe_order, ctas, n1, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.0f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("tile probe: ") + cudaGetErrorString(e));
+  *score = ms > 0.0f ? (double)ctas * pd.nxi / ms : 0.0;
+  return WAKE_OK;
+}
+
+// Choose a tile per simulation (the best probe score per distinct (Nr, Np); the only
+// candidate when there is one) and group the simulations by tile, each group largest work
+// first.  Synchronous (the probes are timed).
+int plan_tiles(wake_sim *h) {
+  std::vector<SimDesc> desc(h->n);
+  CUDA_TRY(cudaMemcpyAsync(desc.data(), h->d_desc, sizeof(SimDesc) * h->n, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  std::vector<std::pair<long long, TileFns>> chosen_by_shape;  // key nr * 2^20 + np
+  std::vector<TileFns> pick(h->n);
+  for (int i = 0; i < h->n; ++i) {
+    const Sim &s = h->sims[i];
+    const long long key = (long long)s.p.nr * (1 << 20) + s.np;
+    bool found = false;
+    for (auto &kv : chosen_by_shape)
+      if (kv.first == key) {
+        pick[i] = kv.second;
+        found = true;
+      }
+    if (found) continue;
+    std::vector<TileFns> cand = tile_candidates(h, s);
+    if (cand.empty()) return fail(WAKE_EINVAL, "no compiled march tile fits a simulation's Nr and rings");
+    TileFns best = cand.back();  // the 512-thread tile when there is no choice to make
+    if (cand.size() > 1 && h->n > 1) {
+      // representative: the simulation of this shape with the most slices
+      int rep = i;
+      for (int j = i + 1; j < h->n; ++j)
+        if ((long long)h->sims[j].p.nr * (1 << 20) + h->sims[j].np == key && h->sims[j].p.nxi > h->sims[rep].p.nxi) rep = j;
+      double best_score = -1.0;
+      for (const TileFns &f : cand) {
+        double sc = 0.0;
+        int rc = probe_tile(h, h->sims[rep], desc[rep], f, &sc);
+        if (rc) return rc;
+        if (sc > best_score) {
+          best_score = sc;
+          best = f;
+        }
+      }
+    }
+    chosen_by_shape.push_back({key, best});
+    pick[i] = best;
+  }
+  // group by tile, largest work first within a group
+  h->classes.clear();
+  h->tile_of.assign(h->n, 0);
+  for (int i = 0; i < h->n; ++i) {
+    int c = -1;
+    for (size_t q = 0; q < h->classes.size(); ++q)
+      if (h->classes[q].fns.nt == pick[i].nt && h->classes[q].fns.ppt == pick[i].ppt) c = (int)q;
+    if (c < 0) {
+      wake_sim::TileClass tc;
+      tc.fns = pick[i];
+      h->classes.push_back(tc);
+      c = (int)h->classes.size() - 1;
+    }
+    h->tile_of[i] = c;
+    h->classes[c].n1max = std::max(h->classes[c].n1max, h->sims[i].p.nr + 1);
+  }
+  std::vector<int> order;
+  for (size_t c = 0; c < h->classes.size(); ++c) {
+    std::vector<int> mine;
+    for (int i = 0; i < h->n; ++i)
+      if (h->tile_of[i] == (int)c) mine.push_back(i);
+    std::stable_sort(mine.begin(), mine.end(), [&](int a, int b) {
+      return (double)h->sims[a].np * h->sims[a].p.nxi > (double)h->sims[b].np * h->sims[b].p.nxi;
+    });
+    const cudaError_t ep = h->classes[c].fns.prepare(h->classes[c].n1max);
+    if (ep != cudaSuccess) return fail(WAKE_ECUDA, std::string("march tile set-up: ") + cudaGetErrorString(ep));
+    h->classes[c].off = (int)order.size();
+    h->classes[c].count = (int)mine.size();
+    order.insert(order.end(), mine.begin(), mine.end());
+    if (c > 0) {
+      CUDA_TRY(cudaStreamCreateWithFlags(&h->classes[c].side, cudaStreamNonBlocking));
+      CUDA_TRY(cudaEventCreateWithFlags(&h->classes[c].done, cudaEventDisableTiming));
+    }
+  }
+  if (h->classes.size() > 1 && !h->fork) CUDA_TRY(cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming));
+  CUDA_TRY(cudaMemcpyAsync(h->d_order, order.data(), sizeof(int) * h->n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  h->planned = true;
+  return WAKE_OK;
+}
+
+// One march of every simulation: one launch per tile class, the classes on forked streams
+// joined back to the handle's stream.
 int launch_march(wake_sim *h) {
-  MarchLaunch L{h->d_desc, h->d_order, h->n, h->max_n1, h->max_np, h->stream};
-  int ppt = 0;
-  const cudaError_t e = h->precision == WAKE_FP64 ? launch_march_fp64(L, &ppt) : launch_march_mixed(L, &ppt);
-  if (ppt == 0) return fail(WAKE_EINVAL, "too many plasma rings per simulation");
-  if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("march launch: ") + cudaGetErrorString(e));
+  int rc;
+  if (!h->planned && (rc = plan_tiles(h))) return rc;
+  const size_t nc = h->classes.size();
+  if (nc > 1) CUDA_TRY(cudaEventRecord(h->fork, h->stream));
+  for (size_t c = 0; c < nc; ++c) {
+    auto &k = h->classes[c];
+    cudaStream_t st = c == 0 ? h->stream : k.side;
+    if (c > 0) CUDA_TRY(cudaStreamWaitEvent(st, h->fork, 0));
+    const cudaError_t e = k.fns.launch(h->d_desc, h->d_order + k.off, k.count, k.n1max, st);
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("march launch: ") + cudaGetErrorString(e));
+    if (c > 0) CUDA_TRY(cudaEventRecord(k.done, st));
+  }
+  for (size_t c = 1; c < nc; ++c) CUDA_TRY(cudaStreamWaitEvent(h->stream, h->classes[c].done, 0));
   return WAKE_OK;
 }
 
@@ -185,6 +364,7 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
   h->precision = p[0].precision;
   h->stream = (cudaStream_t)stream;
   h->sims.resize(n_sims);
+  if (const char *t = std::getenv("WAKE_TILE_NT")) h->tile_nt_forced = std::atoi(t);
   const size_t gs = gsize(h->precision);
   int rc = WAKE_OK;
   for (int i = 0; i < n_sims && rc == WAKE_OK; ++i) {
@@ -237,8 +417,30 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
       }
     }
   }
-  if (rc == WAKE_OK && march_smem_bytes(h->precision == WAKE_FP64, h->max_n1, h->max_np) > 227 * 1024)
-    rc = fail(WAKE_EINVAL, "nr and nr*ppc too large for one march CTA's shared memory");
+  if (rc == WAKE_OK)
+    for (int i = 0; i < n_sims && rc == WAKE_OK; ++i)
+      if (tile_candidates(h, h->sims[i]).empty())
+        rc = fail(WAKE_EINVAL, "nr and nr*ppc too large for one march CTA's shared memory");
+  if (rc == WAKE_OK && h->n > 1) {
+    std::vector<BeamDesc> bd(n_sims);
+    for (int i = 0; i < n_sims; ++i) {
+      bd[i] = beam_desc(h->sims[i], nullptr);
+      h->max_beam = std::max<int64_t>(h->max_beam, h->sims[i].p.n_beam);
+      h->max_ng = std::max(h->max_ng, h->sims[i].ng);
+    }
+    if ((rc = dalloc(&h->d_bdesc, sizeof(BeamDesc) * n_sims)) == WAKE_OK &&
+        cudaMemcpyAsync(h->d_bdesc, bd.data(), sizeof(BeamDesc) * n_sims, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      rc = fail(WAKE_ECUDA, "wake_init: beam descriptor upload");
+    if (rc == WAKE_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(WAKE_ECUDA, "wake_init: sync");
+  }
+  if (rc == WAKE_OK && h->n > 1) {
+    if ((rc = dalloc(&h->d_probe, sizeof(SimDesc))) == WAKE_OK && (rc = dalloc(&h->d_probe_status, sizeof(int))) == WAKE_OK &&
+        (rc = dalloc(&h->d_probe_order, sizeof(int) * kMaxProbeCtas)) == WAKE_OK) {
+      if (cudaMemsetAsync(h->d_probe_order, 0, sizeof(int) * kMaxProbeCtas, h->stream) != cudaSuccess ||
+          cudaMemsetAsync(h->d_probe_status, 0, sizeof(int), h->stream) != cudaSuccess)
+        rc = fail(WAKE_ECUDA, "wake_init: probe scratch");
+    }
+  }
   if (rc == WAKE_OK) {
     // descriptors; CTAs take the simulations largest-work first (LPT order)
     std::vector<SimDesc> desc(n_sims);
@@ -322,6 +524,23 @@ int wake_load_beam(wake_sim *h, int sim, const double *normals) {
 
 int wake_beam_deposit(wake_sim *h) {
   if (!h) return fail(WAKE_EINVAL, "null handle");
+  if (h->n > 1) {  // one launch per phase over all simulations
+    for (auto &s : h->sims)
+      if (s.p.n_beam > 0 && !s.beam) return fail(WAKE_ESTATE, "wake_beam_deposit before wake_load_beam");
+    if (h->max_beam == 0) return WAKE_OK;
+    const dim3 gg(batch_blocks((int64_t)h->max_ng), h->n), gb(batch_blocks(h->max_beam), h->n);
+    if (h->precision == WAKE_FP64) {
+      nb_zero_batch_kernel<double><<<gg, 256, 0, h->stream>>>(h->d_bdesc);
+      beam_deposit_batch_kernel<double, double><<<gb, 256, 0, h->stream>>>(h->d_bdesc);
+      nb_normalize_batch_kernel<double><<<gg, 256, 0, h->stream>>>(h->d_bdesc);
+    } else {
+      nb_zero_batch_kernel<float><<<gg, 256, 0, h->stream>>>(h->d_bdesc);
+      beam_deposit_batch_kernel<float, float><<<gb, 256, 0, h->stream>>>(h->d_bdesc);
+      nb_normalize_batch_kernel<float><<<gg, 256, 0, h->stream>>>(h->d_bdesc);
+    }
+    CUDA_TRY(cudaGetLastError());
+    return WAKE_OK;
+  }
   for (int i = 0; i < h->n; ++i) {
     Sim &s = h->sims[i];
     if (s.p.n_beam == 0) continue;
@@ -353,6 +572,19 @@ int wake_plasma_march(wake_sim *h) {
 
 int wake_beam_push(wake_sim *h) {
   if (!h) return fail(WAKE_EINVAL, "null handle");
+  if (h->n > 1) {
+    for (auto &s : h->sims)
+      if (s.p.n_beam > 0 && (!s.beam || !s.marched))
+        return fail(WAKE_ESTATE, "wake_beam_push needs a loaded beam and a march");
+    if (h->max_beam == 0) return WAKE_OK;
+    const dim3 gb(batch_blocks(h->max_beam), h->n);
+    if (h->precision == WAKE_FP64)
+      beam_push_batch_kernel<double, double><<<gb, 256, 0, h->stream>>>(h->d_bdesc);
+    else
+      beam_push_batch_kernel<float, float><<<gb, 256, 0, h->stream>>>(h->d_bdesc);
+    CUDA_TRY(cudaGetLastError());
+    return WAKE_OK;
+  }
   for (int i = 0; i < h->n; ++i) {
     Sim &s = h->sims[i];
     if (s.p.n_beam == 0) continue;
@@ -431,6 +663,43 @@ int step_sequential(wake_sim *h, int nsteps) {
     int rc;
     if ((rc = wake_beam_deposit(h)) || (rc = wake_plasma_march(h)) || (rc = wake_beam_push(h))) return rc;
   }
+  return WAKE_OK;
+}
+
+// Several simulations: one step is the batched deposit, one march launch per tile class
+// (forked streams), the batched push.  The step is captured once as a CUDA graph and
+// replayed; on the legacy default stream, or while the caller is capturing, the launches
+// are issued directly.
+int step_batched(wake_sim *h, int nsteps) {
+  int rc;
+  for (auto &s : h->sims)
+    if (!s.plasma) return fail(WAKE_ESTATE, "wake_step before wake_load_plasma");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (h->stream) CUDA_TRY(cudaStreamIsCapturing(h->stream, &cs));
+  if (!h->planned) {
+    if (cs != cudaStreamCaptureStatusNone)
+      return fail(WAKE_ESTATE, "the first march of a handle times its tiles: make it before any stream capture");
+    if ((rc = plan_tiles(h))) return rc;
+  }
+  if (!h->stream || cs != cudaStreamCaptureStatusNone) return step_sequential(h, nsteps);
+  if (!h->step_graph) {
+    CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    rc = step_sequential(h, 1);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("step capture: ") + cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(&h->step_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->step_graph = nullptr;
+      return fail(WAKE_ECUDA, std::string("step graph: ") + cudaGetErrorString(ei));
+    }
+  }
+  for (int t = 0; t < nsteps; ++t) CUDA_TRY(cudaGraphLaunch(h->step_graph, h->stream));
   return WAKE_OK;
 }
 
@@ -563,7 +832,21 @@ int wake_step(wake_sim *h, int nsteps) {
     const int ctas = step_max_ctas(h->precision == WAKE_FP64, s.p.nr + 1, s.np);
     if (ctas > 0) return step_pipelined(h, nsteps, ctas);
   }
+  if (h->n > 1) return step_batched(h, nsteps);
   return step_sequential(h, nsteps);
+}
+
+int wake_tile(wake_sim *h, int sim, int *nt, int *ppt) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  if (!nt || !ppt) return fail(WAKE_EINVAL, "wake_tile: null output");
+  *nt = *ppt = 0;
+  if (h->planned) {
+    const TileFns &f = h->classes[h->tile_of[sim]].fns;
+    *nt = f.nt;
+    *ppt = f.ppt;
+  }
+  return WAKE_OK;
 }
 
 int wake_step_kernel_ms(wake_sim *h, float *ms) {
@@ -679,6 +962,16 @@ void wake_destroy(wake_sim *h) {
   if (h->d_desc) cudaFree(h->d_desc);
   if (h->d_order) cudaFree(h->d_order);
   if (h->d_diag) cudaFree(h->d_diag);
+  if (h->d_probe) cudaFree(h->d_probe);
+  if (h->d_probe_status) cudaFree(h->d_probe_status);
+  if (h->d_probe_order) cudaFree(h->d_probe_order);
+  for (auto &k : h->classes) {
+    if (k.side) cudaStreamDestroy(k.side);
+    if (k.done) cudaEventDestroy(k.done);
+  }
+  if (h->fork) cudaEventDestroy(h->fork);
+  if (h->step_graph) cudaGraphExecDestroy(h->step_graph);
+  if (h->d_bdesc) cudaFree(h->d_bdesc);
   for (auto &q : h->ev) {
     cudaEventDestroy(q.first);
     cudaEventDestroy(q.second);

@@ -18,7 +18,7 @@ WAKE_FP64, WAKE_MIXED = 0, 1
 
 # every entry point the header declares
 EXPORTS = ["wake_init", "wake_load_plasma", "wake_load_beam", "wake_beam_deposit", "wake_plasma_march",
-           "wake_beam_push", "wake_step", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
+           "wake_beam_push", "wake_step", "wake_tile", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
            "wake_diagnostics", "wake_status", "wake_beam_deposit_noalloc", "wake_last_error", "wake_destroy"]
 WAKE_NOALLOC_MAX_NODES = 524288
 
@@ -56,6 +56,7 @@ def lib():
             getattr(L, n).argtypes = [vp]
         L.wake_step.argtypes = [vp, i32]
         L.wake_step_kernel_ms.argtypes = [vp, C.POINTER(C.c_float)]
+        L.wake_tile.argtypes = [vp, i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.wake_get_fields.argtypes = [vp, i32, vp, vp, vp, vp]
         L.wake_get_nb.argtypes = [vp, i32, vp]
         L.wake_get_beam.argtypes = [vp, i32, vp, vp]
@@ -127,6 +128,12 @@ def wake_step(h, nsteps):
     _check(lib().wake_step(h, nsteps))
 
 
+def wake_tile(h, sim):
+    nt, ppt = C.c_int(), C.c_int()
+    _check(lib().wake_tile(h, sim, C.byref(nt), C.byref(ppt)))
+    return nt.value, ppt.value
+
+
 def wake_step_kernel_ms(h):
     ms = C.c_float()
     _check(lib().wake_step_kernel_ms(h, C.byref(ms)))
@@ -180,7 +187,18 @@ class Simulations:
         import torch
         self.cfgs = list(cfgs)
         self.torch = torch
+        self.stream = stream
         self.h = wake_init([params_of(c, precision) for c in self.cfgs], stream)
+
+    def _before(self):
+        """Make the handle's stream wait for torch's current stream (buffers it allocated)."""
+        if self.stream is not None:
+            self.stream.wait_stream(self.torch.cuda.current_stream())
+
+    def _order(self):
+        """Make torch's current stream wait for the handle's stream (outputs it wrote)."""
+        if self.stream is not None:
+            self.torch.cuda.current_stream().wait_stream(self.stream)
 
     def grid(self, sim):
         c = self.cfgs[sim]
@@ -188,19 +206,25 @@ class Simulations:
 
     def fields(self, sim):
         out = {k: self.grid(sim) for k in ("psi", "ez", "er", "bth")}
+        self._before()
         wake_get_fields(self.h, sim, out["psi"], out["ez"], out["er"], out["bth"])
+        self._order()
         return out
 
     def nb(self, sim):
         out = self.grid(sim)
+        self._before()
         wake_get_nb(self.h, sim, out)
+        self._order()
         return out
 
     def beam(self, sim):
         c = self.cfgs[sim]
         xyz = self.torch.empty((6, c.n_beam), dtype=self.torch.float64, device="cuda")
         lost = self.torch.empty(c.n_beam, dtype=self.torch.uint8, device="cuda")
+        self._before()
         wake_get_beam(self.h, sim, xyz, lost)
+        self._order()
         return xyz, lost
 
     def diagnostics(self):

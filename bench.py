@@ -203,6 +203,51 @@ def config_dict(cfg, world, beam_steps):
             "parallelism": f"replicas x{world}"}
 
 
+def batched_leg(wake, torch, n_sims, nsteps, rank, flush, world):
+    """The batched sweep: n_sims simulations of uneven size, temperature and witness delay in
+    one handle (mixed form), nsteps beam steps by one wake_step call (one CUDA graph per step).
+    One untimed run (tile probes, graph capture), then one timed run from the initial beams."""
+    cfgs = synth.config_batch(n_sims=n_sims, n_steps=nsteps, seed=synth.SEED_BASE + 3 + 1000 * rank)
+    stream = torch.cuda.Stream()
+    pl = [synth.plasma_normals(c) for c in cfgs]
+    bm = [synth.beam_normals(c) for c in cfgs]
+    sim = wake.Simulations(cfgs, wake.WAKE_MIXED, stream)
+    with torch.cuda.stream(stream):
+        dpl = [None if a is None else torch.from_numpy(a).to("cuda", non_blocking=False) for a in pl]
+        dbm = [torch.from_numpy(a).to("cuda", non_blocking=False) for a in bm]
+        for i in range(n_sims):
+            wake.wake_load_plasma(sim.h, i, dpl[i])
+        times = []
+        for run in range(2):
+            for i in range(n_sims):
+                wake.wake_load_beam(sim.h, i, dbm[i])
+            flush.fill_(1)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            wake.wake_step(sim.h, nsteps)
+            ev[1].record(stream)
+            stream.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]))
+    st = [sim.status(i) for i in range(n_sims)]
+    tiles = {}
+    for i in range(n_sims):
+        t = "x".join(map(str, wake.wake_tile(sim.h, i)))
+        tiles[t] = tiles.get(t, 0) + 1
+    sim.close()
+    if any(x != wake.WAKE_OK for x in st):
+        raise RuntimeError(f"batched leg: simulation status {st}")
+    pushes = sum(c.nr * c.ppc * (c.nxi + 1) for c in cfgs) * nsteps
+    t = barrier_max(times[-1] / 1e3, world)
+    return {"value": world * pushes / t, "unit": "pushes/s", "ms_per_run": 1e3 * t, "sims": n_sims,
+            "beam_steps": nsteps, "plasma_pushes_per_run": pushes,
+            "beam_pushes_per_run": sum(c.n_beam for c in cfgs) * nsteps,
+            "beam_pushes_per_s": world * sum(c.n_beam for c in cfgs) * nsteps / t,
+            "tiles_nt_x_ppt": tiles, "first_run_ms": times[0],
+            "workload": "batched sweep: Nr in {128..1024}, Nxi in {512..4096} log-uniform, ppc 4, "
+                        "u_th ~ U[0,0.02], witness delay ~ U[3.5,5.5], 64k-256k beam particles each",
+            "dtype": "f32", "graph": "one batched step captured once, replayed per step"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -215,6 +260,8 @@ def main():
     ap.add_argument("--nr", type=int, default=0, help="override Nr (profiling a smaller case)")
     ap.add_argument("--nxi", type=int, default=0, help="override Nxi (profiling a smaller case)")
     ap.add_argument("--n-beam", type=int, default=0, help="override the beam size (profiling)")
+    ap.add_argument("--batch-sims", type=int, default=256, help="simulations of the batched leg (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=50, help="beam steps of the batched leg")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -307,6 +354,11 @@ def main():
     sim.close()
     e2e_s = barrier_max(sum(e2e_ms) / 1e3, world)
 
+    # --- batched sweep: uneven simulations in one handle, autotuned tiles, CUDA-graph steps ---
+    batched = None
+    if args.batch_sims > 0:
+        batched = batched_leg(wake, torch, args.batch_sims, args.batch_steps, rank, flush, world)
+
     # --- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -335,7 +387,7 @@ def main():
                 "fp64_gpu": fp64,
                 "e2e": {"value": world * pushes * e2e_steps / e2e_s, "unit": "pushes/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 5 * 8},
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "batched": batched,
                 "gpu_launches": KERNELS_PER_RUN * args.steps,
                 "witness": {"mean_gamma": diag[1], "rms_gamma": diag[2], "alive": diag[0]}}
         print(json.dumps(line), flush=True)

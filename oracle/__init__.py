@@ -80,6 +80,10 @@ def lib():
             L.orc_run.argtypes = [pp, i32, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pu8,
                                   pd, pd, pd, pd]
             L.orc_run.restype = i32
+            L.orc_run_w.argtypes = [pp, i32, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pd, pu8,
+                                    pd, pd, pd, pd, pd]
+            L.orc_run_w.restype = i32
+            L.orc_witness_obs.argtypes = [pp, pd, pd, pd, pu8, pd, pd]
             _lib = L
     return _lib
 
@@ -235,13 +239,45 @@ def diagnostics(cfg, beam):
     return out
 
 
-def run(cfg, plasma, beam, nsteps):
-    """nsteps beam steps (deposit, march, push) in place on beam; returns the last fields."""
+def run(cfg, plasma, beam, nsteps, wmul=None):
+    """nsteps beam steps (deposit, march, push) in place on beam; returns the last fields.
+    wmul: optional per-particle charge multipliers (a witness current profile)."""
     p = params(cfg)
     shape = (cfg.nxi + 1, cfg.nr + 1)
     out = {k: np.zeros(shape) for k in ("psi", "ez", "er", "bth")}
-    _check(lib().orc_run(C.byref(p), nsteps, _p(plasma["r0"]), _p(plasma["ur0"]), _p(plasma["l"]),
-                         _p(plasma["G0"]), _p(plasma["w"]),
-                         *[_p(beam[k]) for k in ("x", "y", "xi", "ux", "uy", "uz", "lost")],
-                         _p(out["psi"]), _p(out["ez"]), _p(out["er"]), _p(out["bth"])), "run")
+    wm = None if wmul is None else np.ascontiguousarray(wmul, dtype=np.float64)
+    _check(lib().orc_run_w(C.byref(p), nsteps, _p(plasma["r0"]), _p(plasma["ur0"]), _p(plasma["l"]),
+                           _p(plasma["G0"]), _p(plasma["w"]),
+                           *[_p(beam[k]) for k in ("x", "y", "xi", "ux", "uy", "uz", "lost")], _p(wm),
+                           _p(out["psi"]), _p(out["ez"]), _p(out["er"]), _p(out["bth"])), "run")
     return out
+
+
+def witness_obs(cfg, beam, wmul=None):
+    """Charge-weighted witness mean energy gain and rms energy spread (Sec. IV)."""
+    p = params(cfg)
+    out = np.zeros(2)
+    wm = None if wmul is None else np.ascontiguousarray(wmul, dtype=np.float64)
+    lib().orc_witness_obs(C.byref(p), _p(beam["ux"]), _p(beam["uy"]), _p(beam["uz"]), _p(beam["lost"]),
+                          _p(wm), _p(out))
+    return out
+
+
+def witness_objective(cfg, theta, profile, plasma_normals, beam_normals, nsteps):
+    """The witness observables after nsteps beam steps as a function of the parameters the
+    adjoint differentiates: theta = (n_w, xi_w - xi_d, sigma_zd, u_th) and the witness current
+    profile (multipliers of the witness charge in len(profile) bins of xi_w +- 3 sigma_zw,
+    by each particle's xi draw).  Returns (mean gain, rms spread)."""
+    import copy
+    c = copy.copy(cfg)
+    c.n_w, c.xi_w, c.sigma_zd, c.u_th = float(theta[0]), c.xi_d + float(theta[1]), float(theta[2]), float(theta[3])
+    pl = plasma_init(c, plasma_normals)
+    bm = beam_init(c, beam_normals)
+    wm = np.ones(c.n_beam)
+    nb = len(profile)
+    if nb > 0:
+        z = beam_normals[4, c.n_drive:]
+        b = np.clip(np.floor((z + 3.0) * nb / 6.0).astype(np.int64), 0, nb - 1)
+        wm[c.n_drive:] = np.asarray(profile, dtype=np.float64)[b]
+    run(c, pl, bm, nsteps, wm)
+    return witness_obs(c, bm, wm)

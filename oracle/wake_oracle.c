@@ -604,9 +604,17 @@ void orc_beam_init(const orc_params *p, const double *normals, double *x, double
 }
 
 /* Beam density on the (nxi+1) x (nr+1) nodes: bilinear hats in (r, xi) divided by the hats'
- * volumes (V_i in r; dxi, or dxi/2 at the two end slices, in xi).  Lost particles skipped. */
+ * volumes (V_i in r; dxi, or dxi/2 at the two end slices, in xi).  Lost particles skipped.
+ * wmul (NULL: all 1) multiplies particle j's charge: a witness current profile other than
+ * the Gaussian of Eq. 12 (Sec. IV studies the witness current). */
+void orc_beam_deposit_w(const orc_params *p, const double *x, const double *y, const double *xi,
+                        const uint8_t *lost, const double *wmul, double *nb);
 void orc_beam_deposit(const orc_params *p, const double *x, const double *y, const double *xi,
                       const uint8_t *lost, double *nb) {
+  orc_beam_deposit_w(p, x, y, xi, lost, NULL, nb);
+}
+void orc_beam_deposit_w(const orc_params *p, const double *x, const double *y, const double *xi,
+                        const uint8_t *lost, const double *wmul, double *nb) {
   const int nr = p->nr, nxi = p->nxi, n1 = nr + 1;
   const double dr = p->rmax / nr, dxi = p->ximax / nxi;
   double wd, ww;
@@ -614,7 +622,7 @@ void orc_beam_deposit(const orc_params *p, const double *x, const double *y, con
   memset(nb, 0, sizeof(double) * (size_t)(nxi + 1) * n1);
   for (int64_t j = 0; j < p->n_beam; ++j) {
     if (lost[j]) continue;
-    const double wj = j < p->n_drive ? wd : ww;
+    const double wj = (j < p->n_drive ? wd : ww) * (wmul ? wmul[j] : 1.0);
     const double r = sqrt(x[j] * x[j] + y[j] * y[j]);
     int c, k;
     double f, g;
@@ -704,13 +712,48 @@ void orc_diagnostics(const orc_params *p, const double *ux, const double *uy, co
   out[4] = nd > 0 ? ref + sd / nd : 0.0;
 }
 
+/* Witness observables weighted by charge (Sec. IV: mean energy gain and energy spread of the
+ * witness): out[0] = sum w g / sum w, out[1] = sqrt(sum w (g - out[0])^2 / sum w) over the
+ * surviving witness particles, g = gamma - gamma_b, w = wmul[j] (NULL: all 1). */
+void orc_witness_obs(const orc_params *p, const double *ux, const double *uy, const double *uz,
+                     const uint8_t *lost, const double *wmul, double *out) {
+  double W = 0.0, S1 = 0.0;
+  for (int64_t j = p->n_drive; j < p->n_beam; ++j) {
+    if (lost[j]) continue;
+    const double w = wmul ? wmul[j] : 1.0;
+    W += w;
+    S1 += w * (sqrt(1.0 + ux[j] * ux[j] + uy[j] * uy[j] + uz[j] * uz[j]) - p->gamma_b);
+  }
+  const double M = W > 0.0 ? S1 / W : 0.0;
+  double S2 = 0.0;
+  for (int64_t j = p->n_drive; j < p->n_beam; ++j) {
+    if (lost[j]) continue;
+    const double w = wmul ? wmul[j] : 1.0;
+    const double d = sqrt(1.0 + ux[j] * ux[j] + uy[j] * uy[j] + uz[j] * uz[j]) - p->gamma_b - M;
+    S2 += w * d * d;
+  }
+  out[0] = M;
+  out[1] = W > 0.0 ? sqrt(S2 / W) : 0.0;
+}
+
 /* A full run (Sec. II.A, last paragraph): for each beam step, deposit the beam, march the
  * plasma with the beam frozen, then push the beam once.  Fields of the last march are left
- * in er, ez, bth, psi (any may be NULL). */
+ * in er, ez, bth, psi (any may be NULL).  orc_run_w takes per-particle charge multipliers
+ * (orc_beam_deposit_w). */
+int orc_run_w(const orc_params *p, int nsteps, const double *r0, const double *ur0,
+              const double *l, const double *G0, const double *w, double *x, double *y,
+              double *xi, double *ux, double *uy, double *uz, uint8_t *lost, const double *wmul,
+              double *psi, double *ez, double *er, double *bth);
 int orc_run(const orc_params *p, int nsteps, const double *r0, const double *ur0,
             const double *l, const double *G0, const double *w, double *x, double *y,
             double *xi, double *ux, double *uy, double *uz, uint8_t *lost, double *psi,
             double *ez, double *er, double *bth) {
+  return orc_run_w(p, nsteps, r0, ur0, l, G0, w, x, y, xi, ux, uy, uz, lost, NULL, psi, ez, er, bth);
+}
+int orc_run_w(const orc_params *p, int nsteps, const double *r0, const double *ur0,
+              const double *l, const double *G0, const double *w, double *x, double *y,
+              double *xi, double *ux, double *uy, double *uz, uint8_t *lost, const double *wmul,
+              double *psi, double *ez, double *er, double *bth) {
   const size_t ng = (size_t)(p->nxi + 1) * (p->nr + 1);
   double *nb = (double *)malloc(sizeof(double) * ng);
   double *fer = (double *)malloc(sizeof(double) * ng);
@@ -722,7 +765,7 @@ int orc_run(const orc_params *p, int nsteps, const double *r0, const double *ur0
     goto done;
   }
   for (int s = 0; s < nsteps; ++s) {
-    orc_beam_deposit(p, x, y, xi, lost, nb);
+    orc_beam_deposit_w(p, x, y, xi, lost, wmul, nb);
     status = orc_march(p, r0, ur0, l, G0, w, nb, psi, fez, fer, fbt, NULL);
     if (status != ORC_OK) goto done;
     orc_beam_push(p, x, y, xi, ux, uy, uz, lost, fer, fez, fbt);

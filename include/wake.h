@@ -197,6 +197,41 @@ int wake_status(wake_sim *s, int sim);
 int wake_beam_deposit_noalloc(const wake_params *p, const double *xyz, const uint8_t *lost, void *stream,
                               double *nb);
 
+/*
+ * The adjoint form: gradients of the witness bunch's observables (Sec. IV: mean energy gain
+ * <gamma - gamma_b> and rms energy spread over the surviving witness particles, weighted by
+ * their charge) after nsteps beam steps, with respect to
+ *   theta[0] = n_w          witness peak density of Eq. 12 (its charge is proportional)
+ *   theta[1] = xi_w - xi_d  witness delay
+ *   theta[2] = sigma_zd     drive bunch length (its peak density n_d held fixed)
+ *   theta[3] = u_th         plasma temperature (Sec. II.A Maxwellian)
+ * and nbins multipliers of the witness current profile: witness macroparticle j carries
+ * weight n_w-bunch weight x profile[b], b its bin of xi_w +- 3 sigma_zw (from its initial
+ * draw).  FP64 throughout; the march is plain (no tiles, one CTA) and is reversed with
+ * checkpoints every ~sqrt(Nxi + 1) slices.  The paper differentiates nothing: this form
+ * serves the parameter studies of its Sec. IV.
+ *
+ * wake_adjoint_init: p gives the grid, box, bunches (n_d, sigma_r, sigma_zw, xi_d, gamma_b,
+ * eps_n, ds, n_beam, n_drive; the theta entries of p are ignored).  Needs nr <= 256, an even
+ * ppc, 0 < n_drive < n_beam, 0 <= nbins <= 1024.  Allocates everything (beam states, densities
+ * and fields of every step: about (nsteps + 1) x 49 x n_beam + nsteps x 32 x (Nxi+1)(Nr+1)
+ * bytes).
+ * wake_adjoint_forward: theta (host, 4), profile (host, nbins; NULL if nbins == 0),
+ * plasma_normals (device, nr*ppc*3 mirrored pairs as wake_load_plasma takes them) and
+ * beam_normals (device, 5 x n_beam as wake_load_beam takes them; both must stay valid until
+ * the next forward) -> obs (host, 2): mean gain, rms spread.  Synchronous.
+ * wake_adjoint_backward: dobs (host, 2) = dL/dobs -> grad (host, 4 + nbins) = dL/dtheta,
+ * dL/dprofile, for the last forward.  Synchronous.
+ * Errors: WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENUMERIC, WAKE_EESCAPE, WAKE_ESTATE (no
+ * surviving witness, or backward before forward).
+ */
+typedef struct wake_adj wake_adj;
+int wake_adjoint_init(const wake_params *p, int nsteps, int nbins, void *stream, wake_adj **out);
+int wake_adjoint_forward(wake_adj *a, const double *theta, const double *profile, const double *plasma_normals,
+                         const double *beam_normals, double *obs);
+int wake_adjoint_backward(wake_adj *a, const double *dobs, double *grad);
+void wake_adjoint_destroy(wake_adj *a);
+
 /* Thread-local message describing the last failed call (never NULL). */
 const char *wake_last_error(void);
 

@@ -19,7 +19,8 @@ WAKE_FP64, WAKE_MIXED = 0, 1
 # every entry point the header declares
 EXPORTS = ["wake_init", "wake_load_plasma", "wake_load_beam", "wake_beam_deposit", "wake_plasma_march",
            "wake_beam_push", "wake_step", "wake_tile", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
-           "wake_diagnostics", "wake_status", "wake_beam_deposit_noalloc", "wake_last_error", "wake_destroy"]
+           "wake_diagnostics", "wake_status", "wake_beam_deposit_noalloc", "wake_adjoint_init",
+           "wake_adjoint_forward", "wake_adjoint_backward", "wake_adjoint_destroy", "wake_last_error", "wake_destroy"]
 WAKE_NOALLOC_MAX_NODES = 524288
 
 
@@ -63,12 +64,17 @@ def lib():
         L.wake_diagnostics.argtypes = [vp, pd]
         L.wake_status.argtypes = [vp, i32]
         L.wake_beam_deposit_noalloc.argtypes = [C.POINTER(wake_params), vp, vp, vp, vp]
+        L.wake_adjoint_init.argtypes = [C.POINTER(wake_params), i32, i32, vp, C.POINTER(vp)]
+        L.wake_adjoint_forward.argtypes = [vp, pd, pd, vp, vp, pd]
+        L.wake_adjoint_backward.argtypes = [vp, pd, pd]
+        L.wake_adjoint_destroy.argtypes = [vp]
+        L.wake_adjoint_destroy.restype = None
         L.wake_last_error.restype = C.c_char_p
         L.wake_last_error.argtypes = []
         L.wake_destroy.argtypes = [vp]
         L.wake_destroy.restype = None
         for n in EXPORTS:
-            if n not in ("wake_last_error", "wake_destroy"):
+            if n not in ("wake_last_error", "wake_destroy", "wake_adjoint_destroy"):
                 getattr(L, n).restype = i32
         _lib = L
     return _lib
@@ -243,3 +249,73 @@ class Simulations:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ---------------------------------------------------------------------------------------
+# the adjoint form
+# ---------------------------------------------------------------------------------------
+
+def _dbuf(vals):
+    arr = (C.c_double * max(1, len(vals)))(*[float(v) for v in vals])
+    return arr
+
+
+class Adjoint:
+    """Owner of a wake_adjoint handle: the witness observables (mean energy gain, rms energy
+    spread) after nsteps beam steps and their gradient with respect to theta = (n_w,
+    xi_w - xi_d, sigma_zd, u_th) and nbins witness-profile multipliers (include/wake.h)."""
+
+    def __init__(self, cfg, nsteps, nbins, plasma_normals, beam_normals, stream=None):
+        import torch
+        self.torch = torch
+        self.nbins = nbins
+        self.p = params_of(cfg, WAKE_FP64)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        _check(lib().wake_adjoint_init(C.byref(self.p), nsteps, nbins, C.c_void_p(st.cuda_stream), C.byref(h)))
+        self.h = h
+        self.nm_p = plasma_normals  # device tensors kept alive for the handle's backward
+        self.nm_b = beam_normals
+
+    def forward(self, theta, profile):
+        obs = (C.c_double * 2)()
+        prof = _dbuf(profile)
+        _check(lib().wake_adjoint_forward(self.h, _dbuf(theta), prof, _ptr(self.nm_p), _ptr(self.nm_b), obs))
+        return [obs[0], obs[1]]
+
+    def backward(self, dobs):
+        g = (C.c_double * (4 + max(1, self.nbins)))()
+        _check(lib().wake_adjoint_backward(self.h, _dbuf(dobs), g))
+        return [g[i] for i in range(4 + self.nbins)]
+
+    def close(self):
+        if self.h is not None:
+            lib().wake_adjoint_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def witness_observables(adj, theta, profile):
+    """torch.autograd entry: (mean gain, rms spread) of the witness as a 2-vector, from theta
+    (4,) and profile (nbins,) float64 tensors; backward runs the library's adjoint."""
+    import torch
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, th, pr):
+            obs = adj.forward(th.detach().cpu().tolist(), pr.detach().cpu().tolist())
+            return torch.tensor(obs, dtype=torch.float64, device=th.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            g = adj.backward(gout.detach().cpu().tolist())
+            dev = gout.device
+            return (torch.tensor(g[:4], dtype=torch.float64, device=dev),
+                    torch.tensor(g[4:], dtype=torch.float64, device=dev))
+
+    return _Fn.apply(theta, profile)

@@ -1,0 +1,82 @@
+"""The adjoint form through the C ABI (wake_adjoint_*) and its torch.autograd binding: the
+CUDA gradient equals the host build of the same arithmetic and central finite differences
+of the FP64 oracle."""
+import numpy as np
+import pytest
+
+import adjoint_host
+import oracle
+import synth
+from test_adjoint import adjoint_case, assert_grad_close, oracle_fd, theta_of
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wk():
+    import torch
+    from paper_1411_3246_gb300 import build, wake
+    build.build()
+    assert torch.cuda.is_available()
+    return wake
+
+
+def _adj(wk, cfg, nsteps, nbins):
+    import torch
+    nm_p = torch.from_numpy(synth.plasma_normals(cfg)).cuda()
+    nm_b = torch.from_numpy(synth.beam_normals(cfg)).cuda()
+    return wk.Adjoint(cfg, nsteps, nbins, nm_p, nm_b)
+
+
+def test_gpu_adjoint_equals_host_build(wk):
+    cfg = adjoint_case(nr=32, nxi=96, n_beam=4096)
+    theta = theta_of(cfg)
+    prof = np.linspace(0.7, 1.3, 8)
+    nm_p, nm_b = synth.plasma_normals(cfg), synth.beam_normals(cfg)
+    for dobs in ((1.0, 0.0), (0.0, 1.0)):
+        o_h, g_h = adjoint_host.gradient(cfg, 4, theta, prof, nm_p, nm_b, np.array(dobs))
+        with _adj(wk, cfg, 4, 8) as a:
+            o = np.array(a.forward(theta, prof))
+            g = np.array(a.backward(dobs))
+        np.testing.assert_allclose(o, o_h, rtol=1e-10)
+        assert np.abs(g - g_h).max() <= 1e-8 * np.abs(g_h).max(), (g, g_h)
+
+
+def test_gpu_adjoint_matches_oracle_finite_differences(wk):
+    cfg = adjoint_case()
+    theta, prof = theta_of(cfg), np.ones(4)
+    nm_p, nm_b = synth.plasma_normals(cfg), synth.beam_normals(cfg)
+    dobs = np.array([1.0, -0.5])
+    with _adj(wk, cfg, 3, 4) as a:
+        obs = np.array(a.forward(theta, prof))
+        g = np.array(a.backward(dobs))
+    np.testing.assert_allclose(obs, oracle.witness_objective(cfg, theta, prof, nm_p, nm_b, 3), rtol=1e-9)
+    assert_grad_close(g, oracle_fd(cfg, 3, theta, prof, nm_p, nm_b, dobs))
+
+
+def test_autograd_function_gives_the_adjoint_gradient(wk):
+    """The autograd binding returns the adjoint's gradient, which central differences of the
+    library's own forward confirm (a case with few beam particles, so that the h-shift moves
+    no particle across a cell edge, where the linear hats have a kink)."""
+    import torch
+    cfg = adjoint_case(nr=16, nxi=40, n_beam=512)
+    with _adj(wk, cfg, 3, 6) as a:
+        th = torch.tensor(theta_of(cfg), dtype=torch.float64, device="cuda", requires_grad=True)
+        pr = torch.ones(6, dtype=torch.float64, device="cuda", requires_grad=True)
+        obs = wk.witness_observables(a, th, pr)
+        loss = obs[0] - 0.5 * obs[1]
+        loss.backward()
+        g = a.backward([1.0, -0.5])
+        # finite differences of the library's own forward
+        x0 = np.concatenate([theta_of(cfg), np.ones(6)])
+        fd = np.zeros_like(x0)
+        for i in range(len(x0)):
+            h = 1e-4 * max(abs(x0[i]), 1e-3)
+            xp, xm = x0.copy(), x0.copy()
+            xp[i] += h
+            xm[i] -= h
+            op, om = np.array(a.forward(xp[:4], xp[4:])), np.array(a.forward(xm[:4], xm[4:]))
+            fd[i] = ((op[0] - 0.5 * op[1]) - (om[0] - 0.5 * om[1])) / (2 * h)
+    got = np.concatenate([th.grad.cpu().numpy(), pr.grad.cpu().numpy()])
+    np.testing.assert_allclose(got, g, rtol=1e-12)
+    assert_grad_close(got, fd)

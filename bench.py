@@ -248,6 +248,45 @@ def batched_leg(wake, torch, n_sims, nsteps, rank, flush, world):
             "dtype": "f32", "graph": "one batched step captured once, replayed per step"}
 
 
+def adjoint_case(nsteps, rank):
+    """The differentiation workload: the linear-driver grid (Nr=128 over 6, 4 rings/cell) at
+    Nxi=1024 over 10, two bunches (witness at the batched sweep's first delay), 262,144 beam
+    particles, u_th = 0.005, a 64-bin witness profile."""
+    cfg = synth.config_batch(n_sims=1, seed=synth.SEED_BASE + 4 + 1000 * rank)[0]
+    cfg.nr, cfg.nxi, cfg.ppc = 128, 1024, 4
+    cfg = synth.two_bunch(cfg, 0.3, cfg.xi_w - cfg.xi_d, 262144)
+    cfg.u_th = 0.005
+    cfg.n_steps = nsteps
+    return cfg
+
+
+def adjoint_leg(wake, torch, nsteps, rank, world):
+    """One forward (observables) and one backward (gradient of both observables' sum) of the
+    adjoint form on the differentiation workload, timed on the host around the synchronous
+    calls."""
+    cfg = adjoint_case(nsteps, rank)
+    nbins = 64
+    nm_p = torch.from_numpy(synth.plasma_normals(cfg)).cuda()
+    nm_b = torch.from_numpy(synth.beam_normals(cfg)).cuda()
+    theta = [cfg.n_w, cfg.xi_w - cfg.xi_d, cfg.sigma_zd, cfg.u_th]
+    torch.cuda.synchronize()
+    with wake.Adjoint(cfg, nsteps, nbins, nm_p, nm_b) as a:
+        t0 = time.perf_counter()
+        obs = a.forward(theta, [1.0] * nbins)
+        t1 = time.perf_counter()
+        g = a.backward([1.0, 1.0])
+        t2 = time.perf_counter()
+    fwd = barrier_max(t1 - t0, world)
+    bwd = barrier_max(t2 - t1, world)
+    pushes = cfg.nr * cfg.ppc * (cfg.nxi + 1) * nsteps
+    return {"adjoint_over_forward": bwd / fwd, "forward_s": fwd, "backward_s": bwd,
+            "forward_plasma_pushes_per_s": world * pushes / fwd, "dtype": "f64",
+            "workload": f"Nr={cfg.nr} x Nxi={cfg.nxi}, {cfg.ppc} rings/cell, {cfg.n_beam} beam particles, "
+                        f"{nsteps} beam steps, gradients w.r.t. n_w, delay, sigma_zd, u_th and {nbins} profile bins",
+            "observables": obs, "grad_scalars": g[:4],
+            "checkpoints": "ring state every round(sqrt(Nxi+1)) slices; beam, density and fields of every step"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -262,6 +301,7 @@ def main():
     ap.add_argument("--n-beam", type=int, default=0, help="override the beam size (profiling)")
     ap.add_argument("--batch-sims", type=int, default=256, help="simulations of the batched leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=50, help="beam steps of the batched leg")
+    ap.add_argument("--adjoint-steps", type=int, default=100, help="beam steps of the adjoint leg (0: skip)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -359,6 +399,11 @@ def main():
     if args.batch_sims > 0:
         batched = batched_leg(wake, torch, args.batch_sims, args.batch_steps, rank, flush, world)
 
+    # --- adjoint form: gradient of the witness observables, backward / forward time ---
+    adjoint = None
+    if args.adjoint_steps > 0:
+        adjoint = adjoint_leg(wake, torch, args.adjoint_steps, rank, world)
+
     # --- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -387,7 +432,7 @@ def main():
                 "fp64_gpu": fp64,
                 "e2e": {"value": world * pushes * e2e_steps / e2e_s, "unit": "pushes/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 5 * 8},
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "batched": batched,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "batched": batched, "adjoint": adjoint,
                 "gpu_launches": KERNELS_PER_RUN * args.steps,
                 "witness": {"mean_gamma": diag[1], "rms_gamma": diag[2], "alive": diag[0]}}
         print(json.dumps(line), flush=True)

@@ -69,8 +69,9 @@ typedef struct wake_sim wake_sim; /* opaque handle: n_sims independent simulatio
  * CUDA stream `stream` (a cudaStream_t; NULL = legacy default stream).  Allocates all
  * scratch: plasma rings, beam state, the beam-density and field grids.  A simulation with
  * n_beam == 0 gets the frozen analytic driver of Eq. 12 on its nodes.
- * Errors: WAKE_EINVAL (sizes out of range: 2 <= nr <= 1024, 2 <= nxi, 1 <= ppc,
- * nr*ppc <= 8192, precision mismatch), WAKE_ENOMEM, WAKE_ECUDA.
+ * Errors: WAKE_EINVAL (sizes out of range: 2 <= nxi, 1 <= ppc; FP64 2 <= nr <= 1024 and
+ * nr*ppc <= 8192; mixed 2 <= nr <= 2048 and nr*ppc <= 65536; precision mismatch),
+ * WAKE_ENOMEM, WAKE_ECUDA.
  */
 int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out);
 
@@ -130,8 +131,11 @@ int wake_step(wake_sim *s, int nsteps);
  * several simulations the first march chooses each simulation's tile by timing the compiled
  * candidates on a short probe march (synchronous: make that first march before any stream
  * capture); the environment variable WAKE_TILE_NT (128, 256 or 512), read by wake_init,
- * restricts the choice to one width.  Before the first march both are 0.  Instrumentation
- * and tuning: the paper has no counterpart.
+ * restricts the choice to one width.  A mixed simulation too large for any tile (more than
+ * 768 radial cells with more than 4096 rings, up to nr = 2048 and 65,536 rings) runs in the
+ * wide form, which keeps its rings in a global buffer and processes them in chunks of
+ * 512 x 8 (nt = 512, ppt = 8 here); WAKE_TILE_NT=-1 forces the wide form.  Before the first
+ * march both are 0.  Instrumentation and tuning: the paper has no counterpart.
  */
 int wake_tile(wake_sim *s, int sim, int *nt, int *ppt);
 

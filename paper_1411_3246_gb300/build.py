@@ -10,9 +10,10 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwake.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-# the mixed-precision march uses approximate FP32 divide and square root (a few ulp) and
-# flushes denormals; every other translation unit keeps IEEE division and sqrt
-EXTRA = {"march_mixed.cu": ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]}
+# the mixed-precision marches use approximate FP32 divide and square root (a few ulp) and
+# flush denormals; every other translation unit keeps IEEE division and sqrt
+_FAST = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
+EXTRA = {"march_mixed.cu": _FAST, "march_mixed_small.cu": _FAST, "march_wide.cu": _FAST}
 
 
 def sources():

@@ -116,6 +116,7 @@ struct PolFP64 {
   static constexpr int kSortEvery = 0;
   static constexpr bool kSmemRings = false;
   static constexpr bool kTables = true;
+  static constexpr int kScanE = 3;  // nodes per thread in the block scans: n1 <= kScanE * NT
 };
 struct PolMixed {
   using R = float;
@@ -127,6 +128,22 @@ struct PolMixed {
   static constexpr int kSortEvery = 2;
   static constexpr bool kSmemRings = true;
   static constexpr bool kTables = false;
+  static constexpr int kScanE = 3;
+};
+// The mixed arithmetic for boxes too large for one CTA's shared memory to hold the rings
+// (up to 2048 radial cells and 65,536 rings): rings in global memory, processed in chunks,
+// not re-sorted; block scans of up to 5 nodes per thread.
+struct PolWide {
+  using R = float;
+  using Acc = float;
+  using Q = long long;
+  using G = float;
+  using W = FF;
+  static constexpr int NT = 512;
+  static constexpr int kSortEvery = 0;
+  static constexpr bool kSmemRings = false;
+  static constexpr bool kTables = false;
+  static constexpr int kScanE = 5;
 };
 
 // Ring slot arrays: cell index, offset in the cell, u_r, the constants l_z, Gamma_0, w, and
@@ -424,7 +441,7 @@ __device__ __forceinline__ void solve_psi(MarchSmem<Pol> &sm, const NodeGeo<Pol>
   using R = typename Pol::R;
   using W = typename Pol::W;
   const int nr = geo.nr, n1 = nr + 1;
-  block_scan_fused<NT, 3, false, W>(
+  block_scan_fused<NT, Pol::kScanE, false, W>(
       n1, wtot, [&](int m) { return q_to_wide<typename Pol::Q, W>(sm.rho[m] - sm.rho0[m]); },
       [&](int m, W incl) {
         R dp = (R)0;
@@ -435,7 +452,7 @@ __device__ __forceinline__ void solve_psi(MarchSmem<Pol> &sm, const NodeGeo<Pol>
         sm.dpsi[m] = dp;
       });
   const R hdr = (R)0.5 * geo.dr;
-  block_scan_fused<NT, 3, true, W>(
+  block_scan_fused<NT, Pol::kScanE, true, W>(
       n1, wtot, [&](int m) { return wide_of<W, R>(m < nr ? hdr * (sm.dpsi[m] + sm.dpsi[m + 1]) : (R)0); },
       [&](int m, W incl) { sm.psi[m] = -(R)wide_value(incl); });
 }
@@ -469,7 +486,7 @@ __device__ __forceinline__ void solve_fields(MarchSmem<Pol> &sm, const NodeGeo<P
   }
   __syncthreads();
   // E_z: inward trapezoid sum from E_z(R) = 0 (in place over the d_xi psi' values)
-  block_scan_fused<NT, 3, true, W>(
+  block_scan_fused<NT, Pol::kScanE, true, W>(
       n1, wtot, [&](int m) { return wide_of<W, R>(m < nr ? hdr * (sm.ez[m] + sm.ez[m + 1]) : (R)0); },
       [&](int m, W incl) { sm.ez[m] = -(R)wide_value(incl); });  // inputs are all read first
   // rows q = 0..nr-1 (node i = q + 1): central differences, a half cell at the wall
@@ -657,6 +674,9 @@ struct ChargeWin<PolMixed> {
   }
   __device__ __forceinline__ long long node(int a) const { return ff_to_q(n[a]); }
 };
+
+template <>
+struct ChargeWin<PolWide> : ChargeWin<PolMixed> {};
 
 __device__ __forceinline__ void q_atomic_add(double *p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void q_atomic_add(long long *p, long long v) {

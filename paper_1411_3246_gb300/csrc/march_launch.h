@@ -15,6 +15,7 @@ constexpr size_t kMaxSmemPerCta = 227 * 1024;
 // A compiled march tile: NT threads per CTA, PPT rings per thread (march_tiles.cuh).
 struct TileFns {
   int nt, ppt;
+  bool wide;  // rings in a global buffer, in chunks of nt x ppt (march_wide.cuh)
   // one CTA per entry of order[0..count-1] (descriptor d[order[i]]), shared memory for n1 nodes
   cudaError_t (*launch)(const SimDesc *d, const int *order, int count, int n1, cudaStream_t s);
   cudaError_t (*prepare)(int n1);  // shared-memory limit for n1 nodes (before any capture)
@@ -26,6 +27,13 @@ bool march_tile(int precision_fp64, int nt, int ppt, TileFns *out);
 bool march_tile_fp64(int nt, int ppt, TileFns *out);
 bool march_tile_mixed512(int nt, int ppt, TileFns *out);
 bool march_tile_mixed_small(int nt, int ppt, TileFns *out);
+// The wide mixed march (march_wide.cuh) and its ring buffer for np rings.
+TileFns march_tile_wide();
+size_t wide_ring_bytes(int np);
+// Pipelined steps in the wide form: shared memory fits, co-resident CTAs, launch.
+int step_wide_max_ctas(int n1);
+size_t step_wide_window_bytes(int n1);
+cudaError_t launch_step_wide(const PipeArgs &a, int ctas, cudaStream_t stream);
 
 // Global-memory ring slot storage one simulation needs (0 when the rings live in shared
 // memory).

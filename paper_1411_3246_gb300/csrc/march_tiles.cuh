@@ -54,7 +54,7 @@ static int tile_occupancy(int n1) {
 
 template <class Pol, int NT, int PPT>
 static TileFns tile_fns() {
-  return TileFns{NT, PPT, &tile_launch<Pol, NT, PPT>, &tile_prepare<Pol, NT, PPT>, &tile_smem<Pol, NT, PPT>,
+  return TileFns{NT, PPT, false, &tile_launch<Pol, NT, PPT>, &tile_prepare<Pol, NT, PPT>, &tile_smem<Pol, NT, PPT>,
                  &tile_occupancy<Pol, NT, PPT>};
 }
 

@@ -1,0 +1,80 @@
+// The wide form of the xi-march (march_wide.cuh): plain launches (one CTA per simulation) and
+// pipelined beam steps with the field window in global memory.
+#include "march_launch.h"
+#include "march_wide.cuh"
+#include "pipeline.cuh"
+
+#include <mutex>
+
+namespace wake {
+
+namespace {
+
+constexpr int kWideNT = PolWide::NT, kWidePPT = 8;
+
+cudaError_t wide_prepare(int n1) {
+  static std::mutex mu;
+  static size_t set = 0;
+  const size_t smem = MarchSmem<PolWide>::bytes(n1, kWideNT * kWidePPT);
+  std::lock_guard<std::mutex> lk(mu);
+  if (smem <= set) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(march_wide_kernel<PolWide, kWideNT, kWidePPT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) set = smem;
+  return e;
+}
+cudaError_t wide_launch(const SimDesc *d, const int *order, int count, int n1, cudaStream_t s) {
+  cudaError_t e = wide_prepare(n1);
+  if (e != cudaSuccess) return e;
+  march_wide_kernel<PolWide, kWideNT, kWidePPT>
+      <<<count, kWideNT, MarchSmem<PolWide>::bytes(n1, kWideNT * kWidePPT), s>>>(d, order);
+  return cudaGetLastError();
+}
+size_t wide_smem(int n1) { return MarchSmem<PolWide>::bytes(n1, kWideNT * kWidePPT); }
+int wide_occupancy(int n1) {
+  const size_t smem = wide_smem(n1);
+  if (smem > kMaxSmemPerCta || wide_prepare(n1) != cudaSuccess) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, march_wide_kernel<PolWide, kWideNT, kWidePPT>, kWideNT,
+                                                    smem) != cudaSuccess)
+    return 0;
+  return per_sm;
+}
+
+size_t step_wide_smem(int n1) {
+  return ((MarchSmem<PolWide>::bytes(n1, kWideNT * kWidePPT) + 63) & ~(size_t)63) + 64;
+}
+
+}  // namespace
+
+TileFns march_tile_wide() {
+  return TileFns{kWideNT, kWidePPT, true, &wide_launch, &wide_prepare, &wide_smem, &wide_occupancy};
+}
+
+size_t wide_ring_bytes(int np) { return WideRings<float>::bytes(wide_slots<kWideNT, kWidePPT>(np)); }
+
+size_t step_wide_window_bytes(int n1) { return sizeof(float) * 12 * (size_t)n1; }
+
+int step_wide_max_ctas(int n1) {
+  auto kern = step_wide_kernel<PolWide, kWideNT, kWidePPT>;
+  const size_t smem = step_wide_smem(n1);
+  if (smem > kMaxSmemPerCta) return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWideNT, smem) != cudaSuccess) return 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * sms;
+}
+
+cudaError_t launch_step_wide(const PipeArgs &a, int ctas, cudaStream_t stream) {
+  auto kern = step_wide_kernel<PolWide, kWideNT, kWidePPT>;
+  const size_t smem = step_wide_smem(a.d.nr + 1);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  PipeArgs arg = a;
+  void *args[] = {&arg};
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(ctas), dim3(kWideNT), args, smem, stream);
+}
+
+}  // namespace wake

@@ -17,6 +17,7 @@
 
 #include "beam.cuh"
 #include "march.cuh"
+#include "march_wide.cuh"
 
 namespace wake {
 
@@ -36,8 +37,10 @@ struct PipeArgs {
   const int *bin_start;
   double wd, ww, ds;
   long long spin_limit;   // polls before a wait gives up
-  void *ring_bufs;        // per-CTA ring slot storage (FP64 form)
+  void *ring_bufs;        // per-CTA ring slot storage (FP64 and wide forms)
   size_t ring_stride;
+  void *win_bufs;         // per-CTA field windows in global memory (wide form)
+  size_t win_stride;
 };
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -202,6 +205,30 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(PipeArgs a) {
     SimDesc d = a.d;
     if (!Pol::kSmemRings) d.ring_buf = (unsigned char *)a.ring_bufs + (size_t)blockIdx.x * a.ring_stride;
     march_body<Pol, NT, PPT>(d, smem_raw, hk);
+    __syncthreads();
+    if (ctl[0]) break;
+  }
+}
+
+// The wide form: rings and the four-slice field window in per-CTA global buffers.
+template <class Pol, int NT, int PPT>
+__global__ void __launch_bounds__(NT, 1) step_wide_kernel(PipeArgs a) {
+  using R = typename Pol::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n1 = a.d.nr + 1;
+  const size_t base = (MarchSmem<Pol>::bytes(n1, NT * PPT) + 63) & ~(size_t)63;
+  int *ctl = (int *)(smem_raw + base);
+  R *win = (R *)((unsigned char *)a.win_bufs + (size_t)blockIdx.x * a.win_stride);
+  for (int t = blockIdx.x; t < a.nsteps; t += gridDim.x) {
+    if (threadIdx.x == 0) {
+      ctl[0] = 0;
+      ctl[1] = 0;
+    }
+    __syncthreads();
+    PipeHooks<Pol, NT> hk{a, t, win, ctl, n1, a.d.nr, a.d.nxi, a.d.dr, a.d.dxi, a.d.rmax, a.d.ximax};
+    SimDesc d = a.d;
+    d.ring_buf = (unsigned char *)a.ring_bufs + (size_t)blockIdx.x * a.ring_stride;
+    march_body_wide<Pol, NT, PPT>(d, smem_raw, hk);
     __syncthreads();
     if (ctl[0]) break;
   }

@@ -57,9 +57,16 @@ struct Sim {
   size_t pring_bytes = 0;
   int *status = nullptr;
   bool plasma = false, beam = false, marched = false;
+  bool wide = false;  // marched by the wide form (rings in a global buffer)
 };
 
 size_t gsize(int precision) { return precision == WAKE_FP64 ? sizeof(double) : sizeof(float); }
+
+// Global ring storage a simulation's march needs: FP64 form and wide form only.
+size_t sim_ring_bytes(int precision, const Sim &s) {
+  if (s.wide) return wide_ring_bytes(s.np);
+  return ring_buf_bytes(precision == WAKE_FP64);
+}
 
 // x-extent of a batched launch (blockIdx.y is the simulation): up to 64 blocks of 256 per
 // simulation, each striding over that simulation's particles or nodes.
@@ -121,9 +128,11 @@ void free_sim(Sim &s) {
 int check_params(const wake_params &p, int prec0) {
   if (p.precision != WAKE_FP64 && p.precision != WAKE_MIXED) return fail(WAKE_EINVAL, "precision must be WAKE_FP64 or WAKE_MIXED");
   if (p.precision != prec0) return fail(WAKE_EINVAL, "all simulations of one handle must share the precision");
-  if (p.nr < 2 || p.nr > 1024) return fail(WAKE_EINVAL, "nr must be in [2, 1024]");
+  const bool fp64 = p.precision == WAKE_FP64;
+  if (p.nr < 2 || p.nr > (fp64 ? 1024 : 2048)) return fail(WAKE_EINVAL, "nr must be in [2, 1024] (FP64) or [2, 2048] (mixed)");
   if (p.nxi < 2 || p.nxi > (1 << 20)) return fail(WAKE_EINVAL, "nxi must be in [2, 2^20]");
-  if (p.ppc < 1 || (int64_t)p.nr * p.ppc > 8192) return fail(WAKE_EINVAL, "need ppc >= 1 and nr*ppc <= 8192");
+  if (p.ppc < 1 || (int64_t)p.nr * p.ppc > (fp64 ? 8192 : 65536))
+    return fail(WAKE_EINVAL, "need ppc >= 1 and nr*ppc <= 8192 (FP64) or 65536 (mixed)");
   if (p.u_th < 0.0 || (p.u_th > 0.0 && p.ppc % 2)) return fail(WAKE_EINVAL, "a warm plasma needs u_th > 0 and an even ppc");
   if (!(p.rmax > 0.0) || !(p.ximax > 0.0)) return fail(WAKE_EINVAL, "rmax and ximax must be positive");
   if (p.n_beam < 0 || p.n_drive < 0 || p.n_drive > p.n_beam) return fail(WAKE_EINVAL, "need 0 <= n_drive <= n_beam");
@@ -191,13 +200,17 @@ std::vector<TileFns> tile_candidates(const wake_sim *h, const Sim &s) {
   const int n1 = s.p.nr + 1;
   for (int nt : {128, 256, 512}) {
     if (h->precision == WAKE_FP64 && nt != 512) continue;
-    if (h->tile_nt_forced && nt != h->tile_nt_forced) continue;
+    if (h->tile_nt_forced && nt != h->tile_nt_forced) continue;  // -1: the wide form only
     if (n1 > 3 * nt) continue;
     const int ppt = pow2_at_least((s.np + nt - 1) / nt);
     TileFns f;
     if (!march_tile(h->precision == WAKE_FP64, nt, ppt, &f)) continue;
     if (f.smem(n1) > kMaxSmemPerCta) continue;
     out.push_back(f);
+  }
+  if (out.empty() && h->precision == WAKE_MIXED && (!h->tile_nt_forced || h->tile_nt_forced == -1)) {
+    const TileFns f = march_tile_wide();
+    if (n1 <= 5 * f.nt && f.smem(n1) <= kMaxSmemPerCta) out.push_back(f);
   }
   return out;
 }
@@ -286,7 +299,9 @@ int plan_tiles(wake_sim *h) {
   for (int i = 0; i < h->n; ++i) {
     int c = -1;
     for (size_t q = 0; q < h->classes.size(); ++q)
-      if (h->classes[q].fns.nt == pick[i].nt && h->classes[q].fns.ppt == pick[i].ppt) c = (int)q;
+      if (h->classes[q].fns.nt == pick[i].nt && h->classes[q].fns.ppt == pick[i].ppt &&
+          h->classes[q].fns.wide == pick[i].wide)
+        c = (int)q;
     if (c < 0) {
       wake_sim::TileClass tc;
       tc.fns = pick[i];
@@ -372,11 +387,16 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
     s.p = p[i];
     s.np = p[i].nr * p[i].ppc;
     s.ng = (size_t)(p[i].nxi + 1) * (p[i].nr + 1);
+    {
+      const std::vector<TileFns> cand = tile_candidates(h, s);
+      s.wide = !cand.empty() && cand.back().wide;
+    }
     h->max_n1 = std::max(h->max_n1, p[i].nr + 1);
     h->max_np = std::max(h->max_np, s.np);
     const size_t pb = sizeof(double) * s.np;
     if ((rc = dalloc(&s.r0, pb)) || (rc = dalloc(&s.ur0, pb)) || (rc = dalloc(&s.lz, pb)) || (rc = dalloc(&s.G0, pb)) ||
-        (rc = dalloc(&s.w, pb)) || (ring_buf_bytes(h->precision == WAKE_FP64) > 0 && (rc = dalloc(&s.ring_buf, ring_buf_bytes(h->precision == WAKE_FP64)))) ||
+        (rc = dalloc(&s.w, pb)) ||
+        (sim_ring_bytes(h->precision, s) > 0 && (rc = dalloc(&s.ring_buf, sim_ring_bytes(h->precision, s)))) ||
         (rc = dalloc(&s.nb, gs * s.ng)) || (rc = dalloc(&s.psi, gs * s.ng)) ||
         (rc = dalloc(&s.ez, gs * s.ng)) || (rc = dalloc(&s.er, gs * s.ng)) || (rc = dalloc(&s.bth, gs * s.ng)) ||
         (rc = dalloc(&s.status, sizeof(int))))
@@ -710,9 +730,12 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
   Sim &s = h->sims[0];
   const int fp64 = h->precision == WAKE_FP64;
   const size_t gs = gsize(h->precision), gbytes = gs * s.ng;
-  // every step of a launch owns a density grid; keep them within ~2 GB
-  const int chmax = (int)std::min<size_t>(1024, std::max<size_t>(1, ((size_t)2 << 30) / gbytes - 1));
-  const size_t rb = ring_buf_bytes(fp64);
+  // every step of a launch owns a density grid: up to a quarter of the free memory
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const int chmax = (int)std::min<size_t>(1024, std::max<size_t>(1, free_b / 4 / gbytes - 1));
+  const size_t rb = s.wide ? wide_ring_bytes(s.np) : ring_buf_bytes(fp64);
+  const size_t wb = s.wide ? step_wide_window_bytes(s.p.nr + 1) : 0;
   int rc, done = 0, last_ch = 0;
   while (done < nsteps) {
     long long lim = 0;
@@ -730,12 +753,12 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
       s.pgrid_cap = cap + 1;
     }
     const int ctas = std::min(ch, ctas_max);
-    if (rb > 0 && s.pring_bytes < rb * ctas) {
+    if (rb + wb > 0 && s.pring_bytes < (rb + wb) * ctas) {
       if (s.pring) cudaFree(s.pring);
       s.pring = nullptr;
       s.pring_bytes = 0;
-      if ((rc = dalloc(&s.pring, rb * ctas))) return rc;
-      s.pring_bytes = rb * ctas;
+      if ((rc = dalloc(&s.pring, (rb + wb) * ctas))) return rc;
+      s.pring_bytes = (rb + wb) * ctas;
     }
     if ((rc = sort_beam(h, s))) return rc;
     const BeamDesc bd = beam_desc(s, nullptr);
@@ -796,6 +819,8 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
     a.spin_limit = 1LL << 24;  // polls of >= 128 ns: a wait gives up after seconds
     a.ring_bufs = s.pring;
     a.ring_stride = rb;
+    a.win_bufs = wb > 0 ? (char *)s.pring + rb * ctas : nullptr;
+    a.win_stride = wb;
     if (h->ev_used == (int)h->ev.size()) {
       std::pair<cudaEvent_t, cudaEvent_t> q{};
       CUDA_TRY(cudaEventCreate(&q.first));
@@ -806,7 +831,7 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
       h->ev.push_back(q);
     }
     CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].first, h->stream));
-    const cudaError_t e = launch_step(fp64, a, s.np, ctas, h->stream);
+    const cudaError_t e = s.wide ? launch_step_wide(a, ctas, h->stream) : launch_step(fp64, a, s.np, ctas, h->stream);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("pipelined step launch: ") + cudaGetErrorString(e));
     CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].second, h->stream));
     ++h->ev_used;
@@ -829,7 +854,7 @@ int wake_step(wake_sim *h, int nsteps) {
   if (h->n == 1 && h->sims[0].p.n_beam > 0) {
     Sim &s = h->sims[0];
     if (!s.beam || !s.plasma) return fail(WAKE_ESTATE, "wake_step needs wake_load_plasma and wake_load_beam");
-    const int ctas = step_max_ctas(h->precision == WAKE_FP64, s.p.nr + 1, s.np);
+    const int ctas = s.wide ? step_wide_max_ctas(s.p.nr + 1) : step_max_ctas(h->precision == WAKE_FP64, s.p.nr + 1, s.np);
     if (ctas > 0) return step_pipelined(h, nsteps, ctas);
   }
   if (h->n > 1) return step_batched(h, nsteps);

@@ -1,0 +1,115 @@
+"""The wide form of the mixed march (rings in a global buffer, chunked passes), used for the
+large configuration (Nr = 2048, 32 rings per cell = 65,536 rings per slice), against the FP64
+oracle: forced on the linear case (fields within 1e-5 of peak |E_z|), at the large config's
+radial size and ring count on a shortened box (peak on-axis E_z within 1%, witness energy
+gain within 0.5%), and pipelined against separate steps."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wk():
+    import torch
+    from paper_1411_3246_gb300 import build, wake
+    build.build()
+    assert torch.cuda.is_available()
+    return wake
+
+
+def test_wide_form_linear_matches_oracle(wk, monkeypatch):
+    import torch
+    monkeypatch.setenv("WAKE_TILE_NT", "-1")
+    cfg = synth.config_linear(nr=128, nxi=256)
+    with wk.Simulations([cfg], wk.WAKE_MIXED) as s:
+        wk.wake_load_plasma(s.h, 0, None)
+        wk.wake_plasma_march(s.h)
+        got = {k: v.cpu().numpy() for k, v in s.fields(0).items()}
+        assert s.status(0) == wk.WAKE_OK, wk.wake_last_error()
+        assert wk.wake_tile(s.h, 0) == (512, 8)
+    ref = oracle.march(cfg, oracle.plasma_init(cfg, None), oracle.nb_analytic(cfg))
+    scale = np.abs(ref["ez"]).max()
+    for k in ("psi", "ez", "er", "bth"):
+        assert np.abs(got[k] - ref[k]).max() <= 1e-5 * scale, k
+
+
+def large_short(nxi=1024, n_beam=0):
+    """The large configuration's radial grid and plasma (Nr=2048 over 10, 32 rings per cell,
+    u_th=0.02, blowout two-bunch driver) on a box shortened to nxi slices over 8 (the witness
+    sits at 6.9)."""
+    cfg = synth.config_large(n_beam=max(n_beam, 2))
+    cfg.nxi, cfg.ximax = nxi, 8.0
+    cfg = synth.two_bunch(cfg, 0.3, 4.5, max(n_beam, 2))
+    cfg.n_beam = n_beam
+    if n_beam == 0:
+        cfg.n_drive = 0
+    return cfg
+
+
+def test_wide_form_large_radial_grid_peak_ez(wk):
+    import torch
+    cfg = large_short()
+    assert cfg.nr * cfg.ppc == 65536
+    nm = synth.plasma_normals(cfg)
+    with wk.Simulations([cfg], wk.WAKE_MIXED) as s:
+        wk.wake_load_plasma(s.h, 0, torch.from_numpy(nm).cuda())
+        wk.wake_plasma_march(s.h)
+        got = {k: v.cpu().numpy() for k, v in s.fields(0).items()}
+        assert s.status(0) == wk.WAKE_OK, wk.wake_last_error()
+        assert wk.wake_tile(s.h, 0) == (512, 8)
+    ref = oracle.march(cfg, oracle.plasma_init(cfg, nm), oracle.nb_analytic(cfg))
+    pk_ref = np.abs(ref["ez"][:, 0]).max()
+    pk = np.abs(got["ez"][:, 0]).max()
+    assert pk_ref > 0.5
+    assert abs(pk - pk_ref) <= 0.01 * pk_ref
+
+
+def test_wide_form_large_beam_steps_witness_energy(wk):
+    import torch
+    cfg = large_short(n_beam=1 << 15)
+    cfg.ds = 50.0
+    nm_p, nm_b = synth.plasma_normals(cfg), synth.beam_normals(cfg)
+    pl, bm = oracle.plasma_init(cfg, nm_p), oracle.beam_init(cfg, nm_b)
+    d0 = oracle.diagnostics(cfg, bm)
+    oracle.run(cfg, pl, bm, 2)
+    d_ref = oracle.diagnostics(cfg, bm)
+    with wk.Simulations([cfg], wk.WAKE_MIXED) as s:
+        wk.wake_load_plasma(s.h, 0, torch.from_numpy(nm_p).cuda())
+        wk.wake_load_beam(s.h, 0, torch.from_numpy(nm_b).cuda())
+        wk.wake_step(s.h, 2)
+        d = s.diagnostics()[0]
+        assert s.status(0) == wk.WAKE_OK, wk.wake_last_error()
+    gain, gain_ref = d[1] - d0[1], d_ref[1] - d0[1]
+    assert abs(gain_ref) > 1.0
+    assert abs(gain - gain_ref) <= 0.005 * abs(gain_ref), (gain, gain_ref)
+
+
+def test_wide_form_pipelined_matches_separate_steps(wk, monkeypatch):
+    import torch
+    monkeypatch.setenv("WAKE_TILE_NT", "-1")
+    cfg = synth.config_blowout(n_beam=1 << 15, nr=128, nxi=256)
+    cfg.ds = 50.0
+    nm_p, nm_b = synth.plasma_normals(cfg), synth.beam_normals(cfg)
+    out = []
+    for pipelined in (True, False):
+        with wk.Simulations([cfg], wk.WAKE_MIXED) as s:
+            wk.wake_load_plasma(s.h, 0, torch.from_numpy(nm_p).cuda())
+            wk.wake_load_beam(s.h, 0, torch.from_numpy(nm_b).cuda())
+            if pipelined:
+                wk.wake_step(s.h, 4)
+                assert wk.wake_step_kernel_ms(s.h) > 0.0
+            else:
+                for _ in range(4):
+                    wk.wake_beam_deposit(s.h)
+                    wk.wake_plasma_march(s.h)
+                    wk.wake_beam_push(s.h)
+            out.append((s.fields(0)["ez"].cpu().numpy(), s.diagnostics()[0]))
+            assert s.status(0) == wk.WAKE_OK, wk.wake_last_error()
+    (ea, da), (eb, db) = out
+    assert np.abs(ea - eb).max() <= 2e-3 * np.abs(eb).max()
+    g0 = cfg.gamma_b
+    assert abs((da[1] - g0) - (db[1] - g0)) <= 1e-3 * abs(db[1] - g0)

@@ -118,11 +118,13 @@ int wake_beam_push(wake_sim *s);
  * that has a beam, the steps run pipelined: the beam is sorted by xi cell and one
  * cooperative launch marches up to one step per SM, each step a few slices behind the one
  * before, pushing each cell of the beam as soon as its fields are solved (same arithmetic as
- * the separate calls; only the order of the deposit sums differs).  A launch is limited to
- * the steps over which no beam particle slips more than a quarter of a xi cell, measured on
- * the beam at its start (this call synchronises the stream once per launch); a beam that
- * slips faster, or a handle of several simulations, takes the separate calls.  A particle
- * found to have slipped further anyway raises WAKE_ESTATE through wake_status.
+ * the separate calls; only the order of the deposit sums differs).  A particle that slips
+ * two or more cells past the cell it was sorted into during a launch is pushed when that
+ * cell's fields are solved.  The beam must slip less than a cell per step: a beam whose
+ * fastest particle, measured at the start of each launch, slips more than 1/8 of a cell
+ * per step takes the separate calls (the check synchronises the stream once per launch), and
+ * a particle found to have slipped a cell or more in one step anyway raises WAKE_ESTATE
+ * through wake_status.
  */
 int wake_step(wake_sim *s, int nsteps);
 

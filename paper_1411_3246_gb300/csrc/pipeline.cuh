@@ -41,6 +41,13 @@ struct PipeArgs {
   size_t ring_stride;
   void *win_bufs;         // per-CTA field windows in global memory (wide form)
   size_t win_stride;
+  // particles that slipped two or more cells past their sorted cell within the launch: step t
+  // lists them (index, target cell) in defer_list[t * defer_cap ...] and pushes them at their
+  // target; target[j] is the latest target any step gave particle j (-1: none)
+  int *defer_cnt;
+  int2 *defer_list;
+  int defer_cap;
+  int *target;
 };
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -117,69 +124,111 @@ struct PipeHooks {
     if (ctl[0] == 0 && nxi >= 1) push_cell(nxi - 1);
   }
 
-  // Push the beam particles sorted into cell b (fields of slices b .. b+2 are in the window)
-  // and deposit them into the grid of step t+1; then publish progress[t] = b + 1.
-  __device__ void push_cell(int b) {
+  // Push particle j, found in cell kk (kk == b or b + 1, fields of slices b .. b+2 in the
+  // window), and deposit it into the grid of step t+1.
+  __device__ __forceinline__ void push_one(int j, uint8_t fl, int kk, double gd) {
     BT *X = (BT *)a.x, *Y = (BT *)a.y, *UX = (BT *)a.ux, *UY = (BT *)a.uy;
     G *nbn = (G *)a.grids + (size_t)(t + 1) * a.ng;
     const BT inv_dr = (BT)(1.0 / dr), dt = (BT)a.ds, Rw = (BT)rmax;
     const double inv_dxi = 1.0 / dxi;
+    BT x = __ldcg(X + j), y = __ldcg(Y + j), ux = __ldcg(UX + j), uy = __ldcg(UY + j);
+    double xi = __ldcg(a.xi + j), uzd = __ldcg(a.uz + j);
+    const BT r = sqrt(x * x + y * y);
+    int c;
+    BT f;
+    locate(r, inv_dr, nr, c, f);
+    const BT g = (BT)gd;
+    const R *w0 = win + (size_t)(kk & 3) * 3 * n1, *w1 = win + (size_t)((kk + 1) & 3) * 3 * n1;
+    const BT a00 = ((BT)1 - f) * ((BT)1 - g), a01 = f * ((BT)1 - g), a10 = ((BT)1 - f) * g, a11 = f * g;
+    const BT Er = a00 * w0[c] + a01 * w0[c + 1] + a10 * w1[c] + a11 * w1[c + 1];
+    const BT Ez = a00 * w0[n1 + c] + a01 * w0[n1 + c + 1] + a10 * w1[n1 + c] + a11 * w1[n1 + c + 1];
+    const BT Bt = a00 * w0[2 * n1 + c] + a01 * w0[2 * n1 + c + 1] + a10 * w1[2 * n1 + c] + a11 * w1[2 * n1 + c + 1];
+    boris_step<BT>(x, y, ux, uy, xi, uzd, r, Er, Ez, Bt, dt);
+    X[j] = x;
+    Y[j] = y;
+    UX[j] = ux;
+    UY[j] = uy;
+    a.xi[j] = xi;
+    a.uz[j] = uzd;
+    const BT rn = sqrt(x * x + y * y);
+    if (!(xi >= 0.0 && xi < ximax && rn < Rw)) {
+      a.flags[j] = fl | 1;
+      return;
+    }
+    // deposit into the next step's grid: bilinear hats over the hat volumes V_i = i dr^2
+    // (dr^2/6 on the axis, dr^2 (nr/2 - 1/6) at the wall) in r, dxi (dxi/2 at the two end
+    // slices) in xi
+    int c2, k2;
+    BT f2;
+    double g2d;
+    locate(rn, inv_dr, nr, c2, f2);
+    locate(xi, inv_dxi, nxi, k2, g2d);
+    const BT g2 = (BT)g2d;
+    const BT wq = (BT)((fl & 2) ? a.ww : a.wd) * (BT)(1.0 / (dr * dr * dxi));
+    auto iv = [&](int i) -> BT {
+      return i == 0 ? (BT)6 : (i == nr ? (BT)1 / ((BT)nr * (BT)0.5 - (BT)(1.0 / 6.0)) : (BT)1 / (BT)i);
+    };
+    const BT ix0 = k2 == 0 ? (BT)2 : (BT)1, ix1 = k2 + 1 == nxi ? (BT)2 : (BT)1;
+    const BT v0 = iv(c2), v1 = iv(c2 + 1);
+    const BT s00 = wq * v0 * ix0, s01 = wq * v1 * ix0, s10 = wq * v0 * ix1, s11 = wq * v1 * ix1;
+    G *row = nbn + (size_t)k2 * n1 + c2;
+    atomicAdd(row, (G)(s00 * ((BT)1 - f2) * ((BT)1 - g2)));
+    atomicAdd(row + 1, (G)(s01 * f2 * ((BT)1 - g2)));
+    atomicAdd(row + n1, (G)(s10 * ((BT)1 - f2) * g2));
+    atomicAdd(row + n1 + 1, (G)(s11 * f2 * g2));
+  }
+
+  // Push the beam particles sorted into cell b (fields of slices b .. b+2 are in the window)
+  // and those this step deferred to cell b, deposit them into the grid of step t+1; then
+  // publish progress[t] = b + 1.  A particle whose cell (or an earlier step's target for it)
+  // is b + 2 or beyond is deferred to that cell: an earlier step may still have to push it
+  // there, and the progress chain makes that happen first.
+  __device__ void push_cell(int b) {
+    const double inv_dxi = 1.0 / dxi;
     const int beg = a.bin_start[b], end = a.bin_start[b + 1];
+    int *cnt = a.defer_cnt + t;
+    int2 *list = a.defer_list + (size_t)t * a.defer_cap;
     for (int j = beg + threadIdx.x; j < end; j += NT) {
-      uint8_t fl = __ldcg(a.flags + j);
+      const uint8_t fl = __ldcg(a.flags + j);
       if (fl & 1) continue;
-      BT x = __ldcg(X + j), y = __ldcg(Y + j), ux = __ldcg(UX + j), uy = __ldcg(UY + j);
-      double xi = __ldcg(a.xi + j), uzd = __ldcg(a.uz + j);
+      const double xi = __ldcg(a.xi + j);
       int kk;
       double gd;
       locate(xi, inv_dxi, nxi, kk, gd);
-      if (kk != b && kk != b + 1) {  // drifted beyond the cell the fields are ready for
+      const int tgt = max(kk, __ldcg(a.target + j));
+      if (tgt >= b + 2) {
+        const int q = atomicAdd(cnt, 1);
+        if (q < a.defer_cap) {
+          list[q] = make_int2(j, tgt);
+          if (tgt > __ldcg(a.target + j)) a.target[j] = tgt;
+        } else {
+          flag(a.d.status, ST_DRIFT);
+        }
+        continue;
+      }
+      if (kk != b && kk != b + 1) {  // behind its sorted cell: cannot happen (xi only grows)
         flag(a.d.status, ST_DRIFT);
         continue;
       }
-      const BT r = sqrt(x * x + y * y);
-      int c;
-      BT f;
-      locate(r, inv_dr, nr, c, f);
-      const BT g = (BT)gd;
-      const R *w0 = win + (size_t)(kk & 3) * 3 * n1, *w1 = win + (size_t)((kk + 1) & 3) * 3 * n1;
-      const BT a00 = ((BT)1 - f) * ((BT)1 - g), a01 = f * ((BT)1 - g), a10 = ((BT)1 - f) * g, a11 = f * g;
-      const BT Er = a00 * w0[c] + a01 * w0[c + 1] + a10 * w1[c] + a11 * w1[c + 1];
-      const BT Ez = a00 * w0[n1 + c] + a01 * w0[n1 + c + 1] + a10 * w1[n1 + c] + a11 * w1[n1 + c + 1];
-      const BT Bt = a00 * w0[2 * n1 + c] + a01 * w0[2 * n1 + c + 1] + a10 * w1[2 * n1 + c] + a11 * w1[2 * n1 + c + 1];
-      boris_step<BT>(x, y, ux, uy, xi, uzd, r, Er, Ez, Bt, dt);
-      X[j] = x;
-      Y[j] = y;
-      UX[j] = ux;
-      UY[j] = uy;
-      a.xi[j] = xi;
-      a.uz[j] = uzd;
-      const BT rn = sqrt(x * x + y * y);
-      if (!(xi >= 0.0 && xi < ximax && rn < Rw)) {
-        a.flags[j] = fl | 1;
+      push_one(j, fl, kk, gd);
+    }
+    __syncthreads();  // every entry counted so far is written
+    // this step's deferred particles whose target is b (all listed by earlier cells)
+    const int nd = min(__ldcg(cnt), a.defer_cap);
+    for (int q = threadIdx.x; q < nd; q += NT) {
+      const int2 e = __ldcg(list + q);
+      if (e.y != b) continue;
+      const int j = e.x;
+      const uint8_t fl = __ldcg(a.flags + j);
+      if (fl & 1) continue;
+      int kk;
+      double gd;
+      locate(__ldcg(a.xi + j), inv_dxi, nxi, kk, gd);
+      if (kk != b && kk != b + 1) {
+        flag(a.d.status, ST_DRIFT);
         continue;
       }
-      // deposit into the next step's grid: bilinear hats over the hat volumes
-      int c2, k2;
-      BT f2;
-      double g2d;
-      locate(rn, inv_dr, nr, c2, f2);
-      locate(xi, inv_dxi, nxi, k2, g2d);
-      const BT g2 = (BT)g2d;
-      // weight over the hat volumes: V_i = i dr^2 (dr^2/6 on the axis, dr^2 (nr/2 - 1/6) at the
-      // wall) in r, dxi (dxi/2 at the two end slices) in xi
-      const BT wq = (BT)((fl & 2) ? a.ww : a.wd) * (BT)(1.0 / (dr * dr * dxi));
-      auto iv = [&](int i) -> BT {
-        return i == 0 ? (BT)6 : (i == nr ? (BT)1 / ((BT)nr * (BT)0.5 - (BT)(1.0 / 6.0)) : (BT)1 / (BT)i);
-      };
-      const BT ix0 = k2 == 0 ? (BT)2 : (BT)1, ix1 = k2 + 1 == nxi ? (BT)2 : (BT)1;
-      const BT v0 = iv(c2), v1 = iv(c2 + 1);
-      const BT s00 = wq * v0 * ix0, s01 = wq * v1 * ix0, s10 = wq * v0 * ix1, s11 = wq * v1 * ix1;
-      G *row = nbn + (size_t)k2 * n1 + c2;
-      atomicAdd(row, (G)(s00 * ((BT)1 - f2) * ((BT)1 - g2)));
-      atomicAdd(row + 1, (G)(s01 * f2 * ((BT)1 - g2)));
-      atomicAdd(row + n1, (G)(s10 * ((BT)1 - f2) * g2));
-      atomicAdd(row + n1 + 1, (G)(s11 * f2 * g2));
+      push_one(j, fl, kk, gd);
     }
     __threadfence();
     __syncthreads();

@@ -55,6 +55,8 @@ struct Sim {
   int *progress = nullptr;
   void *pring = nullptr;
   size_t pring_bytes = 0;
+  int *defer_cnt = nullptr, *target = nullptr;  // pipelined steps: slipped-particle lists
+  int2 *defer_list = nullptr;
   int *status = nullptr;
   bool plasma = false, beam = false, marched = false;
   bool wide = false;  // marched by the wide form (rings in a global buffer)
@@ -119,7 +121,8 @@ namespace {
 void free_sim(Sim &s) {
   void *ptrs[] = {s.r0, s.ur0, s.lz, s.G0, s.w, s.ring_buf, s.nb, s.psi, s.ez, s.er, s.bth, s.bx, s.by, s.bux, s.buy,
                   s.bxi, s.buz, s.blost, s.status, s.orig, s.bx2, s.by2, s.bux2, s.buy2, s.bxi2, s.buz2, s.blost2,
-                  s.orig2, s.bin_count, s.bin_start, s.bin_cursor, s.slip, s.pgrids, s.progress, s.pring};
+                  s.orig2, s.bin_count, s.bin_start, s.bin_cursor, s.slip, s.pgrids, s.progress, s.pring,
+                  s.defer_cnt, s.target, s.defer_list};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   s = Sim();
@@ -656,9 +659,12 @@ int sort_beam(wake_sim *h, Sim &s) {
   return WAKE_OK;
 }
 
-// Steps one pipelined launch may run: every beam particle must stay within one xi cell of
-// the cell it was sorted into (pipeline.cuh), so the launch is kept to a quarter cell of slip
-// at the beam's present largest slip rate.  Synchronises the stream.
+// Steps one pipelined launch may run by the slip of its fastest particle: a particle may slip
+// any distance over a launch (pipeline.cuh defers it to the cell it reached), but less than
+// one cell in a single step.  With 4x headroom for the slip rate to grow (u_perp^2 grows
+// with the betatron motion), a step may slip half a cell at the present largest rate;
+// otherwise the steps are taken one launch sequence at a time (returned limit 0).
+// Synchronises the stream.
 int slip_bound_steps(wake_sim *h, Sim &s, long long *out) {
   BeamDesc b = beam_desc(s, nullptr);
   CUDA_TRY(cudaMemsetAsync(s.slip, 0, sizeof(unsigned long long), h->stream));
@@ -673,8 +679,8 @@ int slip_bound_steps(wake_sim *h, Sim &s, long long *out) {
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   double rate;
   std::memcpy(&rate, &bits, sizeof(rate));
-  const double lim = rate > 0.0 ? 0.25 * (s.p.ximax / s.p.nxi) / (s.p.ds * rate) : 1e18;
-  *out = (long long)std::min(1e18, std::floor(lim));
+  const bool ok = !(4.0 * s.p.ds * rate > 0.5 * (s.p.ximax / s.p.nxi));
+  *out = ok ? (1LL << 40) : 0;
   return WAKE_OK;
 }
 
@@ -742,16 +748,23 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
     if ((rc = slip_bound_steps(h, s, &lim))) return rc;
     if (lim < 4) return step_sequential(h, nsteps - done);  // a beam slipping this fast: one step at a time
     const int ch = (int)std::min<long long>(std::min(nsteps - done, chmax), lim);
+    const int dcap = (int)std::min<int64_t>(s.p.n_beam, 65536);
     if (s.pgrid_cap < ch + 1) {
-      if (s.pgrids) cudaFree(s.pgrids);
-      if (s.progress) cudaFree(s.progress);
+      void *old[] = {s.pgrids, s.progress, s.defer_cnt, s.defer_list};
+      for (void *q : old)
+        if (q) cudaFree(q);
       s.pgrids = nullptr;
       s.progress = nullptr;
+      s.defer_cnt = nullptr;
+      s.defer_list = nullptr;
       s.pgrid_cap = 0;
       const int cap = std::min(nsteps, chmax);
-      if ((rc = dalloc(&s.pgrids, gbytes * (cap + 1))) || (rc = dalloc(&s.progress, sizeof(int) * cap))) return rc;
+      if ((rc = dalloc(&s.pgrids, gbytes * (cap + 1))) || (rc = dalloc(&s.progress, sizeof(int) * cap)) ||
+          (rc = dalloc(&s.defer_cnt, sizeof(int) * cap)) || (rc = dalloc(&s.defer_list, sizeof(int2) * dcap * (size_t)cap)))
+        return rc;
       s.pgrid_cap = cap + 1;
     }
+    if (!s.target && (rc = dalloc(&s.target, sizeof(int) * s.p.n_beam))) return rc;
     const int ctas = std::min(ch, ctas_max);
     if (rb + wb > 0 && s.pring_bytes < (rb + wb) * ctas) {
       if (s.pring) cudaFree(s.pring);
@@ -778,6 +791,8 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
     }
     CUDA_TRY(cudaMemsetAsync((char *)s.pgrids + gbytes, 0, gbytes * ch, h->stream));
     CUDA_TRY(cudaMemsetAsync(s.progress, 0, sizeof(int) * ch, h->stream));
+    CUDA_TRY(cudaMemsetAsync(s.defer_cnt, 0, sizeof(int) * ch, h->stream));
+    CUDA_TRY(cudaMemsetAsync(s.target, 0xff, sizeof(int) * s.p.n_beam, h->stream));  // -1: no target
     PipeArgs a{};
     SimDesc &d = a.d;
     d.nr = s.p.nr;
@@ -821,6 +836,10 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
     a.ring_stride = rb;
     a.win_bufs = wb > 0 ? (char *)s.pring + rb * ctas : nullptr;
     a.win_stride = wb;
+    a.defer_cnt = s.defer_cnt;
+    a.defer_list = s.defer_list;
+    a.defer_cap = dcap;
+    a.target = s.target;
     if (h->ev_used == (int)h->ev.size()) {
       std::pair<cudaEvent_t, cudaEvent_t> q{};
       CUDA_TRY(cudaEventCreate(&q.first));

@@ -107,3 +107,22 @@ def test_pipelined_mixed_matches_sequential(wk):
     # witness mean energy gain within 0.1%
     g0 = cfg.gamma_b
     assert abs((da[1] - g0) - (db[1] - g0)) <= 1e-3 * abs(db[1] - g0)
+
+
+def test_particles_slipping_several_cells_in_one_launch(wk):
+    """gamma_b = 40 (linear driver): the beam slips ~1/30 cell per step, about two cells over
+    60 steps of one launch; particles past their sorted cell are pushed at the cell they
+    reached.  Same result as separate steps."""
+    cfg = synth.config_linear(nr=64, nxi=256)
+    cfg.ximax = 12.0
+    cfg = synth.two_bunch(cfg, 0.3, 4.0, 4096)
+    cfg.gamma_b, cfg.ds, cfg.eps_n = 40.0, 5.0, 1e-3
+    a = _run(wk, cfg, wk.WAKE_FP64, [60])
+    b = _run(wk, cfg, wk.WAKE_FP64, [("seq", 60)])
+    _compare_fp64(a, b, 1e-8)
+    nm = synth.beam_normals(cfg)
+    xi0 = np.where(np.arange(cfg.n_beam) < cfg.n_drive, cfg.xi_d + cfg.sigma_zd * nm[4], cfg.xi_w + cfg.sigma_zw * nm[4])
+    dxi = cfg.ximax / cfg.nxi
+    live = a["lost"] == 0
+    moved = np.floor(a["xyz"][2][live] / dxi) - np.floor(xi0[live] / dxi)
+    assert moved.max() >= 2

@@ -272,16 +272,22 @@ __device__ __forceinline__ int beam_bin(const BeamDesc &b, int64_t j) {
   locate(b.xi[j], 1.0 / b.dxi, b.nxi, k, g);
   return k;
 }
-// Largest xi slip rate dxi/dt = (1 + u_perp^2) / (gamma (gamma + u_z)) over the live beam, as
-// the bits of a non-negative double (ordered like unsigned integers) in *out (zeroed before).
+// Slip rates dxi/dt = (1 + u_perp^2) / (gamma (gamma + u_z)) of the live beam: the largest, as
+// the bits of a non-negative double (ordered like unsigned integers) in *out, and a histogram
+// of floor(log2(span / rate)) (clamped to 0..63; span / rate = steps until the particle has
+// slipped a given span) in hist.  Both zeroed before.
 template <class BT>
-__global__ void beam_slip_kernel(BeamDesc b, unsigned long long *out) {
+__global__ void beam_slip_kernel(BeamDesc b, double span, unsigned long long *out, int *hist) {
   double m = 0.0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
     if (b.lost[j] & 1) continue;
     const double ux = ((const BT *)b.ux)[j], uy = ((const BT *)b.uy)[j], uz = b.uz[j];
     const double up2 = ux * ux + uy * uy, g = sqrt(1.0 + up2 + uz * uz);
-    m = fmax(m, (1.0 + up2) / (g * (g + uz)));
+    const double rate = (1.0 + up2) / (g * (g + uz));
+    m = fmax(m, rate);
+    const double steps = rate > 0.0 ? span / rate : 1e300;
+    const int q = steps < 1.0 ? 0 : (steps >= 9.2e18 ? 63 : min(63, 63 - __clzll((long long)steps)));
+    atomicAdd(&hist[q], 1);
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));

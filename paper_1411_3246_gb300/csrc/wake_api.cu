@@ -57,6 +57,7 @@ struct Sim {
   size_t pring_bytes = 0;
   int *defer_cnt = nullptr, *target = nullptr;  // pipelined steps: slipped-particle lists
   int2 *defer_list = nullptr;
+  size_t defer_bytes = 0;
   int *status = nullptr;
   bool plasma = false, beam = false, marched = false;
   bool wide = false;  // marched by the wide form (rings in a global buffer)
@@ -420,7 +421,7 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
           (rc = dalloc(&s.bin_count, sizeof(int) * (p[i].nxi + 2))) ||
           (rc = dalloc(&s.bin_start, sizeof(int) * (p[i].nxi + 2))) ||
           (rc = dalloc(&s.bin_cursor, sizeof(int) * (p[i].nxi + 2))) ||
-          (rc = dalloc(&s.slip, sizeof(unsigned long long))))
+          (rc = dalloc(&s.slip, sizeof(unsigned long long) + 64 * sizeof(int))))
         break;
     } else {
       // frozen analytic driver (Eq. 12) on the nodes
@@ -659,28 +660,34 @@ int sort_beam(wake_sim *h, Sim &s) {
   return WAKE_OK;
 }
 
-// Steps one pipelined launch may run by the slip of its fastest particle: a particle may slip
-// any distance over a launch (pipeline.cuh defers it to the cell it reached), but less than
-// one cell in a single step.  With 4x headroom for the slip rate to grow (u_perp^2 grows
-// with the betatron motion), a step may slip half a cell at the present largest rate;
-// otherwise the steps are taken one launch sequence at a time (returned limit 0).
+// The beam's slip rates at the start of a launch.  A particle may slip any distance over a
+// launch (pipeline.cuh lists it for the cell it reached), but less than one cell per step.
+//   *ok: the fastest particle, with 4x headroom for its rate to grow (u_perp^2 grows with the
+//        betatron motion), slips at most half a cell per step (else the steps are taken one
+//        launch sequence at a time);
+//   hist[q]: particles that, at twice their present rate, slip two cells after [2^q, 2^(q+1))
+//        steps - a launch of L steps lists at most those of the buckets with 2^q < L.
 // Synchronises the stream.
-int slip_bound_steps(wake_sim *h, Sim &s, long long *out) {
+int slip_stats(wake_sim *h, Sim &s, bool *ok, long long *hist) {
   BeamDesc b = beam_desc(s, nullptr);
-  CUDA_TRY(cudaMemsetAsync(s.slip, 0, sizeof(unsigned long long), h->stream));
+  const double dxi = s.p.ximax / s.p.nxi;
+  CUDA_TRY(cudaMemsetAsync(s.slip, 0, sizeof(unsigned long long) + 64 * sizeof(int), h->stream));
+  int *dh = (int *)(s.slip + 1);
   const int blocks = grid_blocks(s.p.n_beam, 256);
+  const double span = 2.0 * dxi / (2.0 * s.p.ds);  // steps_j = span / rate_j
   if (h->precision == WAKE_FP64)
-    beam_slip_kernel<double><<<blocks, 256, 0, h->stream>>>(b, s.slip);
+    beam_slip_kernel<double><<<blocks, 256, 0, h->stream>>>(b, span, s.slip, dh);
   else
-    beam_slip_kernel<float><<<blocks, 256, 0, h->stream>>>(b, s.slip);
+    beam_slip_kernel<float><<<blocks, 256, 0, h->stream>>>(b, span, s.slip, dh);
   CUDA_TRY(cudaGetLastError());
-  unsigned long long bits = 0;
-  CUDA_TRY(cudaMemcpyAsync(&bits, s.slip, sizeof(bits), cudaMemcpyDeviceToHost, h->stream));
+  unsigned long long buf[1 + 32] = {};
+  CUDA_TRY(cudaMemcpyAsync(buf, s.slip, sizeof(unsigned long long) + 64 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   double rate;
-  std::memcpy(&rate, &bits, sizeof(rate));
-  const bool ok = !(4.0 * s.p.ds * rate > 0.5 * (s.p.ximax / s.p.nxi));
-  *out = ok ? (1LL << 40) : 0;
+  std::memcpy(&rate, &buf[0], sizeof(rate));
+  *ok = !(4.0 * s.p.ds * rate > 0.5 * dxi);
+  const int *hc = (const int *)(buf + 1);
+  for (int q = 0; q < 64; ++q) hist[q] = hc[q];
   return WAKE_OK;
 }
 
@@ -743,26 +750,48 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
   const size_t rb = s.wide ? wide_ring_bytes(s.np) : ring_buf_bytes(fp64);
   const size_t wb = s.wide ? step_wide_window_bytes(s.p.nr + 1) : 0;
   int rc, done = 0, last_ch = 0;
+  // the lists of slipped particles: up to 16 GB (or an eighth of the free memory) for a launch
+  const size_t list_budget = std::min<size_t>((size_t)16 << 30, free_b / 8);
   while (done < nsteps) {
-    long long lim = 0;
-    if ((rc = slip_bound_steps(h, s, &lim))) return rc;
-    if (lim < 4) return step_sequential(h, nsteps - done);  // a beam slipping this fast: one step at a time
-    const int ch = (int)std::min<long long>(std::min(nsteps - done, chmax), lim);
-    const int dcap = (int)std::min<int64_t>(s.p.n_beam, 65536);
+    bool ok = false;
+    long long hist[64];
+    if ((rc = slip_stats(h, s, &ok, hist))) return rc;
+    if (!ok) return step_sequential(h, nsteps - done);  // a beam slipping this fast: one step at a time
+    // the longest launch (whole waves of co-resident steps where possible; the first launch of
+    // a call, when a fresh beam's u_perp grows fastest, is one wave) whose predicted lists fit
+    const long long want = std::min<long long>(nsteps - done, done == 0 ? std::min(ctas_max, chmax) : chmax);
+    long long L = want, dcap_l = 0;
+    for (;;) {
+      long long pred = 0;
+      for (int q = 0; q < 64 && (1LL << q) < L; ++q) pred += hist[q];
+      dcap_l = std::min<long long>(s.p.n_beam, 2 * pred + 65536);
+      const long long fit = (long long)(list_budget / (sizeof(int2) * (size_t)L));
+      if (dcap_l <= fit || L == 1) break;
+      L = L > ctas_max ? (L - 1) / ctas_max * ctas_max : L / 2;
+    }
+    if (L >= ctas_max) L = L / ctas_max * ctas_max;
+    const int ch = (int)std::max<long long>(1, L);
+    const int dcap = (int)dcap_l;
     if (s.pgrid_cap < ch + 1) {
-      void *old[] = {s.pgrids, s.progress, s.defer_cnt, s.defer_list};
+      void *old[] = {s.pgrids, s.progress, s.defer_cnt};
       for (void *q : old)
         if (q) cudaFree(q);
       s.pgrids = nullptr;
       s.progress = nullptr;
       s.defer_cnt = nullptr;
-      s.defer_list = nullptr;
       s.pgrid_cap = 0;
       const int cap = std::min(nsteps, chmax);
       if ((rc = dalloc(&s.pgrids, gbytes * (cap + 1))) || (rc = dalloc(&s.progress, sizeof(int) * cap)) ||
-          (rc = dalloc(&s.defer_cnt, sizeof(int) * cap)) || (rc = dalloc(&s.defer_list, sizeof(int2) * dcap * (size_t)cap)))
+          (rc = dalloc(&s.defer_cnt, sizeof(int) * cap)))
         return rc;
       s.pgrid_cap = cap + 1;
+    }
+    if (s.defer_bytes < sizeof(int2) * (size_t)dcap * ch) {
+      if (s.defer_list) cudaFree(s.defer_list);
+      s.defer_list = nullptr;
+      s.defer_bytes = 0;
+      if ((rc = dalloc(&s.defer_list, sizeof(int2) * (size_t)dcap * ch))) return rc;
+      s.defer_bytes = sizeof(int2) * (size_t)dcap * ch;
     }
     if (!s.target && (rc = dalloc(&s.target, sizeof(int) * s.p.n_beam))) return rc;
     const int ctas = std::min(ch, ctas_max);

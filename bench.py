@@ -248,6 +248,41 @@ def batched_leg(wake, torch, n_sims, nsteps, rank, flush, world):
             "dtype": "f32", "graph": "one batched step captured once, replayed per step"}
 
 
+def large_leg(wake, torch, nsteps, rank, flush, world):
+    """The large configuration (mixed, the wide march form): one run of nsteps beam steps from
+    the initial beam by one wake_step call, after an untimed run of one step (allocation)."""
+    cfg = synth.config_large()
+    cfg.seed += 1000 * rank
+    stream = torch.cuda.Stream()
+    nm_p = torch.from_numpy(synth.plasma_normals(cfg)).pin_memory()
+    nm_b = torch.from_numpy(synth.beam_normals(cfg)).pin_memory()
+    sim = wake.Simulations([cfg], wake.WAKE_MIXED, stream)
+    with torch.cuda.stream(stream):
+        dp, db = nm_p.cuda(non_blocking=True), nm_b.cuda(non_blocking=True)
+        wake.wake_load_plasma(sim.h, 0, dp)
+        wake.wake_load_beam(sim.h, 0, db)
+        wake.wake_step(sim.h, 1)
+        wake.wake_load_beam(sim.h, 0, db)
+        flush.fill_(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        wake.wake_step(sim.h, nsteps)
+        ev[1].record(stream)
+    stream.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    st = sim.status(0)
+    sim.close()
+    if st != wake.WAKE_OK:
+        raise RuntimeError(f"large leg: simulation status {st}: {wake.wake_last_error()}")
+    pushes = plasma_pushes_per_step(cfg) * nsteps
+    t = barrier_max(ms / 1e3, world)
+    return {"value": world * pushes / t, "unit": "pushes/s", "ms_per_run": 1e3 * t, "beam_steps": nsteps,
+            "beam_pushes_per_s": world * cfg.n_beam * nsteps / t,
+            "workload": f"large: Nr={cfg.nr} x Nxi={cfg.nxi}, {cfg.ppc} rings/cell ({cfg.nr * cfg.ppc} per slice), "
+                        f"u_th={cfg.u_th}, {cfg.n_beam} beam particles, {nsteps} of the configuration's 1000 steps",
+            "form": "wide march (rings in global memory, chunks of 512 x 8 slots), pipelined", "dtype": "f32"}
+
+
 def adjoint_case(nsteps, rank):
     """The differentiation workload: the linear-driver grid (Nr=128 over 6, 4 rings/cell) at
     Nxi=1024 over 10, two bunches (witness at the batched sweep's first delay), 262,144 beam
@@ -302,6 +337,8 @@ def main():
     ap.add_argument("--batch-sims", type=int, default=256, help="simulations of the batched leg (0: skip)")
     ap.add_argument("--batch-steps", type=int, default=50, help="beam steps of the batched leg")
     ap.add_argument("--adjoint-steps", type=int, default=100, help="beam steps of the adjoint leg (0: skip)")
+    ap.add_argument("--large-steps", type=int, default=304,
+                    help="beam steps of the large-configuration leg (0: skip; the configuration has 1000)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -404,6 +441,11 @@ def main():
     if args.adjoint_steps > 0:
         adjoint = adjoint_leg(wake, torch, args.adjoint_steps, rank, world)
 
+    # --- large configuration: Nr=2048, 65,536 rings per slice, 16M beam particles ---
+    large = None
+    if args.large_steps > 0:
+        large = large_leg(wake, torch, args.large_steps, rank, flush, world)
+
     # --- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -433,6 +475,7 @@ def main():
                 "e2e": {"value": world * pushes * e2e_steps / e2e_s, "unit": "pushes/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 5 * 8},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "batched": batched, "adjoint": adjoint,
+                "large": large,
                 "gpu_launches": KERNELS_PER_RUN * args.steps,
                 "witness": {"mean_gamma": diag[1], "rms_gamma": diag[2], "alive": diag[0]}}
         print(json.dumps(line), flush=True)

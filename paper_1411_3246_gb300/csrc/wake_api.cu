@@ -757,19 +757,22 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
     long long hist[64];
     if ((rc = slip_stats(h, s, &ok, hist))) return rc;
     if (!ok) return step_sequential(h, nsteps - done);  // a beam slipping this fast: one step at a time
-    // the longest launch (whole waves of co-resident steps where possible; the first launch of
-    // a call, when a fresh beam's u_perp grows fastest, is one wave) whose predicted lists fit
-    const long long want = std::min<long long>(nsteps - done, done == 0 ? std::min(ctas_max, chmax) : chmax);
-    long long L = want, dcap_l = 0;
+    // the longest launch whose lists - as long as the budget allows, the prediction being
+    // only a guide for a fresh beam whose u_perp is still growing - hold twice the predicted
+    // count
+    long long L = std::min<long long>(nsteps - done, chmax), dcap_l = 0;
     for (;;) {
       long long pred = 0;
       for (int q = 0; q < 64 && (1LL << q) < L; ++q) pred += hist[q];
-      dcap_l = std::min<long long>(s.p.n_beam, 2 * pred + 65536);
-      const long long fit = (long long)(list_budget / (sizeof(int2) * (size_t)L));
-      if (dcap_l <= fit || L == 1) break;
+      dcap_l = std::min<long long>(s.p.n_beam, (long long)(list_budget / (sizeof(int2) * (size_t)L)));
+      if (2 * pred <= dcap_l || L == 1) break;
       L = L > ctas_max ? (L - 1) / ctas_max * ctas_max : L / 2;
     }
-    if (L >= ctas_max) L = L / ctas_max * ctas_max;
+    dcap_l = std::max<long long>(dcap_l, 1);
+    // a launch that does not finish the call ends on a whole wave (the next launch waits for
+    // it to drain); one that does keeps every remaining step (its last wave overlaps the
+    // tail of the one before)
+    if (L < nsteps - done && L >= ctas_max) L = L / ctas_max * ctas_max;
     const int ch = (int)std::max<long long>(1, L);
     const int dcap = (int)dcap_l;
     if (s.pgrid_cap < ch + 1) {

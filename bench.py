@@ -205,8 +205,9 @@ def config_dict(cfg, world, beam_steps):
 
 def batched_leg(wake, torch, n_sims, nsteps, rank, flush, world):
     """The batched sweep: n_sims simulations of uneven size, temperature and witness delay in
-    one handle (mixed form), nsteps beam steps by one wake_step call (one CUDA graph per step).
-    One untimed run (tile probes, graph capture), then one timed run from the initial beams."""
+    one handle (mixed form), nsteps beam steps by one wake_step call (every simulation's steps
+    pipelined in one persistent launch).  One untimed run (allocation), then one timed run
+    from the initial beams."""
     cfgs = synth.config_batch(n_sims=n_sims, n_steps=nsteps, seed=synth.SEED_BASE + 3 + 1000 * rank)
     stream = torch.cuda.Stream()
     pl = [synth.plasma_normals(c) for c in cfgs]
@@ -229,10 +230,6 @@ def batched_leg(wake, torch, n_sims, nsteps, rank, flush, world):
             stream.synchronize()
             times.append(ev[0].elapsed_time(ev[1]))
     st = [sim.status(i) for i in range(n_sims)]
-    tiles = {}
-    for i in range(n_sims):
-        t = "x".join(map(str, wake.wake_tile(sim.h, i)))
-        tiles[t] = tiles.get(t, 0) + 1
     sim.close()
     if any(x != wake.WAKE_OK for x in st):
         raise RuntimeError(f"batched leg: simulation status {st}")
@@ -242,10 +239,12 @@ def batched_leg(wake, torch, n_sims, nsteps, rank, flush, world):
             "beam_steps": nsteps, "plasma_pushes_per_run": pushes,
             "beam_pushes_per_run": sum(c.n_beam for c in cfgs) * nsteps,
             "beam_pushes_per_s": world * sum(c.n_beam for c in cfgs) * nsteps / t,
-            "tiles_nt_x_ppt": tiles, "first_run_ms": times[0],
+            "first_run_ms": times[0],
             "workload": "batched sweep: Nr in {128..1024}, Nxi in {512..4096} log-uniform, ppc 4, "
                         "u_th ~ U[0,0.02], witness delay ~ U[3.5,5.5], 64k-256k beam particles each",
-            "dtype": "f32", "graph": "one batched step captured once, replayed per step"}
+            "dtype": "f32",
+            "form": "every simulation's steps pipelined in one persistent launch (wide march, "
+                    "256-thread CTAs, two per SM); WAKE_BATCH_PIPELINE=0 takes the CUDA-graph step"}
 
 
 def large_leg(wake, torch, nsteps, rank, flush, world):

@@ -110,11 +110,14 @@ int wake_beam_push(wake_sim *s);
 
 /*
  * nsteps x (wake_beam_deposit, wake_plasma_march, wake_beam_push).  With several
- * simulations one step is a batched deposit, one march launch per tile class (concurrent
- * streams) and a batched push; the first call captures that step as a CUDA graph on the
- * handle's stream and every call replays it nsteps times (on the legacy default stream, or
- * while the caller's stream is capturing, the launches are issued directly).  With one
- * simulation
+ * simulations of the mixed form that all have beams, every simulation's steps run pipelined
+ * (as below) in one persistent cooperative launch, largest simulations first, each march in
+ * the wide form (the environment variable WAKE_BATCH_PIPELINE=0, read by wake_init, turns
+ * this off).  Otherwise, with several simulations, one step is a batched deposit, one march
+ * launch per tile class (concurrent streams) and a batched push; the first call captures that
+ * step as a CUDA graph on the handle's stream and every call replays it nsteps times (on the
+ * legacy default stream, or while the caller's stream is capturing, the launches are issued
+ * directly).  With one simulation
  * that has a beam, the steps run pipelined: the beam is sorted by xi cell and one
  * cooperative launch marches up to one step per SM, each step a few slices behind the one
  * before, pushing each cell of the beam as soon as its fields are solved (same arithmetic as

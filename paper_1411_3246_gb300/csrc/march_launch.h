@@ -34,6 +34,11 @@ size_t wide_ring_bytes(int np);
 int step_wide_max_ctas(int n1);
 size_t step_wide_window_bytes(int n1);
 cudaError_t launch_step_wide(const PipeArgs &a, int ctas, cudaStream_t stream);
+// Pipelined steps of many simulations (pipeline.cuh batch_step_kernel), wide form.
+struct BatchArgs;
+int batch_step_max_ctas(int max_n1, int bnt);
+size_t batch_ring_bytes(int max_np, int bnt);
+cudaError_t launch_batch_steps(const BatchArgs &b, int max_n1, int bnt, int ctas, cudaStream_t stream);
 
 // Global-memory ring slot storage one simulation needs (0 when the rings live in shared
 // memory).

@@ -77,4 +77,38 @@ cudaError_t launch_step_wide(const PipeArgs &a, int ctas, cudaStream_t stream) {
   return cudaLaunchCooperativeKernel((const void *)kern, dim3(ctas), dim3(kWideNT), args, smem, stream);
 }
 
+// The batched pipelined kernel in CTAs of bnt = 512 or 256 threads (the latter two per SM).
+template <int NT>
+static int batch_ctas(int max_n1) {
+  auto kern = batch_step_kernel<PolWide, NT, kWidePPT>;
+  const size_t smem = ((MarchSmem<PolWide>::bytes(max_n1, NT * kWidePPT) + 63) & ~(size_t)63) + 64;
+  if (smem > kMaxSmemPerCta || max_n1 > PolWide::kScanE * NT) return 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) return 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * sms;
+}
+template <int NT>
+static cudaError_t batch_launch(const BatchArgs &b, int max_n1, int ctas, cudaStream_t stream) {
+  auto kern = batch_step_kernel<PolWide, NT, kWidePPT>;
+  const size_t smem = ((MarchSmem<PolWide>::bytes(max_n1, NT * kWidePPT) + 63) & ~(size_t)63) + 64;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  BatchArgs arg = b;
+  void *args[] = {&arg};
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(ctas), dim3(NT), args, smem, stream);
+}
+
+int batch_step_max_ctas(int max_n1, int bnt) { return bnt == 256 ? batch_ctas<256>(max_n1) : batch_ctas<512>(max_n1); }
+
+size_t batch_ring_bytes(int max_np, int bnt) {
+  return bnt == 256 ? WideRings<float>::bytes(wide_slots<256, kWidePPT>(max_np)) : wide_ring_bytes(max_np);
+}
+
+cudaError_t launch_batch_steps(const BatchArgs &b, int max_n1, int bnt, int ctas, cudaStream_t stream) {
+  return bnt == 256 ? batch_launch<256>(b, max_n1, ctas, stream) : batch_launch<512>(b, max_n1, ctas, stream);
+}
+
 }  // namespace wake

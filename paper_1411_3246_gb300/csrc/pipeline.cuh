@@ -283,6 +283,46 @@ __global__ void __launch_bounds__(NT, 1) step_wide_kernel(PipeArgs a) {
   }
 }
 
+// Pipelined steps of many simulations in one persistent launch.  Work items are (simulation,
+// step) pairs in the order the host gives (all steps of a simulation consecutive, largest
+// simulations first); CTA c takes items c, c + gridDim.x, ...  An item's predecessor (the
+// same simulation's previous step) comes earlier in the order, so with every CTA resident
+// the earliest unfinished item can always run.  Every simulation is marched in the wide form.
+struct BatchSim {
+  PipeArgs p;  // the simulation's pipeline (its grids, progress, beam, lists); nsteps = steps
+};
+struct BatchArgs {
+  const BatchSim *sims;
+  const int2 *items;  // (simulation, step)
+  int nitems;
+  void *ring_bufs, *win_bufs;  // per CTA
+  size_t ring_stride, win_stride;
+};
+
+template <class Pol, int NT, int PPT>
+__global__ void __launch_bounds__(NT, (NT < 512 ? 512 / NT : 1)) batch_step_kernel(BatchArgs b) {
+  using R = typename Pol::R;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  for (int i = blockIdx.x; i < b.nitems; i += gridDim.x) {
+    const int2 it = b.items[i];
+    const PipeArgs &a = b.sims[it.x].p;
+    const int n1 = a.d.nr + 1;
+    const size_t base = (MarchSmem<Pol>::bytes(n1, NT * PPT) + 63) & ~(size_t)63;
+    int *ctl = (int *)(smem_raw + base);
+    R *win = (R *)((unsigned char *)b.win_bufs + (size_t)blockIdx.x * b.win_stride);
+    if (threadIdx.x == 0) {
+      ctl[0] = 0;
+      ctl[1] = 0;
+    }
+    __syncthreads();
+    PipeHooks<Pol, NT> hk{a, it.y, win, ctl, n1, a.d.nr, a.d.nxi, a.d.dr, a.d.dxi, a.d.rmax, a.d.ximax};
+    SimDesc d = a.d;
+    d.ring_buf = (unsigned char *)b.ring_bufs + (size_t)blockIdx.x * b.ring_stride;
+    march_body_wide<Pol, NT, PPT>(d, smem_raw, hk);
+    __syncthreads();
+  }
+}
+
 template <class Pol, int NT, int PPT>
 size_t step_smem_bytes(int n1) {
   return ((MarchSmem<Pol>::bytes(n1, NT * PPT) + 63) & ~(size_t)63) + sizeof(typename Pol::R) * 12 * (size_t)n1 + 64;

@@ -115,6 +115,10 @@ struct wake_sim {
   int64_t max_beam = 0;
   size_t max_ng = 0;
   cudaGraphExec_t step_graph = nullptr;  // one batched step, captured at the first wake_step
+  bool batch_pipeline = true;             // WAKE_BATCH_PIPELINE=0: batched steps by the graph
+  int batch_nt = 256;                     // threads per CTA of the pipelined batch (256 or 512)
+  void *bp_rings = nullptr, *bp_sims = nullptr, *bp_items = nullptr;  // pipelined batch scratch
+  size_t bp_rings_bytes = 0, bp_sims_bytes = 0, bp_items_bytes = 0;
 };
 
 namespace {
@@ -384,6 +388,8 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
   h->stream = (cudaStream_t)stream;
   h->sims.resize(n_sims);
   if (const char *t = std::getenv("WAKE_TILE_NT")) h->tile_nt_forced = std::atoi(t);
+  if (const char *t = std::getenv("WAKE_BATCH_PIPELINE")) h->batch_pipeline = std::atoi(t) != 0;
+  if (const char *t = std::getenv("WAKE_BATCH_NT")) h->batch_nt = std::atoi(t) == 512 ? 512 : 256;
   const size_t gs = gsize(h->precision);
   int rc = WAKE_OK;
   for (int i = 0; i < n_sims && rc == WAKE_OK; ++i) {
@@ -699,6 +705,209 @@ int step_sequential(wake_sim *h, int nsteps) {
   return WAKE_OK;
 }
 
+int upload_beam_descs(wake_sim *h) {
+  std::vector<BeamDesc> bd(h->n);
+  for (int i = 0; i < h->n; ++i) bd[i] = beam_desc(h->sims[i], nullptr);
+  CUDA_TRY(cudaMemcpyAsync(h->d_bdesc, bd.data(), sizeof(BeamDesc) * h->n, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));  // bd is a host temporary
+  return WAKE_OK;
+}
+
+// Several simulations with beams, mixed form: pipelined steps of all of them in one
+// persistent launch (pipeline.cuh batch_step_kernel), every simulation in the wide form.
+// Returns WAKE_OK after running, or a positive value when the path does not apply (the
+// caller then takes the graph path).
+int step_batch_pipelined(wake_sim *h, int nsteps) {
+  if (h->precision != WAKE_MIXED || !h->batch_pipeline) return 1;
+  int max_n1 = 0, max_np = 0;
+  for (auto &s : h->sims) {
+    if (s.p.n_beam == 0 || !s.beam || !s.plasma) return 1;
+    max_n1 = std::max(max_n1, s.p.nr + 1);
+    max_np = std::max(max_np, s.np);
+  }
+  const int ctas_max = batch_step_max_ctas(max_n1, h->batch_nt);
+  if (ctas_max < 1) return 1;
+  int rc;
+  // every beam must slip less than half a cell per step (4x headroom), as for one simulation
+  for (auto &s : h->sims) {
+    BeamDesc b = beam_desc(s, nullptr);
+    CUDA_TRY(cudaMemsetAsync(s.slip, 0, sizeof(unsigned long long) + 64 * sizeof(int), h->stream));
+    const double span = 2.0 * (s.p.ximax / s.p.nxi) / (2.0 * s.p.ds);
+    beam_slip_kernel<float><<<grid_blocks(s.p.n_beam, 256), 256, 0, h->stream>>>(b, span, s.slip, (int *)(s.slip + 1));
+  }
+  CUDA_TRY(cudaGetLastError());
+  std::vector<unsigned long long> rates(h->n);
+  for (int i = 0; i < h->n; ++i)
+    CUDA_TRY(cudaMemcpyAsync(&rates[i], h->sims[i].slip, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  for (int i = 0; i < h->n; ++i) {
+    double rate;
+    std::memcpy(&rate, &rates[i], sizeof(rate));
+    const Sim &s = h->sims[i];
+    if (4.0 * s.p.ds * rate > 0.5 * (s.p.ximax / s.p.nxi)) return 1;
+  }
+  // steps per launch: the per-step density grids of all simulations within half the free memory
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  size_t per_step = 0;
+  for (auto &s : h->sims) per_step += sizeof(float) * s.ng;
+  const int chmax = (int)std::max<size_t>(1, std::min<size_t>(nsteps, free_b / 2 / per_step - 1));
+  // per-CTA ring and window buffers
+  const int ctas = ctas_max;
+  const size_t rb = batch_ring_bytes(max_np, h->batch_nt), wb = step_wide_window_bytes(max_n1);
+  if (h->bp_rings_bytes < (rb + wb) * ctas) {
+    if (h->bp_rings) cudaFree(h->bp_rings);
+    h->bp_rings = nullptr;
+    h->bp_rings_bytes = 0;
+    if ((rc = dalloc(&h->bp_rings, (rb + wb) * ctas))) return rc;
+    h->bp_rings_bytes = (rb + wb) * ctas;
+  }
+  // simulations largest work first
+  std::vector<int> order(h->n);
+  for (int i = 0; i < h->n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (double)h->sims[a].np * (h->sims[a].p.nxi + 1) > (double)h->sims[b].np * (h->sims[b].p.nxi + 1);
+  });
+  int done = 0;
+  while (done < nsteps) {
+    const int ch = std::min(nsteps - done, chmax);
+    std::vector<BatchSim> bs(h->n);
+    for (int i = 0; i < h->n; ++i) {
+      Sim &s = h->sims[i];
+      const size_t gbytes = sizeof(float) * s.ng;
+      const int dcap = (int)std::min<int64_t>(s.p.n_beam, 4096);
+      if (s.pgrid_cap < ch + 1) {
+        void *old[] = {s.pgrids, s.progress, s.defer_cnt};
+        for (void *q : old)
+          if (q) cudaFree(q);
+        s.pgrids = nullptr;
+        s.progress = nullptr;
+        s.defer_cnt = nullptr;
+        s.pgrid_cap = 0;
+        if ((rc = dalloc(&s.pgrids, gbytes * (ch + 1))) || (rc = dalloc(&s.progress, sizeof(int) * ch)) ||
+            (rc = dalloc(&s.defer_cnt, sizeof(int) * ch)))
+          return rc;
+        s.pgrid_cap = ch + 1;
+      }
+      if (s.defer_bytes < sizeof(int2) * (size_t)dcap * ch) {
+        if (s.defer_list) cudaFree(s.defer_list);
+        s.defer_list = nullptr;
+        s.defer_bytes = 0;
+        if ((rc = dalloc(&s.defer_list, sizeof(int2) * (size_t)dcap * ch))) return rc;
+        s.defer_bytes = sizeof(int2) * (size_t)dcap * ch;
+      }
+      if (!s.target && (rc = dalloc(&s.target, sizeof(int) * s.p.n_beam))) return rc;
+      if ((rc = sort_beam(h, s))) return rc;
+      BeamDesc b = beam_desc(s, nullptr);
+      b.nb = s.pgrids;
+      CUDA_TRY(cudaMemsetAsync(s.pgrids, 0, gbytes * (ch + 1), h->stream));
+      beam_deposit_kernel<float, float><<<grid_blocks(s.p.n_beam, 256), 256, 0, h->stream>>>(b);
+      nb_normalize_kernel<float><<<grid_blocks((int64_t)s.ng, 256), 256, 0, h->stream>>>((float *)s.pgrids, s.p.nr, s.p.nxi,
+                                                                                       b.dr, b.dxi);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(cudaMemsetAsync(s.progress, 0, sizeof(int) * ch, h->stream));
+      CUDA_TRY(cudaMemsetAsync(s.defer_cnt, 0, sizeof(int) * ch, h->stream));
+      CUDA_TRY(cudaMemsetAsync(s.target, 0xff, sizeof(int) * s.p.n_beam, h->stream));
+      PipeArgs &a = bs[i].p;
+      a = PipeArgs{};
+      SimDesc &d = a.d;
+      d.nr = s.p.nr;
+      d.nxi = s.p.nxi;
+      d.np = s.np;
+      d.has_beam = 1;
+      d.rmax = s.p.rmax;
+      d.ximax = s.p.ximax;
+      d.dr = s.p.rmax / s.p.nr;
+      d.dxi = s.p.ximax / s.p.nxi;
+      d.r0 = s.r0;
+      d.ur0 = s.ur0;
+      d.lz = s.lz;
+      d.G0 = s.G0;
+      d.w = s.w;
+      d.psi = s.psi;
+      d.ez = s.ez;
+      d.er = s.er;
+      d.bth = s.bth;
+      d.status = s.status;
+      a.grids = s.pgrids;
+      a.ng = s.ng;
+      a.progress = s.progress;
+      a.nsteps = ch;
+      a.write_last = 1;
+      a.x = b.x;
+      a.y = b.y;
+      a.ux = b.ux;
+      a.uy = b.uy;
+      a.xi = b.xi;
+      a.uz = b.uz;
+      a.flags = b.lost;
+      a.bin_start = s.bin_start;
+      a.wd = b.wd;
+      a.ww = b.ww;
+      a.ds = s.p.ds;
+      a.spin_limit = 1LL << 24;
+      a.defer_cnt = s.defer_cnt;
+      a.defer_list = s.defer_list;
+      a.defer_cap = dcap;
+      a.target = s.target;
+    }
+    if ((rc = upload_beam_descs(h))) return rc;  // the sort swapped the beam copies
+    std::vector<int2> items;
+    items.reserve((size_t)h->n * ch);
+    for (int i : order)
+      for (int t = 0; t < ch; ++t) items.push_back(make_int2(i, t));
+    const size_t sb = sizeof(BatchSim) * h->n, ib = sizeof(int2) * items.size();
+    if (h->bp_sims_bytes < sb) {
+      if (h->bp_sims) cudaFree(h->bp_sims);
+      h->bp_sims = nullptr;
+      h->bp_sims_bytes = 0;
+      if ((rc = dalloc(&h->bp_sims, sb))) return rc;
+      h->bp_sims_bytes = sb;
+    }
+    if (h->bp_items_bytes < ib) {
+      if (h->bp_items) cudaFree(h->bp_items);
+      h->bp_items = nullptr;
+      h->bp_items_bytes = 0;
+      if ((rc = dalloc(&h->bp_items, ib))) return rc;
+      h->bp_items_bytes = ib;
+    }
+    CUDA_TRY(cudaMemcpyAsync(h->bp_sims, bs.data(), sb, cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(h->bp_items, items.data(), ib, cudaMemcpyHostToDevice, h->stream));
+    BatchArgs ba{};
+    ba.sims = (const BatchSim *)h->bp_sims;
+    ba.items = (const int2 *)h->bp_items;
+    ba.nitems = (int)items.size();
+    ba.ring_bufs = h->bp_rings;
+    ba.ring_stride = rb;
+    ba.win_bufs = (char *)h->bp_rings + rb * ctas;
+    ba.win_stride = wb;
+    const int nctas = std::min(ctas, ba.nitems);
+    if (h->ev_used == (int)h->ev.size()) {
+      std::pair<cudaEvent_t, cudaEvent_t> q{};
+      CUDA_TRY(cudaEventCreate(&q.first));
+      if (cudaEventCreate(&q.second) != cudaSuccess) {
+        cudaEventDestroy(q.first);
+        return fail(WAKE_ECUDA, "cudaEventCreate");
+      }
+      h->ev.push_back(q);
+    }
+    CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].first, h->stream));
+    const cudaError_t e = launch_batch_steps(ba, max_n1, h->batch_nt, nctas, h->stream);
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("pipelined batch launch: ") + cudaGetErrorString(e));
+    CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].second, h->stream));
+    ++h->ev_used;
+    // the host arrays are read by the copies above: finish them before bs and items go
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (auto &s : h->sims) {
+      CUDA_TRY(cudaMemcpyAsync(s.nb, (char *)s.pgrids + sizeof(float) * s.ng * (ch - 1), sizeof(float) * s.ng,
+                               cudaMemcpyDeviceToDevice, h->stream));
+      s.marched = true;
+    }
+    done += ch;
+  }
+  return WAKE_OK;
+}
+
 // Several simulations: one step is the batched deposit, one march launch per tile class
 // (forked streams), the batched push.  The step is captured once as a CUDA graph and
 // replayed; on the legacy default stream, or while the caller is capturing, the launches
@@ -908,7 +1117,11 @@ int wake_step(wake_sim *h, int nsteps) {
     const int ctas = s.wide ? step_wide_max_ctas(s.p.nr + 1) : step_max_ctas(h->precision == WAKE_FP64, s.p.nr + 1, s.np);
     if (ctas > 0) return step_pipelined(h, nsteps, ctas);
   }
-  if (h->n > 1) return step_batched(h, nsteps);
+  if (h->n > 1) {
+    const int rc = step_batch_pipelined(h, nsteps);
+    if (rc <= 0) return rc;
+    return step_batched(h, nsteps);
+  }
   return step_sequential(h, nsteps);
 }
 
@@ -1047,6 +1260,9 @@ void wake_destroy(wake_sim *h) {
   }
   if (h->fork) cudaEventDestroy(h->fork);
   if (h->step_graph) cudaGraphExecDestroy(h->step_graph);
+  if (h->bp_rings) cudaFree(h->bp_rings);
+  if (h->bp_sims) cudaFree(h->bp_sims);
+  if (h->bp_items) cudaFree(h->bp_items);
   if (h->d_bdesc) cudaFree(h->d_bdesc);
   for (auto &q : h->ev) {
     cudaEventDestroy(q.first);

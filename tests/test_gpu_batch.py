@@ -126,10 +126,11 @@ def test_mixed_tile_widths_match_oracle_linear(wk, nt, monkeypatch):
             assert np.abs(got[k] - ref[k]).max() <= 1e-5 * scale, (nt, k)
 
 
-def test_batched_mixed_autotuned_steps_match_oracle(wk):
+def test_batched_mixed_autotuned_steps_match_oracle(wk, monkeypatch):
     """Autotuned tiles, graph path, mixed form: witness mean energy gain within 0.5% and
     fields within 1e-4 of peak |E_z| (warm plasma) of the FP64 oracle."""
     import torch
+    monkeypatch.setenv("WAKE_BATCH_PIPELINE", "0")
     cfgs = small_batch()
     for c in cfgs:
         c.ds = 50.0
@@ -150,3 +151,41 @@ def test_batched_mixed_autotuned_steps_match_oracle(wk):
         assert abs(gain - gain_ref) <= 0.005 * abs(gain_ref), (i, gain, gain_ref)
         scale = np.abs(ref["ez"]).max()
         assert np.abs(res[i]["ez"] - ref["ez"]).max() <= 1e-4 * scale, i
+
+
+def _mixed_batch_run(wk, cfgs, nsteps):
+    import torch
+    with wk.Simulations(cfgs, wk.WAKE_MIXED, torch.cuda.Stream()) as s:
+        keep = _load(wk, s, cfgs)
+        d0 = s.diagnostics()
+        wk.wake_step(s.h, nsteps)
+        kern_ms = wk.wake_step_kernel_ms(s.h)
+        res = _collect(wk, s, cfgs)
+        d1 = s.diagnostics()
+        del keep
+    return d0, d1, res, kern_ms
+
+
+def test_batched_pipelined_steps_match_oracle_and_graph_path(wk, monkeypatch):
+    """Mixed form, one persistent launch of every simulation's pipelined steps (the default
+    for a mixed handle whose simulations all have beams): witness energy gain within 0.5% and
+    fields within 1e-4 of peak |E_z| of the FP64 oracle, and the graph path's results within
+    FP32 rounding."""
+    cfgs = small_batch()
+    for c in cfgs:
+        c.ds = 50.0
+    d0, d1, res, kern_ms = _mixed_batch_run(wk, cfgs, 3)
+    assert kern_ms > 0.0  # the pipelined launch ran
+    monkeypatch.setenv("WAKE_BATCH_PIPELINE", "0")
+    _, g1, gres, gms = _mixed_batch_run(wk, cfgs, 3)
+    assert gms == 0.0  # the graph path launches no pipelined kernel
+    for i, cfg in enumerate(cfgs):
+        ref, bm = _oracle_steps(cfg, 3)
+        dr = oracle.diagnostics(cfg, bm)
+        gain, gain_ref = d1[i][1] - d0[i][1], dr[1] - d0[i][1]
+        assert abs(gain - gain_ref) <= 0.005 * abs(gain_ref), (i, gain, gain_ref)
+        scale = np.abs(ref["ez"]).max()
+        assert np.abs(res[i]["ez"] - ref["ez"]).max() <= 1e-4 * scale, i
+        assert np.array_equal(res[i]["lost"], gres[i]["lost"])
+        assert np.abs(res[i]["ez"] - gres[i]["ez"]).max() <= 1e-4 * scale, i
+        assert abs((d1[i][1] - g1[i][1])) <= 1e-3 * abs(gain_ref) + 1e-6 * cfg.gamma_b, i

@@ -137,13 +137,21 @@ def dist_setup():
 
 
 def barrier_max(x, world):
+    """The largest x over the ranks (each rank's timed region ends at its own clock; the job's
+    time is the slowest rank's).  NCCL reduces a CUDA tensor, gloo a host one."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(base, rank):
+    """Seed of rank's replica: the replicas are independent simulations of the same workload."""
+    return base + 1000 * rank
 
 
 def barrier(world):
@@ -208,7 +216,7 @@ def batched_leg(wake, torch, n_sims, nsteps, rank, flush, world):
     one handle (mixed form), nsteps beam steps by one wake_step call (every simulation's steps
     pipelined in one persistent launch).  One untimed run (allocation), then one timed run
     from the initial beams."""
-    cfgs = synth.config_batch(n_sims=n_sims, n_steps=nsteps, seed=synth.SEED_BASE + 3 + 1000 * rank)
+    cfgs = synth.config_batch(n_sims=n_sims, n_steps=nsteps, seed=replica_seed(synth.SEED_BASE + 3, rank))
     stream = torch.cuda.Stream()
     pl = [synth.plasma_normals(c) for c in cfgs]
     bm = [synth.beam_normals(c) for c in cfgs]
@@ -251,7 +259,7 @@ def large_leg(wake, torch, nsteps, rank, flush, world):
     """The large configuration (mixed, the wide march form): one run of nsteps beam steps from
     the initial beam by one wake_step call, after an untimed run of one step (allocation)."""
     cfg = synth.config_large()
-    cfg.seed += 1000 * rank
+    cfg.seed = replica_seed(cfg.seed, rank)
     stream = torch.cuda.Stream()
     nm_p = torch.from_numpy(synth.plasma_normals(cfg)).pin_memory()
     nm_b = torch.from_numpy(synth.beam_normals(cfg)).pin_memory()
@@ -286,7 +294,7 @@ def adjoint_case(nsteps, rank):
     """The differentiation workload: the linear-driver grid (Nr=128 over 6, 4 rings/cell) at
     Nxi=1024 over 10, two bunches (witness at the batched sweep's first delay), 262,144 beam
     particles, u_th = 0.005, a 64-bin witness profile."""
-    cfg = synth.config_batch(n_sims=1, seed=synth.SEED_BASE + 4 + 1000 * rank)[0]
+    cfg = synth.config_batch(n_sims=1, seed=replica_seed(synth.SEED_BASE + 4, rank))[0]
     cfg.nr, cfg.nxi, cfg.ppc = 128, 1024, 4
     cfg = synth.two_bunch(cfg, 0.3, cfg.xi_w - cfg.xi_d, 262144)
     cfg.u_th = 0.005
@@ -355,7 +363,7 @@ def main():
     if args.n_beam:
         cfg = synth.two_bunch(cfg, 0.3, 4.5, args.n_beam)
     nbs = args.beam_steps
-    cfg.seed += 1000 * rank  # independent replicas
+    cfg.seed = replica_seed(cfg.seed, rank)  # independent replicas
     nm_p = torch.from_numpy(synth.plasma_normals(cfg)).pin_memory()
     nm_b = torch.from_numpy(synth.beam_normals(cfg)).pin_memory()
     stream = torch.cuda.Stream()

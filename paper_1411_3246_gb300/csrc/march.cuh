@@ -132,7 +132,7 @@ struct PolMixed {
 };
 // The mixed arithmetic for boxes too large for one CTA's shared memory to hold the rings
 // (up to 2048 radial cells and 65,536 rings): rings in global memory, processed in chunks,
-// not re-sorted; block scans of up to 5 nodes per thread.
+// re-sorted by cell every two slices; block scans of up to 5 nodes per thread.
 struct PolWide {
   using R = float;
   using Acc = float;
@@ -140,7 +140,7 @@ struct PolWide {
   using G = float;
   using W = FF;
   static constexpr int NT = 512;
-  static constexpr int kSortEvery = 0;
+  static constexpr int kSortEvery = 2;  // rings re-sorted by cell through a second global buffer
   static constexpr bool kSmemRings = false;
   static constexpr bool kTables = false;
   static constexpr int kScanE = 5;

@@ -31,9 +31,11 @@ bool march_tile_mixed_small(int nt, int ppt, TileFns *out);
 TileFns march_tile_wide();
 size_t wide_ring_bytes(int np);
 // Pipelined steps in the wide form: shared memory fits, co-resident CTAs, launch.
-int step_wide_max_ctas(int n1);
+// Pipelined steps in the wide form, CTAs of nt = 256 (two per SM) or 512 threads.
+int step_wide_max_ctas(int n1, int nt);
 size_t step_wide_window_bytes(int n1);
-cudaError_t launch_step_wide(const PipeArgs &a, int ctas, cudaStream_t stream);
+size_t step_wide_ring_bytes(int np, int nt);
+cudaError_t launch_step_wide(const PipeArgs &a, int nt, int ctas, cudaStream_t stream);
 // Pipelined steps of many simulations (pipeline.cuh batch_step_kernel), wide form.
 struct BatchArgs;
 int batch_step_max_ctas(int max_n1, int bnt);

@@ -55,26 +55,41 @@ size_t wide_ring_bytes(int np) { return WideRings<float>::bytes(wide_slots<kWide
 
 size_t step_wide_window_bytes(int n1) { return sizeof(float) * 12 * (size_t)n1; }
 
-int step_wide_max_ctas(int n1) {
-  auto kern = step_wide_kernel<PolWide, kWideNT, kWidePPT>;
-  const size_t smem = step_wide_smem(n1);
-  if (smem > kMaxSmemPerCta) return 0;
+template <int NT>
+static size_t step_wide_smem_nt(int n1) {
+  return ((MarchSmem<PolWide>::bytes(n1, NT * kWidePPT) + 63) & ~(size_t)63) + 64;
+}
+template <int NT>
+static int step_wide_ctas(int n1) {
+  auto kern = step_wide_kernel<PolWide, NT, kWidePPT>;
+  const size_t smem = step_wide_smem_nt<NT>(n1);
+  if (smem > kMaxSmemPerCta || n1 > PolWide::kScanE * NT) return 0;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
   int per_sm = 0, dev = 0, sms = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kWideNT, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) return 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   return per_sm * sms;
 }
-
-cudaError_t launch_step_wide(const PipeArgs &a, int ctas, cudaStream_t stream) {
-  auto kern = step_wide_kernel<PolWide, kWideNT, kWidePPT>;
-  const size_t smem = step_wide_smem(a.d.nr + 1);
+template <int NT>
+static cudaError_t step_wide_launch(const PipeArgs &a, int ctas, cudaStream_t stream) {
+  auto kern = step_wide_kernel<PolWide, NT, kWidePPT>;
+  const size_t smem = step_wide_smem_nt<NT>(a.d.nr + 1);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   PipeArgs arg = a;
   void *args[] = {&arg};
-  return cudaLaunchCooperativeKernel((const void *)kern, dim3(ctas), dim3(kWideNT), args, smem, stream);
+  return cudaLaunchCooperativeKernel((const void *)kern, dim3(ctas), dim3(NT), args, smem, stream);
+}
+
+int step_wide_max_ctas(int n1, int nt) { return nt == 256 ? step_wide_ctas<256>(n1) : step_wide_ctas<512>(n1); }
+
+size_t step_wide_ring_bytes(int np, int nt) {
+  return nt == 256 ? WideRings<float>::bytes(wide_slots<256, kWidePPT>(np)) : wide_ring_bytes(np);
+}
+
+cudaError_t launch_step_wide(const PipeArgs &a, int nt, int ctas, cudaStream_t stream) {
+  return nt == 256 ? step_wide_launch<256>(a, ctas, stream) : step_wide_launch<512>(a, ctas, stream);
 }
 
 // The batched pipelined kernel in CTAs of bnt = 512 or 256 threads (the latter two per SM).

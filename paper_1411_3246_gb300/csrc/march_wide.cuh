@@ -2,26 +2,92 @@
 // cells and 65,536 rings per slice, the mixed arithmetic of PolWide): the node arrays and
 // the radial solves stay in shared memory as in march_body, the ring slots live in a global
 // buffer and every ring pass runs over them in chunks of NT x PPT slots (the same per-ring
-// code, offset by the chunk).  Rings are not re-sorted; the stage-2 Gamma and force, which
-// march_body keeps in registers between its passes, get slot arrays of their own.
+// code, offset by the chunk).  Every two slices the rings are re-sorted by cell through a
+// second buffer; the stage-2 Gamma and force, which march_body keeps in registers between its
+// passes, get slot arrays of their own.
 #pragma once
 
 #include "march.cuh"
 
 namespace wake {
 
-// Ring slots of the wide march: RingSoA (np_pad slots) followed by the stage-2 G2, F2.
+// Ring slots of the wide march: RingSoA (np_pad slots) followed by the stage-2 G2, F2, and a
+// second copy of the ring state (c, f, u_r and the constants) that the re-sort scatters into.
 template <class R>
 struct WideRings {
-  RingSoA<R> s;
+  RingSoA<R> s, alt;
   R *G2, *F2;
-  __host__ __device__ static size_t bytes(int slots) { return RingSoA<R>::bytes(slots) + 2 * sizeof(R) * (size_t)slots + 64; }
+  __host__ __device__ static size_t bytes(int slots) { return 2 * RingSoA<R>::bytes(slots) + 2 * sizeof(R) * (size_t)slots + 128; }
   __device__ __forceinline__ void carve(void *base, int slots) {
     s.carve(base, slots);
     G2 = (R *)(((uintptr_t)(s.F1 + slots) + 31) & ~(uintptr_t)31);
     F2 = G2 + slots;
+    alt.carve((void *)(((uintptr_t)(F2 + slots) + 31) & ~(uintptr_t)31), slots);
   }
 };
+
+// Re-sort the rings of a wide march by cell (counting sort through the second buffer, then
+// the buffers swap): rank r goes to chunk r / SLOTS, thread (r % SLOTS) / PPT, ring
+// (r % SLOTS) % PPT, so each thread's rings are consecutive in radius again.  Ends with a
+// barrier.
+template <class Pol, int NT, int PPT>
+__device__ __forceinline__ void resort_rings_wide(MarchSmem<Pol> &sm, WideRings<typename Pol::R> &wr, int np, int nr,
+                                                  int nch) {
+  constexpr int SLOTS = NT * PPT;
+  const int t = threadIdx.x, n1 = nr + 1;
+  for (int m = t; m < n1; m += NT) sm.cnt[m] = 0;
+  __syncthreads();
+  for (int ch = 0; ch < nch; ++ch) {
+    const int base = ch * SLOTS, npc = np - base < SLOTS ? np - base : SLOTS;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+      if (t * PPT + p < npc) {
+        const int sl = base + p * NT + t;
+        wr.alt.G1[sl] = __int_as_float(atomicAdd(&sm.cnt[wr.s.c[sl]], 1));  // rank in its cell
+      }
+  }
+  __syncthreads();
+  if (t < 32) {  // exclusive scan of the counts
+    const int E = (n1 + 31) / 32, beg = min(n1, t * E), end = min(n1, beg + E);
+    int s = 0;
+    for (int q = beg; q < end; ++q) s += sm.cnt[q];
+    int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(kFull, incl, o);
+      if (t >= o) incl += u;
+    }
+    int run = incl - s;
+    for (int q = beg; q < end; ++q) {
+      const int v = sm.cnt[q];
+      sm.cnt[q] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+  for (int ch = 0; ch < nch; ++ch) {
+    const int base = ch * SLOTS, npc = np - base < SLOTS ? np - base : SLOTS;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+      if (t * PPT + p < npc) {
+        const int sl = base + p * NT + t;
+        const int c = wr.s.c[sl];
+        const int r = sm.cnt[c] + __float_as_int(wr.alt.G1[sl]);
+        const int rr = r % SLOTS;
+        const int dl = (r - rr) + (rr % PPT) * NT + rr / PPT;
+        wr.alt.c[dl] = c;
+        wr.alt.f[dl] = wr.s.f[sl];
+        wr.alt.ur[dl] = wr.s.ur[sl];
+        wr.alt.lz[dl] = wr.s.lz[sl];
+        wr.alt.G0[dl] = wr.s.G0[sl];
+        wr.alt.w[dl] = wr.s.w[sl];
+      }
+  }
+  __syncthreads();
+  const RingSoA<typename Pol::R> tmp = wr.s;
+  wr.s = wr.alt;
+  wr.alt = tmp;
+}
 
 template <class R>
 __device__ __forceinline__ RingSoA<R> shifted(const RingSoA<R> &r, int off) {
@@ -54,7 +120,7 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
   sm.carve(smem_raw, n1, SLOTS);
   WideRings<R> wr;
   wr.carve(d.ring_buf, nch * SLOTS);
-  const RingSoA<R> &rs = wr.s;
+  const RingSoA<R> &rs = wr.s;  // follows the swaps of the re-sort
   const double drd = d.dr;
   const R h = (R)d.dxi, R_wall = (R)d.rmax, dR = (R)drd, inv_dr = (R)(1.0 / drd);
   const NodeGeo<Pol> geo{sm.invR, sm.invV, sm.alpha, sm.ga, sm.gb, sm.gc, nr, dR, inv_dr, (R)(1.0 / (drd * drd)),
@@ -126,6 +192,7 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
   __syncthreads();
 
   for (int k = 0; k <= nxi; ++k) {
+    if (Pol::kSortEvery > 0 && k > 0 && k % Pol::kSortEvery == 0) resort_rings_wide<Pol, NT, PPT>(sm, wr, np, nr, nch);
     const R *nbk = (k & 1) ? sm.nb1 : sm.nb0, *nbk1 = (k & 1) ? sm.nb0 : sm.nb1;
     if (!hk.wait_rows(k)) break;
     if (k == 0)

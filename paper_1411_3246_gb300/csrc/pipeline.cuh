@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(PipeArgs a) {
 
 // The wide form: rings and the four-slice field window in per-CTA global buffers.
 template <class Pol, int NT, int PPT>
-__global__ void __launch_bounds__(NT, 1) step_wide_kernel(PipeArgs a) {
+__global__ void __launch_bounds__(NT, (NT < 512 ? 512 / NT : 1)) step_wide_kernel(PipeArgs a) {
   using R = typename Pol::R;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n1 = a.d.nr + 1;

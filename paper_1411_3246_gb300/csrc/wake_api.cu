@@ -117,6 +117,8 @@ struct wake_sim {
   cudaGraphExec_t step_graph = nullptr;  // one batched step, captured at the first wake_step
   bool batch_pipeline = true;             // WAKE_BATCH_PIPELINE=0: batched steps by the graph
   int batch_nt = 256;                     // threads per CTA of the pipelined batch (256 or 512)
+  int step_form = 0;                      // one simulation's pipelined steps: 0 tile (or wide 512 when
+                                          // no tile fits), 256 / 512 wide form (WAKE_STEP_FORM)
   void *bp_rings = nullptr, *bp_sims = nullptr, *bp_items = nullptr;  // pipelined batch scratch
   size_t bp_rings_bytes = 0, bp_sims_bytes = 0, bp_items_bytes = 0;
 };
@@ -390,6 +392,7 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
   if (const char *t = std::getenv("WAKE_TILE_NT")) h->tile_nt_forced = std::atoi(t);
   if (const char *t = std::getenv("WAKE_BATCH_PIPELINE")) h->batch_pipeline = std::atoi(t) != 0;
   if (const char *t = std::getenv("WAKE_BATCH_NT")) h->batch_nt = std::atoi(t) == 512 ? 512 : 256;
+  if (const char *t = std::getenv("WAKE_STEP_FORM")) h->step_form = std::atoi(t);
   const size_t gs = gsize(h->precision);
   int rc = WAKE_OK;
   for (int i = 0; i < n_sims && rc == WAKE_OK; ++i) {
@@ -948,7 +951,7 @@ int step_batched(wake_sim *h, int nsteps) {
 // nsteps beam steps of a single simulation as pipelined cooperative launches (pipeline.cuh).
 // Per launch: sort the beam by xi cell, deposit the first step's density into grid 0, zero
 // the grids of the later steps and the progress counters, launch.
-int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
+int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
   Sim &s = h->sims[0];
   const int fp64 = h->precision == WAKE_FP64;
   const size_t gs = gsize(h->precision), gbytes = gs * s.ng;
@@ -956,8 +959,9 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
   size_t free_b = 0, total_b = 0;
   CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   const int chmax = (int)std::min<size_t>(1024, std::max<size_t>(1, free_b / 4 / gbytes - 1));
-  const size_t rb = s.wide ? wide_ring_bytes(s.np) : ring_buf_bytes(fp64);
-  const size_t wb = s.wide ? step_wide_window_bytes(s.p.nr + 1) : 0;
+  const int wnt = wide_nt;  // 0: the tiled step kernel
+  const size_t rb = wnt ? step_wide_ring_bytes(s.np, wnt) : ring_buf_bytes(fp64);
+  const size_t wb = wnt ? step_wide_window_bytes(s.p.nr + 1) : 0;
   int rc, done = 0, last_ch = 0;
   // the lists of slipped particles: up to 16 GB (or an eighth of the free memory) for a launch
   const size_t list_budget = std::min<size_t>((size_t)16 << 30, free_b / 8);
@@ -1091,7 +1095,7 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max) {
       h->ev.push_back(q);
     }
     CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].first, h->stream));
-    const cudaError_t e = s.wide ? launch_step_wide(a, ctas, h->stream) : launch_step(fp64, a, s.np, ctas, h->stream);
+    const cudaError_t e = wnt ? launch_step_wide(a, wnt, ctas, h->stream) : launch_step(fp64, a, s.np, ctas, h->stream);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("pipelined step launch: ") + cudaGetErrorString(e));
     CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].second, h->stream));
     ++h->ev_used;
@@ -1114,8 +1118,10 @@ int wake_step(wake_sim *h, int nsteps) {
   if (h->n == 1 && h->sims[0].p.n_beam > 0) {
     Sim &s = h->sims[0];
     if (!s.beam || !s.plasma) return fail(WAKE_ESTATE, "wake_step needs wake_load_plasma and wake_load_beam");
-    const int ctas = s.wide ? step_wide_max_ctas(s.p.nr + 1) : step_max_ctas(h->precision == WAKE_FP64, s.p.nr + 1, s.np);
-    if (ctas > 0) return step_pipelined(h, nsteps, ctas);
+    int wnt = s.wide ? 512 : 0;
+    if (h->precision == WAKE_MIXED && (h->step_form == 256 || h->step_form == 512)) wnt = h->step_form;
+    const int ctas = wnt ? step_wide_max_ctas(s.p.nr + 1, wnt) : step_max_ctas(h->precision == WAKE_FP64, s.p.nr + 1, s.np);
+    if (ctas > 0) return step_pipelined(h, nsteps, ctas, wnt);
   }
   if (h->n > 1) {
     const int rc = step_batch_pipelined(h, nsteps);

@@ -44,6 +44,21 @@ FLOP_PER_PUSH = 236.0
 FLOP_PER_NODE_STAGE = 62.0
 FLOP_PER_BEAM_PUSH = 140.0
 BEAM_STEPS = 200
+# DRAM traffic of one launch of the step kernel on this workload (200 steps), from one ncu
+# capture with one pass (dram__bytes_read.sum + dram__bytes_write.sum: 945.70 + 121.04 MB),
+# valid while the kernel's sources hash to STEP_TRAFFIC_SOURCES
+STEP_TRAFFIC_BYTES = 1066.74e6
+STEP_TRAFFIC_SOURCES = "12e1f0e1b0e69820"
+STEP_SOURCES = ("beam.cuh", "march.cuh", "march_mixed.cu", "march_wide.cuh", "pipeline.cuh", "wake_common.cuh")
+
+
+def step_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in STEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_1411_3246_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 # kernels of one pipelined wake_step launch sequence: slip bound, three of the cell sort,
 # deposit and normalise of the first step's density, the step kernel
 KERNELS_PER_RUN = 7
@@ -468,8 +483,11 @@ def main():
     kern_s = sum(kern_ms) / len(kern_ms) / 1e3
     achieved = flops_run / kern_s / 1e12
     peak = fp32_peak_tflops(sm_mhz)
+    default_workload = (cfg.nr, cfg.nxi, cfg.n_beam, nbs) == (512, 2048, 1 << 20, BEAM_STEPS)
+    traffic = STEP_TRAFFIC_BYTES if default_workload and step_sources_hash() == STEP_TRAFFIC_SOURCES else None
     roof = {"kernel": "step_kernel<PolMixed>", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
             "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max clock of {src} peaks file)",
             "kernel_ms": 1e3 * kern_s, "kernel_share_of_run": kern_s * 1e3 / (sum(run_ms) / len(run_ms))}
     if rank == 0:

@@ -278,6 +278,9 @@ __device__ __forceinline__ int beam_bin(const BeamDesc &b, int64_t j) {
 // slipped a given span) in hist.  Both zeroed before.
 template <class BT>
 __global__ void beam_slip_kernel(BeamDesc b, double span, unsigned long long *out, int *hist) {
+  __shared__ int sh[64];  // the block's histogram, added to hist once per bin
+  for (int q = threadIdx.x; q < 64; q += blockDim.x) sh[q] = 0;
+  __syncthreads();
   double m = 0.0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
     if (b.lost[j] & 1) continue;
@@ -287,10 +290,13 @@ __global__ void beam_slip_kernel(BeamDesc b, double span, unsigned long long *ou
     m = fmax(m, rate);
     const double steps = rate > 0.0 ? span / rate : 1e300;
     const int q = steps < 1.0 ? 0 : (steps >= 9.2e18 ? 63 : min(63, 63 - __clzll((long long)steps)));
-    atomicAdd(&hist[q], 1);
+    atomicAdd(&sh[q], 1);
   }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_down_sync(kFull, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0.0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+  __syncthreads();
+  for (int q = threadIdx.x; q < 64; q += blockDim.x)
+    if (sh[q]) atomicAdd(&hist[q], sh[q]);
 }
 static __global__ void bin_count_kernel(BeamDesc b, int *count) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x)

@@ -92,6 +92,17 @@ int wake_load_plasma(wake_sim *s, int sim, const double *normals);
  */
 int wake_load_beam(wake_sim *s, int sim, const double *normals);
 
+/*
+ * A beam of simulation `sim` given by the caller (a beam from another code, another bunch
+ * shape, or a state saved with wake_get_beam): xyz is a device array of 6 x n_beam doubles in
+ * wake_get_beam's layout (rows x, y, xi, u_x, u_y, u_z); w a device array of n_beam charge
+ * weights per 2 pi (NULL: the Eq. 12 bunch weights, as wake_load_beam gives them); tag a
+ * device array of n_beam bytes, nonzero for witness particles (NULL: the particles from
+ * n_drive on).  Particles outside 0 <= xi < ximax, r < rmax start lost.  Replaces the beam
+ * state; wake_get_beam returns particles in this order.
+ */
+int wake_set_beam(wake_sim *s, int sim, const double *xyz, const double *w, const uint8_t *tag);
+
 /* Beam -> (r, xi) grid density of every simulation with a beam (bilinear hats divided by
  * the hats' ring volumes).  Needs wake_load_beam. */
 int wake_beam_deposit(wake_sim *s);

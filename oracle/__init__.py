@@ -84,6 +84,7 @@ def lib():
                                     pd, pd, pd, pd, pd]
             L.orc_run_w.restype = i32
             L.orc_witness_obs.argtypes = [pp, pd, pd, pd, pu8, pd, pd]
+            L.orc_beam_deposit_w.argtypes = [pp, pd, pd, pd, pu8, pd, pd]
             _lib = L
     return _lib
 
@@ -216,10 +217,13 @@ def beam_init(cfg, normals):
     return b
 
 
-def beam_deposit(cfg, beam):
+def beam_deposit(cfg, beam, wmul=None):
+    """Beam density on the nodes; wmul: optional per-particle charge multipliers."""
     p = params(cfg)
     nb = np.zeros((cfg.nxi + 1, cfg.nr + 1))
-    lib().orc_beam_deposit(C.byref(p), _p(beam["x"]), _p(beam["y"]), _p(beam["xi"]), _p(beam["lost"]), _p(nb))
+    wm = None if wmul is None else np.ascontiguousarray(wmul, dtype=np.float64)
+    lib().orc_beam_deposit_w(C.byref(p), _p(beam["x"]), _p(beam["y"]), _p(beam["xi"]), _p(beam["lost"]), _p(wm),
+                             _p(nb))
     return nb
 
 

@@ -21,6 +21,7 @@ struct BeamDesc {
   double *xi, *uz;
   uint8_t *lost;           // flags: bit 0 lost, bit 1 witness
   int *orig;               // index in the caller's order
+  void *w;                 // per-particle weight (BT): charge per 2 pi
   void *nb;                // beam-density grid (G)
   const void *er, *ez, *bth;  // fields of the last march (G)
   double *diag;            // 5 accumulators
@@ -47,6 +48,29 @@ __global__ void beam_init_kernel(BeamDesc b, BunchInit q, const double *__restri
     const double r = sqrt(x * x + y * y);
     b.lost[j] = (uint8_t)((xi >= 0.0 && xi < b.ximax && r < b.rmax) ? 0 : 1) | (uint8_t)(drive ? 0 : 2);
     b.orig[j] = (int)j;
+    ((BT *)b.w)[j] = (BT)(drive ? b.wd : b.ww);
+  }
+}
+
+// A beam given by the caller: xyz rows x, y, xi, u_x, u_y, u_z (6 x n, FP64), weights w (NULL:
+// the Eq. 12 bunch weights), witness tags (NULL: the particles from n_drive on).  Particles
+// outside 0 <= xi < ximax, r < rmax are lost.
+template <class BT>
+__global__ void beam_set_kernel(BeamDesc b, const double *__restrict__ xyz, const double *__restrict__ w,
+                                const uint8_t *__restrict__ tag) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+    const bool witness = tag ? tag[j] != 0 : j >= b.n_drive;
+    const double x = xyz[j], y = xyz[b.n + j], xi = xyz[2 * b.n + j];
+    ((BT *)b.x)[j] = (BT)x;
+    ((BT *)b.y)[j] = (BT)y;
+    ((BT *)b.ux)[j] = (BT)xyz[3 * b.n + j];
+    ((BT *)b.uy)[j] = (BT)xyz[4 * b.n + j];
+    b.xi[j] = xi;
+    b.uz[j] = xyz[5 * b.n + j];
+    const double r = sqrt(x * x + y * y);
+    b.lost[j] = (uint8_t)((xi >= 0.0 && xi < b.ximax && r < b.rmax) ? 0 : 1) | (uint8_t)(witness ? 2 : 0);
+    b.orig[j] = (int)j;
+    ((BT *)b.w)[j] = (BT)(w ? w[j] : (witness ? b.ww : b.wd));
   }
 }
 
@@ -69,7 +93,7 @@ __device__ __forceinline__ void deposit_range(const BeamDesc &b, int64_t j0, int
     double g;
     locate(b.xi[j], inv_dxi, b.nxi, k, g);
     const BT gg = (BT)g;
-    const BT w = (BT)((fl & 2) ? b.ww : b.wd);
+    const BT w = ((const BT *)b.w)[j];
     G *row = nb + (size_t)k * n1 + c;
     atomicAdd(row, (G)(w * ((BT)1 - f) * ((BT)1 - gg)));
     atomicAdd(row + 1, (G)(w * f * ((BT)1 - gg)));
@@ -336,6 +360,7 @@ __global__ void bin_scatter_kernel(BeamDesc b, BeamDesc dst, int *cursor) {
     dst.uz[q] = b.uz[j];
     dst.lost[q] = b.lost[j];
     dst.orig[q] = b.orig[j];
+    ((BT *)dst.w)[q] = ((const BT *)b.w)[j];
   }
 }
 // Scatter the beam back to the caller's order: out rows x, y, xi, u_x, u_y, u_z (6 x n).

@@ -35,7 +35,8 @@ struct PipeArgs {
   double *xi, *uz;
   uint8_t *flags;
   const int *bin_start;
-  double wd, ww, ds;
+  void *w;               // per-particle weights (BT)
+  double ds;
   long long spin_limit;   // polls before a wait gives up
   void *ring_bufs;        // per-CTA ring slot storage (FP64 and wide forms)
   size_t ring_stride;
@@ -164,7 +165,7 @@ struct PipeHooks {
     locate(rn, inv_dr, nr, c2, f2);
     locate(xi, inv_dxi, nxi, k2, g2d);
     const BT g2 = (BT)g2d;
-    const BT wq = (BT)((fl & 2) ? a.ww : a.wd) * (BT)(1.0 / (dr * dr * dxi));
+    const BT wq = __ldcg((const BT *)a.w + j) * (BT)(1.0 / (dr * dr * dxi));
     auto iv = [&](int i) -> BT {
       return i == 0 ? (BT)6 : (i == nr ? (BT)1 / ((BT)nr * (BT)0.5 - (BT)(1.0 / 6.0)) : (BT)1 / (BT)i);
     };

@@ -43,6 +43,7 @@ struct Sim {
   double *bxi = nullptr, *buz = nullptr;
   uint8_t *blost = nullptr;  // flags: bit 0 lost, bit 1 witness
   int *orig = nullptr;       // index of each particle in the caller's order
+  void *bwt = nullptr, *bwt2 = nullptr;  // per-particle weights (and the sort's second copy)
   // second copy of the beam for the re-sort by xi cell, and the cell table
   void *bx2 = nullptr, *by2 = nullptr, *bux2 = nullptr, *buy2 = nullptr;
   double *bxi2 = nullptr, *buz2 = nullptr;
@@ -129,7 +130,7 @@ void free_sim(Sim &s) {
   void *ptrs[] = {s.r0, s.ur0, s.lz, s.G0, s.w, s.ring_buf, s.nb, s.psi, s.ez, s.er, s.bth, s.bx, s.by, s.bux, s.buy,
                   s.bxi, s.buz, s.blost, s.status, s.orig, s.bx2, s.by2, s.bux2, s.buy2, s.bxi2, s.buz2, s.blost2,
                   s.orig2, s.bin_count, s.bin_start, s.bin_cursor, s.slip, s.pgrids, s.progress, s.pring,
-                  s.defer_cnt, s.target, s.defer_list};
+                  s.defer_cnt, s.target, s.defer_list, s.bwt, s.bwt2};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   s = Sim();
@@ -186,6 +187,7 @@ BeamDesc beam_desc(const Sim &s, double *diag) {
   b.uz = s.buz;
   b.lost = s.blost;
   b.orig = s.orig;
+  b.w = s.bwt;
   b.nb = s.nb;
   b.er = s.er;
   b.ez = s.ez;
@@ -430,7 +432,8 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
           (rc = dalloc(&s.bin_count, sizeof(int) * (p[i].nxi + 2))) ||
           (rc = dalloc(&s.bin_start, sizeof(int) * (p[i].nxi + 2))) ||
           (rc = dalloc(&s.bin_cursor, sizeof(int) * (p[i].nxi + 2))) ||
-          (rc = dalloc(&s.slip, sizeof(unsigned long long) + 64 * sizeof(int))))
+          (rc = dalloc(&s.slip, sizeof(unsigned long long) + 64 * sizeof(int))) || (rc = dalloc(&s.bwt, bt)) ||
+          (rc = dalloc(&s.bwt2, bt)))
         break;
     } else {
       // frozen analytic driver (Eq. 12) on the nodes
@@ -555,6 +558,23 @@ int wake_load_beam(wake_sim *h, int sim, const double *normals) {
   return WAKE_OK;
 }
 
+int wake_set_beam(wake_sim *h, int sim, const double *xyz, const double *w, const uint8_t *tag) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  Sim &s = h->sims[sim];
+  if (s.p.n_beam == 0) return fail(WAKE_EINVAL, "simulation has no beam (n_beam == 0)");
+  if (!xyz) return fail(WAKE_EINVAL, "null beam state");
+  BeamDesc b = beam_desc(s, nullptr);
+  const int nb = grid_blocks(s.p.n_beam, 256);
+  if (h->precision == WAKE_FP64)
+    beam_set_kernel<double><<<nb, 256, 0, h->stream>>>(b, xyz, w, tag);
+  else
+    beam_set_kernel<float><<<nb, 256, 0, h->stream>>>(b, xyz, w, tag);
+  CUDA_TRY(cudaGetLastError());
+  s.beam = true;
+  return WAKE_OK;
+}
+
 int wake_beam_deposit(wake_sim *h) {
   if (!h) return fail(WAKE_EINVAL, "null handle");
   if (h->n > 1) {  // one launch per phase over all simulations
@@ -648,6 +668,7 @@ int sort_beam(wake_sim *h, Sim &s) {
   d.uz = s.buz2;
   d.lost = s.blost2;
   d.orig = s.orig2;
+  d.w = s.bwt2;
   const int nbins = s.p.nxi + 1;
   CUDA_TRY(cudaMemsetAsync(s.bin_count, 0, sizeof(int) * (nbins + 1), h->stream));
   const int blocks = grid_blocks(s.p.n_beam, 256);
@@ -666,6 +687,7 @@ int sort_beam(wake_sim *h, Sim &s) {
   std::swap(s.buz, s.buz2);
   std::swap(s.blost, s.blost2);
   std::swap(s.orig, s.orig2);
+  std::swap(s.bwt, s.bwt2);
   return WAKE_OK;
 }
 
@@ -845,8 +867,7 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
       a.uz = b.uz;
       a.flags = b.lost;
       a.bin_start = s.bin_start;
-      a.wd = b.wd;
-      a.ww = b.ww;
+      a.w = b.w;
       a.ds = s.p.ds;
       a.spin_limit = 1LL << 24;
       a.defer_cnt = s.defer_cnt;
@@ -1073,8 +1094,7 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
     a.uz = bd.uz;
     a.flags = bd.lost;
     a.bin_start = s.bin_start;
-    a.wd = bd.wd;
-    a.ww = bd.ww;
+    a.w = bd.w;
     a.ds = s.p.ds;
     a.spin_limit = 1LL << 24;  // polls of >= 128 ns: a wait gives up after seconds
     a.ring_bufs = s.pring;

@@ -17,7 +17,7 @@ WAKE_OK, WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENUMERIC, WAKE_ETIMEOUT, WAK
 WAKE_FP64, WAKE_MIXED = 0, 1
 
 # every entry point the header declares
-EXPORTS = ["wake_init", "wake_load_plasma", "wake_load_beam", "wake_beam_deposit", "wake_plasma_march",
+EXPORTS = ["wake_init", "wake_load_plasma", "wake_load_beam", "wake_set_beam", "wake_beam_deposit", "wake_plasma_march",
            "wake_beam_push", "wake_step", "wake_tile", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
            "wake_diagnostics", "wake_status", "wake_beam_deposit_noalloc", "wake_adjoint_init",
            "wake_adjoint_forward", "wake_adjoint_backward", "wake_adjoint_destroy", "wake_last_error", "wake_destroy"]
@@ -53,6 +53,7 @@ def lib():
         L.wake_init.argtypes = [C.POINTER(wake_params), i32, vp, C.POINTER(vp)]
         L.wake_load_plasma.argtypes = [vp, i32, vp]
         L.wake_load_beam.argtypes = [vp, i32, vp]
+        L.wake_set_beam.argtypes = [vp, i32, vp, vp, vp]
         for n in ("wake_beam_deposit", "wake_plasma_march", "wake_beam_push"):
             getattr(L, n).argtypes = [vp]
         L.wake_step.argtypes = [vp, i32]
@@ -116,6 +117,12 @@ def wake_load_plasma(h, sim, normals=None):
 
 def wake_load_beam(h, sim, normals):
     _check(lib().wake_load_beam(h, sim, _ptr(normals)))
+
+
+def wake_set_beam(h, sim, xyz, w=None, tag=None):
+    """xyz: (6, n_beam) float64 CUDA tensor (x, y, xi, u_x, u_y, u_z); w: (n_beam,) float64 or
+    None; tag: (n_beam,) uint8 or None."""
+    _check(lib().wake_set_beam(h, sim, _ptr(xyz), _ptr(w), _ptr(tag)))
 
 
 def wake_beam_deposit(h):

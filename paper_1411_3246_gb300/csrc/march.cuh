@@ -313,10 +313,11 @@ __device__ __forceinline__ void fill_tables(MarchSmem<Pol> &sm, int nr, double d
   }
 }
 
-// Charge sums.  FP64 form: plain doubles.  Mixed form: a ring's hat contributions w(1-f) and
-// w f are exact float-float products (two-product by FMA), summed over the window in
-// float-float, and converted to 64-bit fixed point (2^44 units) for the shared-memory
-// atomics; the integer sums are exact, so rho - rho0 loses nothing to cancellation.
+// Charge sums.  FP64 form: plain doubles.  Mixed form: 64-bit fixed point (2^44 units).  A
+// ring's share w f is the exact float-float product (two-product by FMA) rounded once to the
+// fixed-point grid, and its share w (1 - f) is the ring's fixed-point weight minus that, so
+// the two add up to the same integer on every slice; window, warp and shared-memory sums
+// are integer and exact, so rho - rho0 loses nothing to cancellation.
 constexpr double kQScale = 17592186044416.0;  // 2^44
 __device__ __forceinline__ FF two_prod(float a, float b) {
   const float p = a * b;
@@ -467,44 +468,37 @@ __device__ __forceinline__ void solve_fields(MarchSmem<Pol> &sm, const NodeGeo<P
   using Acc = typename Pol::Acc;
   const int tid = threadIdx.x, nr = geo.nr, n1 = nr + 1;
   const R inv_dr = geo.inv_dr, hdr = (R)0.5 * geo.dr;
-  // node densities; d_xi psi'_m = -((1 - alpha_m) K_{m-1} + alpha_m K_m) / (dr r_m) into ez
-  for (int m = tid; m < n1; m += NT) {
-    const R iv = geo.invV(m);
-    const R nbm = (R)0.5 * (nbA[m] + nbB[m]);
-    sm.jz[m] = (Acc)((R)sm.jz[m] * iv - nbm);
-    sm.chi[m] = (Acc)((R)sm.chi[m] * iv);
-    sm.T[m] = (Acc)((R)sm.T[m] * iv);
-    sm.P[m] = (Acc)((R)sm.P[m] * iv);
-    sm.U[m] = (Acc)((R)sm.U[m] * iv);
-    R dz = (R)0;
-    if (m > 0) {
-      const R al = geo.alpha(m);
-      const R Km = m < nr ? (R)sm.K[m] : (R)0;
-      dz = -(((R)1 - al) * (R)sm.K[m - 1] + al * Km) * geo.invR(m) * inv_dr;
-    }
-    sm.ez[m] = dz;
-  }
-  __syncthreads();
-  // E_z: inward trapezoid sum from E_z(R) = 0 (in place over the d_xi psi' values)
+  // d_xi psi'_m = -((1 - alpha_m) K_{m-1} + alpha_m K_m) / (dr r_m), from the K deposits
+  auto dxi_dpsi = [&](int m) -> R {
+    if (m == 0) return (R)0;
+    const R al = geo.alpha(m);
+    const R Km = m < nr ? (R)sm.K[m] : (R)0;
+    return -(((R)1 - al) * (R)sm.K[m - 1] + al * Km) * geo.invR(m) * inv_dr;
+  };
+  // E_z: inward trapezoid sum from E_z(R) = 0
   block_scan_fused<NT, Pol::kScanE, true, W>(
-      n1, wtot, [&](int m) { return wide_of<W, R>(m < nr ? hdr * (sm.ez[m] + sm.ez[m + 1]) : (R)0); },
-      [&](int m, W incl) { sm.ez[m] = -(R)wide_value(incl); });  // inputs are all read first
+      n1, wtot, [&](int m) { return wide_of<W, R>(m < nr ? hdr * (dxi_dpsi(m) + dxi_dpsi(m + 1)) : (R)0); },
+      [&](int m, W incl) { sm.ez[m] = -(R)wide_value(incl); });
+  // node densities (deposit / hat volume; J_z less the beam density averaged over the two
+  // rows) read where the rows need them
+  auto dens = [&](const Acc *v, int m) -> R { return (R)v[m] * geo.invV(m); };
+  auto jz_node = [&](int m) -> R { return (R)sm.jz[m] * geo.invV(m) - (R)0.5 * (nbA[m] + nbB[m]); };
   // rows q = 0..nr-1 (node i = q + 1): central differences, a half cell at the wall
   const R i2dr = (R)0.5 * inv_dr;
   for (int q = tid; q < nr; q += NT) {
     const int i = q + 1;
-    const R Qi = (R)sm.P[i] + sm.ez[i] * (R)sm.U[i];
-    const R Ti = (R)sm.T[i];
+    const R Qi = dens(sm.P, i) + sm.ez[i] * dens(sm.U, i);
+    const R Ti = dens(sm.T, i);
     R a, c, sgeo;
     geo.row(q, a, c, sgeo);
     R rhs;
     if (i < nr)
-      rhs = ((R)sm.jz[i + 1] - (R)sm.jz[i - 1]) * i2dr + Qi + ((R)sm.T[i + 1] - (R)sm.T[i - 1]) * i2dr +
+      rhs = (jz_node(i + 1) - jz_node(i - 1)) * i2dr + Qi + (dens(sm.T, i + 1) - dens(sm.T, i - 1)) * i2dr +
             Ti * geo.invR(i);
     else
-      rhs = Qi + (Ti - (R)sm.T[i - 1]) * inv_dr + Ti * geo.invR(i) - ((R)sm.jz[i - 1] + (R)sm.jz[i]) * inv_dr;
+      rhs = Qi + (Ti - dens(sm.T, i - 1)) * inv_dr + Ti * geo.invR(i) - (jz_node(i - 1) + jz_node(i)) * inv_dr;
     sm.ta[q] = a;
-    sm.tb[q] = sgeo - (R)sm.chi[i];  // row sum a + b + c (both terms negative)
+    sm.tb[q] = sgeo - dens(sm.chi, i);  // row sum a + b + c (both terms negative)
     sm.tc[q] = c;
     sm.td[q] = rhs;
   }
@@ -576,17 +570,20 @@ struct WindowAcc {
 #pragma unroll
       for (int q = 0; q < NV; ++q) n[a][q] = (R)0;
   }
+  // the hat weights (1 - f, f) placed on the window's nodes o, o + 1 once, then one
+  // multiply-add per node and value
   __device__ __forceinline__ bool add(int c, R f, const R (&v)[NV]) {
     const int o = c - c0;
     if (o < 0 || o > 2) return false;
     const R g = (R)1 - f;
+    const R w0 = o == 0 ? g : (R)0, w1 = o == 0 ? f : (o == 1 ? g : (R)0);
+    const R w2 = o == 1 ? f : (o == 2 ? g : (R)0), w3 = o == 2 ? f : (R)0;
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      const R lo = v[q] * g, hi = v[q] * f;
-      n[0][q] += o == 0 ? lo : (R)0;
-      n[1][q] += o == 0 ? hi : (o == 1 ? lo : (R)0);
-      n[2][q] += o == 1 ? hi : (o == 2 ? lo : (R)0);
-      n[3][q] += o == 2 ? hi : (R)0;
+      n[0][q] += v[q] * w0;
+      n[1][q] += v[q] * w1;
+      n[2][q] += v[q] * w2;
+      n[3][q] += v[q] * w3;
     }
     return true;
   }
@@ -597,7 +594,7 @@ struct WindowAcc {
 // lane then holds the total, so one lane per segment issues the shared-memory atomics
 // (same-address atomics of one instruction serialise).
 struct WarpSeg {
-  int lane, seg_start, tail_lane;
+  int lane, seg_start, tail_lane, max_len;
   bool is_tail;
   __device__ __forceinline__ explicit WarpSeg(int key) {
     lane = threadIdx.x & 31;
@@ -609,15 +606,22 @@ struct WarpSeg {
     const unsigned tails = __ballot_sync(kFull, is_tail);
     seg_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
     tail_lane = __ffs(tails & (0xffffffffu << lane)) - 1;
+    max_len = __reduce_max_sync(kFull, (unsigned)(lane - seg_start + 1));
   }
-  template <class T>
-  __device__ __forceinline__ T sum(T v) const {
+  // Inclusive segmented sums of N values from the segment's head, in place.  The strides
+  // double while they are below the warp's longest segment: a longer stride would add
+  // nothing (no lane is that far into its segment), so the sums equal those of all five
+  // steps.  The bound is warp-uniform.
+  template <class T, int N>
+  __device__ __forceinline__ void sum_n(T (&v)[N]) const {
+    for (int o = 1; o < max_len; o <<= 1) {
+      const bool take = lane - o >= seg_start;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T u = __shfl_up_sync(kFull, v, o);
-      if (lane - o >= seg_start) v += u;
+      for (int i = 0; i < N; ++i) {
+        const T u = __shfl_up_sync(kFull, v[i], o);
+        if (take) v[i] += u;
+      }
     }
-    return v;
   }
 };
 
@@ -651,28 +655,35 @@ struct ChargeWin<PolFP64> {
 template <>
 struct ChargeWin<PolMixed> {
   int c0 = -1;
-  FF n[4];
+  long long n[4];
   __device__ __forceinline__ void init(int c) {
     c0 = c;
-    n[0] = n[1] = n[2] = n[3] = FF{0.f, 0.f};
+    n[0] = n[1] = n[2] = n[3] = 0;
+  }
+  // w f as an exact float-float product, w and w f in fixed point, w (1 - f) = w - w f there
+  __device__ __forceinline__ static void split(float f, float w, long long &qlo, long long &qhi) {
+    const FF hi = two_prod(w, f);
+    qhi = ff_to_q(hi);
+    qlo = __float2ll_rn(w * (float)kQScale) - qhi;
   }
   __device__ __forceinline__ bool add(int c, float f, float w) {
     const int o = c - c0;
     if (o < 0 || o > 2) return false;
-    const FF hi = two_prod(w, f), lo = ff_add(FF{w, 0.f}, FF{-hi.h, -hi.l});  // lo + hi = w
-    const FF z{0.f, 0.f};
-    n[0] = ff_add(n[0], o == 0 ? lo : z);
-    n[1] = ff_add(n[1], o == 0 ? hi : (o == 1 ? lo : z));
-    n[2] = ff_add(n[2], o == 1 ? hi : (o == 2 ? lo : z));
-    n[3] = ff_add(n[3], o == 2 ? hi : z);
+    long long lo, hi;
+    split(f, w, lo, hi);
+    n[0] += o == 0 ? lo : 0ll;
+    n[1] += o == 0 ? hi : (o == 1 ? lo : 0ll);
+    n[2] += o == 1 ? hi : (o == 2 ? lo : 0ll);
+    n[3] += o == 2 ? hi : 0ll;
     return true;
   }
   __device__ __forceinline__ static void direct(long long *rho, int c, float f, float w) {
-    const FF hi = two_prod(w, f), lo = ff_add(FF{w, 0.f}, FF{-hi.h, -hi.l});
-    atomicAdd((unsigned long long *)&rho[c], (unsigned long long)ff_to_q(lo));
-    atomicAdd((unsigned long long *)&rho[c + 1], (unsigned long long)ff_to_q(hi));
+    long long lo, hi;
+    split(f, w, lo, hi);
+    atomicAdd((unsigned long long *)&rho[c], (unsigned long long)lo);
+    atomicAdd((unsigned long long *)&rho[c + 1], (unsigned long long)hi);
   }
-  __device__ __forceinline__ long long node(int a) const { return ff_to_q(n[a]); }
+  __device__ __forceinline__ long long node(int a) const { return n[a]; }
 };
 
 template <>
@@ -688,11 +699,13 @@ template <class Pol>
 __device__ __forceinline__ void flush_charge(MarchSmem<Pol> &sm, const ChargeWin<Pol> &acc, int nr) {
   using Q = typename Pol::Q;
   const WarpSeg seg(acc.c0);
+  Q t[4];
 #pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const Q t = seg.sum(acc.node(a));
-    if (seg.is_tail && acc.c0 >= 0 && acc.c0 + a <= nr) q_atomic_add(&sm.rho[acc.c0 + a], t);
-  }
+  for (int a = 0; a < 4; ++a) t[a] = acc.node(a);
+  seg.sum_n(t);
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+    if (seg.is_tail && acc.c0 >= 0 && acc.c0 + a <= nr) q_atomic_add(&sm.rho[acc.c0 + a], t[a]);
 }
 
 // Charge deposit of one ring through a window (direct atomics outside it).
@@ -764,19 +777,23 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
   const WarpSeg seg(acc.c0);
   const int c = acc.c0;
   const bool emit = seg.is_tail && c >= 0;
+  R tot[23];
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) tot[q * 4 + a] = acc.n[a][q];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) tot[20 + a] = kw[a];
+  seg.sum_n(tot);
   Acc *arr[5] = {sm.jz, sm.chi, sm.T, sm.P, sm.U};
 #pragma unroll
   for (int q = 0; q < 5; ++q)
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const R tsum = seg.sum(acc.n[a][q]);
-      if (emit && c + a <= nr) atomicAdd(&arr[q][c + a], (Acc)tsum);
-    }
+    for (int a = 0; a < 4; ++a)
+      if (emit && c + a <= nr) atomicAdd(&arr[q][c + a], (Acc)tot[q * 4 + a]);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const R tsum = seg.sum(kw[a]);
-    if (emit && c + a < nr) atomicAdd(&sm.K[c + a], (Acc)tsum);
-  }
+  for (int a = 0; a < 3; ++a)
+    if (emit && c + a < nr) atomicAdd(&sm.K[c + a], (Acc)tot[20 + a]);
 }
 
 // Re-sort the rings of the CTA by cell (counting sort) so that each thread's rings are
@@ -826,10 +843,11 @@ __device__ __forceinline__ void resort_rings(MarchSmem<Pol> &sm, const RingSoA<t
       }
     }
     const WarpSeg seg(c0);
-    int base[3];
+    int base[3], inc[3] = {cw[0], cw[1], cw[2]};
+    seg.sum_n(inc);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const int incl = seg.sum(cw[a]);
+      const int incl = inc[a];
       int b = 0;
       if (seg.is_tail && c0 >= 0 && c0 + a < nr && incl > 0) b = atomicAdd(&sm.cnt[c0 + a], incl);
       b = __shfl_sync(kFull, b, seg.tail_lane);

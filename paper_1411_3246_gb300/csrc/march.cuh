@@ -29,6 +29,7 @@
 #pragma once
 
 #include "wake_common.cuh"
+#include <type_traits>
 
 namespace wake {
 
@@ -740,7 +741,10 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
       const int sl = p * NT + t;
       int c;
       R f, u_r, u_t;
-      pos(sl, c, f, u_r, u_t);
+      if constexpr (std::is_invocable_v<Pos, int, int, int &, R &, R &, R &>)
+        pos(p, sl, c, f, u_r, u_t);
+      else
+        pos(sl, c, f, u_r, u_t);
       if (p == 0) acc.init(c);
       const R rp = ((R)c + f) * dr;
       const R G = rs.G0[sl] + interp(sm.psi, c, f);
@@ -951,7 +955,8 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
 
   // positions of the stages: the slice state (stage 1), and the midpoint reached from it with
   // the stage-1 derivative in the local Cartesian frame (x, y) = (r, 0), (u_x, u_y) =
-  // (u_r, u_theta) (stage 2), recomputed where it is needed
+  // (u_r, u_theta) (stage 2), computed once per slice in the midpoint deposit and kept in
+  // registers for stage 2 and the full step
   auto state_pos = [&](int sl, int &c, R &f, R &u_r, R &u_t) {
     c = rs.c[sl];
     f = rs.f[sl];
@@ -1030,6 +1035,14 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
     hk.slice_done(k, sm);
     if (k == nxi) break;
     for (int i = tid; i < n1; i += NT) sm.jz[i] = sm.chi[i] = sm.T[i] = sm.P[i] = sm.U[i] = sm.K[i] = (Acc)0;
+    // the midpoint of each ring, kept in registers for stage 2 and the full step
+    int MC[PPT];
+    R MF[PPT], MUR[PPT], MUT[PPT];
+#pragma unroll
+    for (int p = 0; p < PPT; ++p) {
+      MC[p] = 0;
+      MF[p] = MUR[p] = MUT[p] = (R)0;
+    }
     {
       ChargeWin<Pol> acc;
       acc.init(-8);
@@ -1042,6 +1055,10 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
           R f, u_r, u_t;
           const R rr = midpoint(sl, c, f, u_r, u_t);
           if (!(rr >= (R)0 && rr <= R_wall)) flag(d.status, ST_ESCAPE);
+          MC[p] = c;
+          MF[p] = f;
+          MUR[p] = u_r;
+          MUT[p] = u_t;
           add_charge<Pol>(sm, acc, p, c, f, rs.w[sl]);
         }
       }
@@ -1053,7 +1070,12 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
     __syncthreads();
     for (int i = tid; i < n1; i += NT) sm.rho[i] = (typename Pol::Q)0;  // P1
     pass_currents<Pol, NT, PPT>(sm, rs, np, nr, dR, d.status,
-                                [&](int sl, int &c, R &f, R &u_r, R &u_t) { midpoint(sl, c, f, u_r, u_t); },
+                                [&](int p, int, int &c, R &f, R &u_r, R &u_t) {
+                                  c = MC[p];
+                                  f = MF[p];
+                                  u_r = MUR[p];
+                                  u_t = MUT[p];
+                                },
                                 G2, F2);
     __syncthreads();
     solve_fields<Pol, NT>(sm, geo, nbk, nbk1, sm.wtot);  // P2
@@ -1068,10 +1090,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
       for (int p = 0; p < PPT; ++p) {
         if (tid * PPT + p < np) {
           const int sl = p * NT + tid;
-          int mc;
-          R mf, mu_r, mu_t;
-          midpoint(sl, mc, mf, mu_r, mu_t);
-          const R F2b = F2[p] - interp(sm.bth, mc, mf);
+          const R F2b = F2[p] - interp(sm.bth, MC[p], MF[p]);  // at the midpoint
           const int c0 = rs.c[sl];
           const R f0 = rs.f[sl], ur0 = rs.ur[sl], G1v = rs.G1[sl], F1v = rs.F1[sl];
           const R r = ((R)c0 + f0) * dR;

@@ -305,6 +305,48 @@ def large_leg(wake, torch, nsteps, rank, flush, world):
             "form": "wide march (rings in global memory, chunks of 512 x 8 slots), pipelined", "dtype": "f32"}
 
 
+def facet_leg(wake, torch, length_m, rank, flush, world):
+    """The Table I two-bunch beam (2^20 particles, zero emittance) carried length_m metres
+    through a 5 eV plasma (Nr=256 over 6, Nxi=1024 over 16, 8 rings/cell): one wake_step call
+    of all its steps, timed, after an untimed step; then the witness spectrum."""
+    from paper_1411_3246_gb300 import studies
+    cfg = synth.config_facet(te_ev=5.0)
+    cfg.seed = replica_seed(cfg.seed, rank)
+    nsteps = studies.steps_for_length(length_m, cfg.ds)
+    stream = torch.cuda.Stream()
+    nm_p = torch.from_numpy(synth.plasma_normals(cfg)).pin_memory()
+    nm_b = torch.from_numpy(synth.beam_normals(cfg)).pin_memory()
+    sim = wake.Simulations([cfg], wake.WAKE_MIXED, stream)
+    with torch.cuda.stream(stream):
+        dp, db = nm_p.cuda(non_blocking=True), nm_b.cuda(non_blocking=True)
+        wake.wake_load_plasma(sim.h, 0, dp)
+        wake.wake_load_beam(sim.h, 0, db)
+        wake.wake_step(sim.h, 1)
+        wake.wake_load_beam(sim.h, 0, db)
+        flush.fill_(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        wake.wake_step(sim.h, nsteps)
+        ev[1].record(stream)
+    stream.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    xyz, lost = sim.beam(0)
+    torch.cuda.synchronize()
+    e = studies.witness_energies_gev(xyz.cpu().numpy(), lost.cpu().numpy(), cfg.n_drive)
+    st = sim.status(0)
+    sim.close()
+    if st != wake.WAKE_OK:
+        raise RuntimeError(f"facet leg: simulation status {st}: {wake.wake_last_error()}")
+    pushes = plasma_pushes_per_step(cfg) * nsteps
+    t = barrier_max(ms / 1e3, world)
+    return {"value": world * pushes / t, "unit": "pushes/s", "ms_per_run": 1e3 * t, "beam_steps": nsteps,
+            "beam_pushes_per_s": world * cfg.n_beam * nsteps / t,
+            "witness_peak_gev": studies.spectrum_peak(e), "witness_mean_gev": float(e.mean()),
+            "workload": f"Table I two-bunch beam, {cfg.n_beam} particles, carried {length_m} m "
+                        f"({nsteps} steps of ds={cfg.ds}) in a 5 eV plasma, Nr={cfg.nr} x Nxi={cfg.nxi}, "
+                        f"{cfg.ppc} rings/cell", "dtype": "f32"}
+
+
 def adjoint_case(nsteps, rank):
     """The differentiation workload: the linear-driver grid (Nr=128 over 6, 4 rings/cell) at
     Nxi=1024 over 10, two bunches (witness at the batched sweep's first delay), 262,144 beam
@@ -361,6 +403,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=100, help="beam steps of the adjoint leg (0: skip)")
     ap.add_argument("--large-steps", type=int, default=304,
                     help="beam steps of the large-configuration leg (0: skip; the configuration has 1000)")
+    ap.add_argument("--facet-m", type=float, default=1.49,
+                    help="metres the Table I beam is carried in the propagation leg (0: skip)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -468,6 +512,11 @@ def main():
     if args.large_steps > 0:
         large = large_leg(wake, torch, args.large_steps, rank, flush, world)
 
+    # --- propagation: the Table I beam carried 1.49 m (the paper's FACET run) ---
+    facet = None
+    if args.facet_m > 0:
+        facet = facet_leg(wake, torch, args.facet_m, rank, flush, world)
+
     # --- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -500,7 +549,7 @@ def main():
                 "e2e": {"value": world * pushes * e2e_steps / e2e_s, "unit": "pushes/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 5 * 8},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "batched": batched, "adjoint": adjoint,
-                "large": large,
+                "large": large, "facet": facet,
                 "gpu_launches": KERNELS_PER_RUN * args.steps,
                 "witness": {"mean_gamma": diag[1], "rms_gamma": diag[2], "alive": diag[0]}}
         print(json.dumps(line), flush=True)

@@ -108,6 +108,20 @@ def config_table1(nr=256, nxi=1024, u_th=0.0, n_beam=0) -> WakeConfig:
                       n_beam=n_beam, n_drive=n_beam, seed=SEED_BASE + 11)
 
 
+def config_facet(n_beam=1 << 20, te_ev=0.0, nr=256, nxi=1024, ds=5.0) -> WakeConfig:
+    """The Table I two-bunch beam as macroparticles in a plasma of temperature te_ev
+    (u_th = sqrt(T_e / m c^2)), with zero initial emittance as in the paper's FACET runs
+    (Sec. III).  Macroparticles are split between the bunches in proportion to their charge
+    (n sigma_z sigma_r^2, both bunches sharing sigma_r)."""
+    cfg = config_table1(nr=nr, nxi=nxi, u_th=math.sqrt(te_ev / 511.0e3))
+    q_ratio = (cfg.n_w * cfg.sigma_zw) / (cfg.n_d * cfg.sigma_zd)
+    cfg.n_beam = int(n_beam)
+    cfg.n_drive = int(n_beam) - int(round(n_beam * q_ratio / (1.0 + q_ratio)))
+    cfg.eps_n = 0.0
+    cfg.ds = ds
+    return cfg
+
+
 def config_batch(n_sims=256, n_steps=50, seed=SEED_BASE + 3) -> list[WakeConfig]:
     """Batched sweep of the linear-driver physics plus a witness: Nr in {128..1024} and
     Nxi in {512..4096}, each log-uniform over powers of two; R=6, L=10, ppc=4;

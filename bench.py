@@ -347,6 +347,43 @@ def facet_leg(wake, torch, length_m, rank, flush, world):
                         f"{cfg.ppc} rings/cell", "dtype": "f32"}
 
 
+def osiris_leg(wake, torch, length_m, rank, flush, world):
+    """The single-bunch parameter set of the paper's OSIRIS comparison (200 x 500 cells, 9
+    rings/cell, 2.5e6 beam particles) carried length_m metres (k_p^-1 = 0.367 mm): one
+    wake_step call of all its steps, timed, after an untimed step."""
+    cfg = synth.config_osiris()
+    cfg.seed = replica_seed(cfg.seed, rank)
+    nsteps = int(round(length_m / 0.367e-3 / cfg.ds))
+    stream = torch.cuda.Stream()
+    nm_b = torch.from_numpy(synth.beam_normals(cfg)).pin_memory()
+    sim = wake.Simulations([cfg], wake.WAKE_MIXED, stream)
+    with torch.cuda.stream(stream):
+        db = nm_b.cuda(non_blocking=True)
+        wake.wake_load_plasma(sim.h, 0, None)
+        wake.wake_load_beam(sim.h, 0, db)
+        wake.wake_step(sim.h, 1)
+        wake.wake_load_beam(sim.h, 0, db)
+        flush.fill_(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        wake.wake_step(sim.h, nsteps)
+        ev[1].record(stream)
+    stream.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    d = sim.diagnostics()[0]
+    st = sim.status(0)
+    sim.close()
+    if st != wake.WAKE_OK:
+        raise RuntimeError(f"osiris leg: simulation status {st}: {wake.wake_last_error()}")
+    pushes = plasma_pushes_per_step(cfg) * nsteps
+    t = barrier_max(ms / 1e3, world)
+    return {"value": world * pushes / t, "unit": "pushes/s", "ms_per_run": 1e3 * t, "beam_steps": nsteps,
+            "beam_pushes_per_s": world * cfg.n_beam * nsteps / t, "drive_mean_gamma": d[4],
+            "workload": f"single bunch of the OSIRIS comparison, {cfg.n_beam} particles, carried {length_m} m "
+                        f"({nsteps} steps of ds={cfg.ds}), cold plasma, Nr={cfg.nr} x Nxi={cfg.nxi}, "
+                        f"{cfg.ppc} rings/cell", "dtype": "f32"}
+
+
 def adjoint_case(nsteps, rank):
     """The differentiation workload: the linear-driver grid (Nr=128 over 6, 4 rings/cell) at
     Nxi=1024 over 10, two bunches (witness at the batched sweep's first delay), 262,144 beam
@@ -405,6 +442,8 @@ def main():
                     help="beam steps of the large-configuration leg (0: skip; the configuration has 1000)")
     ap.add_argument("--facet-m", type=float, default=1.49,
                     help="metres the Table I beam is carried in the propagation leg (0: skip)")
+    ap.add_argument("--osiris-m", type=float, default=1.4,
+                    help="metres the single bunch of the OSIRIS parameter set is carried (0: skip)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -517,6 +556,10 @@ def main():
     if args.facet_m > 0:
         facet = facet_leg(wake, torch, args.facet_m, rank, flush, world)
 
+    osiris = None
+    if args.osiris_m > 0:
+        osiris = osiris_leg(wake, torch, args.osiris_m, rank, flush, world)
+
     # --- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -549,7 +592,7 @@ def main():
                 "e2e": {"value": world * pushes * e2e_steps / e2e_s, "unit": "pushes/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 5 * 8},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "batched": batched, "adjoint": adjoint,
-                "large": large, "facet": facet,
+                "large": large, "facet": facet, "osiris": osiris,
                 "gpu_launches": KERNELS_PER_RUN * args.steps,
                 "witness": {"mean_gamma": diag[1], "rms_gamma": diag[2], "alive": diag[0]}}
         print(json.dumps(line), flush=True)

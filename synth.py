@@ -122,6 +122,17 @@ def config_facet(n_beam=1 << 20, te_ev=0.0, nr=256, nxi=1024, ds=5.0) -> WakeCon
     return cfg
 
 
+def config_osiris(n_beam=2_500_000, nr=200, nxi=500, ds=5.0) -> WakeConfig:
+    """The single-bunch parameter set of the paper's OSIRIS comparison (Sec. III): box
+    10 x 25 with 200 x 500 cells, cold plasma with 9 macroparticles per cell, driver
+    n_d = 3.6, sigma_r = 0.19, sigma_zd = 1.72 at 30 GeV, 2.5e6 beam macroparticles, no
+    witness.  Readings: the driver centred at xi_d = 4 sigma_zd, and zero emittance (the
+    paper states none for this run)."""
+    return WakeConfig(nr=nr, nxi=nxi, ppc=9, rmax=10.0, ximax=25.0, u_th=0.0, n_d=3.6, n_w=0.0,
+                      sigma_r=0.19, sigma_zd=1.72, xi_d=4 * 1.72, xi_w=4 * 1.72, gamma_b=30.0e3 / 0.511,
+                      eps_n=0.0, n_beam=int(n_beam), n_drive=int(n_beam), ds=ds, seed=SEED_BASE + 12)
+
+
 def config_batch(n_sims=256, n_steps=50, seed=SEED_BASE + 3) -> list[WakeConfig]:
     """Batched sweep of the linear-driver physics plus a witness: Nr in {128..1024} and
     Nxi in {512..4096}, each log-uniform over powers of two; R=6, L=10, ppc=4;

@@ -266,8 +266,10 @@ def batched_leg(wake, torch, n_sims, nsteps, rank, flush, world):
             "workload": "batched sweep: Nr in {128..1024}, Nxi in {512..4096} log-uniform, ppc 4, "
                         "u_th ~ U[0,0.02], witness delay ~ U[3.5,5.5], 64k-256k beam particles each",
             "dtype": "f32",
-            "form": "every simulation's steps pipelined in one persistent launch (wide march, "
-                    "256-thread CTAs, two per SM); WAKE_BATCH_PIPELINE=0 takes the CUDA-graph step"}
+            "form": ("one CUDA graph per beam step: batched deposit, one march launch per tile class, "
+                     "batched push (WAKE_BATCH_PIPELINE=0)" if os.environ.get("WAKE_BATCH_PIPELINE", "1") == "0"
+                     else "every simulation's steps pipelined in one persistent launch (wide march, "
+                          "256-thread CTAs, two per SM); WAKE_BATCH_PIPELINE=0 takes the CUDA-graph step")}
 
 
 def large_leg(wake, torch, nsteps, rank, flush, world):

@@ -16,7 +16,10 @@ Timing: W untimed warm-up runs, then K runs, each bracketed by CUDA events on th
 stream; before each timed run the beam is re-initialised on the device (outside the timed
 region) and a 512 MB buffer is written to flush L2.  The JSON line also carries the plain
 FP64 GPU path (same scheme, FP64 throughout), an end-to-end number through the C ABI from
-pinned host buffers, the step kernel's roofline and the oracle CPU baseline.
+pinned host buffers, the step kernel's roofline and the oracle CPU baseline, and further
+legs (each skippable by its flag): the batched sweep, the adjoint, the large configuration,
+the Table I beam carried 1.49 m and the single bunch of the OSIRIS parameter set carried
+1.4 m.
 """
 from __future__ import annotations
 
@@ -45,7 +48,7 @@ FLOP_PER_NODE_STAGE = 62.0
 FLOP_PER_BEAM_PUSH = 140.0
 BEAM_STEPS = 200
 # DRAM traffic of one launch of the step kernel on this workload (200 steps), from one ncu
-# capture with one pass (dram__bytes_read.sum + dram__bytes_write.sum: 945.70 + 121.04 MB),
+# capture with one pass (dram__bytes_read.sum + dram__bytes_write.sum: 954.93 + 120.74 MB),
 # valid while the kernel's sources hash to STEP_TRAFFIC_SOURCES
 STEP_TRAFFIC_BYTES = 1075.67e6
 STEP_TRAFFIC_SOURCES = "54f1813b46fb15d5"

@@ -125,15 +125,37 @@ struct PipeHooks {
     if (ctl[0] == 0 && nxi >= 1) push_cell(nxi - 1);
   }
 
-  // Push particle j, found in cell kk (kk == b or b + 1, fields of slices b .. b+2 in the
-  // window), and deposit it into the grid of step t+1.
-  __device__ __forceinline__ void push_one(int j, uint8_t fl, int kk, double gd) {
+  // A particle's state as the push reads it, loaded in one go: the flag, xi and target
+  // checks then wait for one round trip to L2 instead of a chain of them.  (Loading several
+  // particles per thread ahead of their stores spilled registers of the march and was slower.)
+  struct Part {
+    BT x, y, ux, uy, w;
+    double xi, uz;
+    int tgt;
+    uint8_t fl;
+  };
+  __device__ __forceinline__ void load_part(int j, Part &p) const {
+    p.fl = __ldcg(a.flags + j);
+    p.xi = __ldcg(a.xi + j);
+    p.tgt = __ldcg(a.target + j);
+    p.x = __ldcg((const BT *)a.x + j);
+    p.y = __ldcg((const BT *)a.y + j);
+    p.ux = __ldcg((const BT *)a.ux + j);
+    p.uy = __ldcg((const BT *)a.uy + j);
+    p.uz = __ldcg(a.uz + j);
+    p.w = __ldcg((const BT *)a.w + j);
+  }
+
+  // Push particle j (state p), found in cell kk (kk == b or b + 1, fields of slices b .. b+2 in
+  // the window), and deposit it into the grid of step t+1.
+  __device__ __forceinline__ void push_one(int j, const Part &p, int kk, double gd) {
     BT *X = (BT *)a.x, *Y = (BT *)a.y, *UX = (BT *)a.ux, *UY = (BT *)a.uy;
     G *nbn = (G *)a.grids + (size_t)(t + 1) * a.ng;
     const BT inv_dr = (BT)(1.0 / dr), dt = (BT)a.ds, Rw = (BT)rmax;
     const double inv_dxi = 1.0 / dxi;
-    BT x = __ldcg(X + j), y = __ldcg(Y + j), ux = __ldcg(UX + j), uy = __ldcg(UY + j);
-    double xi = __ldcg(a.xi + j), uzd = __ldcg(a.uz + j);
+    const uint8_t fl = p.fl;
+    BT x = p.x, y = p.y, ux = p.ux, uy = p.uy;
+    double xi = p.xi, uzd = p.uz;
     const BT r = sqrt(x * x + y * y);
     int c;
     BT f;
@@ -165,7 +187,7 @@ struct PipeHooks {
     locate(rn, inv_dr, nr, c2, f2);
     locate(xi, inv_dxi, nxi, k2, g2d);
     const BT g2 = (BT)g2d;
-    const BT wq = __ldcg((const BT *)a.w + j) * (BT)(1.0 / (dr * dr * dxi));
+    const BT wq = p.w * (BT)(1.0 / (dr * dr * dxi));
     auto iv = [&](int i) -> BT {
       return i == 0 ? (BT)6 : (i == nr ? (BT)1 / ((BT)nr * (BT)0.5 - (BT)(1.0 / 6.0)) : (BT)1 / (BT)i);
     };
@@ -190,18 +212,18 @@ struct PipeHooks {
     int *cnt = a.defer_cnt + t;
     int2 *list = a.defer_list + (size_t)t * a.defer_cap;
     for (int j = beg + threadIdx.x; j < end; j += NT) {
-      const uint8_t fl = __ldcg(a.flags + j);
-      if (fl & 1) continue;
-      const double xi = __ldcg(a.xi + j);
+      Part p;
+      load_part(j, p);  // every load of the particle at once, before any branch on them
+      if (p.fl & 1) continue;
       int kk;
       double gd;
-      locate(xi, inv_dxi, nxi, kk, gd);
-      const int tgt = max(kk, __ldcg(a.target + j));
+      locate(p.xi, inv_dxi, nxi, kk, gd);
+      const int tgt = max(kk, p.tgt);
       if (tgt >= b + 2) {
         const int q = atomicAdd(cnt, 1);
         if (q < a.defer_cap) {
           list[q] = make_int2(j, tgt);
-          if (tgt > __ldcg(a.target + j)) a.target[j] = tgt;
+          if (tgt > p.tgt) a.target[j] = tgt;
         } else {
           flag(a.d.status, ST_DRIFT);
         }
@@ -211,7 +233,7 @@ struct PipeHooks {
         flag(a.d.status, ST_DRIFT);
         continue;
       }
-      push_one(j, fl, kk, gd);
+      push_one(j, p, kk, gd);
     }
     __syncthreads();  // every entry counted so far is written
     // this step's deferred particles whose target is b (all listed by earlier cells)
@@ -220,16 +242,17 @@ struct PipeHooks {
       const int2 e = __ldcg(list + q);
       if (e.y != b) continue;
       const int j = e.x;
-      const uint8_t fl = __ldcg(a.flags + j);
-      if (fl & 1) continue;
+      Part p;
+      load_part(j, p);
+      if (p.fl & 1) continue;
       int kk;
       double gd;
-      locate(__ldcg(a.xi + j), inv_dxi, nxi, kk, gd);
+      locate(p.xi, inv_dxi, nxi, kk, gd);
       if (kk != b && kk != b + 1) {
         flag(a.d.status, ST_DRIFT);
         continue;
       }
-      push_one(j, fl, kk, gd);
+      push_one(j, p, kk, gd);
     }
     __threadfence();
     __syncthreads();

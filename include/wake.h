@@ -196,19 +196,23 @@ int wake_status(wake_sim *s, int sim);
  * where a cudaMalloc could fail or make the pool give back its cached blocks, and code that
  * cannot take the device-wide synchronisation of cudaFree among concurrent streams.
  *   p       host pointer; reads nr, nxi, rmax, ximax, n_d, n_w, sigma_r, sigma_zd, sigma_zw,
- *           n_beam and n_drive (the macroparticle weights of Eq. 12, as wake_beam_deposit
- *           takes them); precision is ignored (FP64 throughout)
+ *           n_beam and n_drive (the bunch macroparticle weights, as wake_beam_deposit takes
+ *           them); precision is ignored (FP64 throughout)
  *   xyz     device, 6 x n_beam doubles in wake_get_beam's layout (rows x, y, xi, u_x, u_y,
  *           u_z; only x, y and xi are read); the first n_drive particles are the drive bunch
  *   lost    device, n_beam bytes, nonzero = lost (NULL: none lost); a particle outside
  *           0 <= xi < ximax, r < rmax also counts as lost
- *   stream  a cudaStream_t (NULL = legacy default stream); the call is asynchronous
+ *   stream  a cudaStream_t of the current device (NULL = legacy default stream); the call is
+ *           asynchronous
  *   nb      device output, (nxi+1)*(nr+1) doubles, overwritten
  * The arithmetic is that of wake_beam_deposit's FP64 form; results agree up to the order of
  * the atomic sums.  Scratch: a static device array of WAKE_NOALLOC_MAX_NODES doubles, which
  * each call zeroes on `stream` before it accumulates there; larger grids are rejected.  The
  * first call on a device looks up that array's address (cudaGetSymbolAddress), which may load
- * the library's device code: make it before any stream capture.  Calls that overlap in time
+ * the library's device code: make it before any stream capture.  The address is cached per
+ * device index; the cache is dropped when a launch fails, and does not survive
+ * cudaDeviceReset (after a reset, a call whose launch fails returns WAKE_ECUDA and the next
+ * call looks the address up again).  Calls that overlap in time
  * (on other streams or from other host threads) share the array and race: order them on one
  * stream.
  * Errors: WAKE_EINVAL (null p or nb, xyz NULL with n_beam > 0, sizes or grid out of range),

@@ -2,30 +2,31 @@
 // all of its slices, persistent over xi.
 //
 // Per slice, RK2 (midpoint) in xi; each stage solves the fields for the rings' positions in
-// four phases separated by block barriers:
-//   P0 (warp 0)    psi from Gauss's law for the hat charge density (enclosed charge Phi_m at
-//                  node m, r_m psi'_m = Phi_m), psi(R) = 0, inward trapezoid sum;
-//   P1 (all warps) per ring: Gamma = Gamma_0 + psi (Eq. 1), gamma and u_z (Eqs. 2-3),
-//                  a = u_r/Gamma, F0 = (gamma/Gamma) psi' + u_theta^2/(Gamma r) (Eq. 4 without
-//                  -B); deposit J_z, chi = n/gamma, T = D[w a^2], P = D[w (a^2 psi' - F0)/Gamma],
-//                  U = D[w a/Gamma] on the nodes and the radial current K_c of each cell;
-//   P2 (warp 0)    node densities; E_z = d_xi psi (Eq. 7) by an inward sum of the cell
-//                  currents; Q = P + E_z U; B_theta from Eq. 6 differentiated in r (Helmholtz
-//                  form, shift chi), a tridiagonal system solved by a warp partition method;
-//   P3 (all warps) per ring: the Cartesian radial force (gamma/Gamma) psi' - B_theta (Eqs. 4-5
-//                  with the centrifugal term carried by the local frame), the move to the next
-//                  stage's position, and that position's charge deposit (linear hats).
+// four phases separated by block barriers, every phase run by all threads of the CTA:
+//   P0  psi from Gauss's law for the hat charge density (enclosed charge Phi_m at node m,
+//       r_m psi'_m = Phi_m), psi(R) = 0, inward trapezoid sum: two block-wide scans over
+//       the nodes (solve_psi);
+//   P1  per ring: Gamma = Gamma_0 + psi (Eq. 1), gamma and u_z (Eqs. 2-3), a = u_r/Gamma,
+//       F0 = (gamma/Gamma) psi' + u_theta^2/(Gamma r) (Eq. 4 without -B); deposit J_z,
+//       chi = n/gamma, T = D[w a^2], P = D[w (a^2 psi' - F0)/Gamma], U = D[w a/Gamma] on the
+//       nodes and the radial current K_c of each cell (pass_currents);
+//   P2  E_z = d_xi psi (Eq. 7) by a block-wide inward scan of the cell currents; Q = P + E_z U;
+//       B_theta from Eq. 6 differentiated in r (Helmholtz form, shift chi), a tridiagonal
+//       system solved by block-wide parallel cyclic reduction on row sums (solve_fields);
+//   P3  per ring: the Cartesian radial force (gamma/Gamma) psi' - B_theta (Eqs. 4-5 with the
+//       centrifugal term carried by the local frame), the move to the next stage's position,
+//       and that position's charge deposit (linear hats).
 // Stage 1 at xi_k writes the slice's fields; stage 2 at xi_k + dxi/2 uses n_b averaged over
 // slices k and k+1.
 //
 // Layout.  Ring state lives in slot arrays (structure of arrays, slot p*NT + t for the p-th
 // ring of thread t): shared memory in the mixed form, global memory in the FP64 form.  A
-// thread's rings are consecutive in radius (the mixed form re-sorts them by cell every few
-// slices), so its deposits are summed over a window of cells in registers, combined across
-// the lanes of a warp that share a window, and flushed with one shared-memory atomic per node
-// and array.  Node work runs warp-synchronously in warp 0 on lane chunks: the scans in a
-// wide type (FP64, or float-float pairs on the FP32 pipe), the tridiagonal solve by chunk
-// elimination plus a 32-unknown interface system solved by cyclic reduction across lanes.
+// thread's rings are consecutive in radius (the mixed form re-sorts them by cell every two
+// slices), so its deposits are summed over a window of three cells in registers, combined
+// across the lanes of a warp that share a window by segmented shuffle sums, and flushed with
+// one shared-memory atomic per segment, node and array.  The node scans run block-wide (each
+// thread up to kScanE consecutive nodes, warp shuffles, one warp for the warp totals) in a
+// wide type: FP64, or float-float pairs on the FP32 pipe.
 #pragma once
 
 #include "wake_common.cuh"

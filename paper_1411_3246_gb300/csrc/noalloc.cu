@@ -130,6 +130,11 @@ extern "C" int wake_beam_deposit_noalloc(const wake_params *p, const double *xyz
                                                             p->rmax, p->ximax, dr, dxi, wd, ww, acc);
   na_normalize_kernel<<<blocks_for(nodes), 256, 0, s>>>(acc, nb, p->nr, p->nxi, dr, dxi);
   e = cudaGetLastError();
-  if (e != cudaSuccess) return fail_na(WAKE_ECUDA, std::string("wake_beam_deposit_noalloc launch: ") + cudaGetErrorString(e));
+  if (e != cudaSuccess) {
+    // a stale address (e.g. after cudaDeviceReset) is looked up again by the next call
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    g_scratch_addr[dev] = nullptr;
+    return fail_na(WAKE_ECUDA, std::string("wake_beam_deposit_noalloc launch: ") + cudaGetErrorString(e));
+  }
   return WAKE_OK;
 }

@@ -392,3 +392,134 @@ def test_beam_push_betatron_frequency():
     assert np.abs(A @ coef - xs).max() < 2e-3 * 0.05
     zero = np.where(np.diff(np.sign(xs)) != 0)[0]
     assert len(zero) == 2
+
+
+# ---------------------------------------------------------------------------------------
+# Boris push, magnetic half (Eqs. 8-11: the v x B term of the Lorentz force)
+# ---------------------------------------------------------------------------------------
+def _btheta_grid(cfg, b0, er0=0.0):
+    """Uniform B_theta = b0 (and E_r = er0) on every node, no E_z."""
+    shape = (cfg.nxi + 1, cfg.nr + 1)
+    return {"er": np.full(shape, er0), "ez": np.zeros(shape), "bth": np.full(shape, b0)}
+
+
+def _one_particle(x, y, ux, uy, uz, xi=5.0):
+    return {"x": np.array([x]), "y": np.array([y]), "ux": np.array([ux]), "uy": np.array([uy]),
+            "xi": np.array([xi]), "uz": np.array([uz]), "lost": np.zeros(1, dtype=np.uint8)}
+
+
+@pytest.mark.parametrize("theta", [0.0, math.pi / 3, -2.0])
+def test_beam_push_pure_btheta_exact_rotation(theta):
+    """A charge -1 in a pure azimuthal field B = b theta_hat, started with u = u_z z_hat at
+    azimuth theta, feels F = q v x B = +v_z b r_hat (since z_hat x theta_hat = -r_hat): its
+    momentum rotates in the (r_hat, z_hat) plane at the rate b/gamma, outwards for b > 0.  The
+    Boris step rotates it by exactly 2 atan(b dt / (2 gamma)) per step and keeps |u| (Boris
+    1970), and the motion stays in the plane of theta, so B keeps its direction."""
+    cfg = synth.config_blowout(n_beam=1, nr=32, nxi=16)
+    b0, uz0 = 0.4, 30.0
+    gam = math.sqrt(1.0 + uz0 * uz0)
+    b = _one_particle(1.0 * math.cos(theta), 1.0 * math.sin(theta), 0.0, 0.0, uz0)
+    f = _btheta_grid(cfg, b0)
+    dphi = 2.0 * math.atan(b0 * cfg.ds / (2.0 * gam))
+    for n in range(1, 4):
+        oracle.beam_push(cfg, b, f)
+        ur_expect = uz0 * math.sin(n * dphi)
+        uz_expect = uz0 * math.cos(n * dphi)
+        ux, uy, uz = b["ux"][0], b["uy"][0], b["uz"][0]
+        assert abs(math.hypot(ux, uy) ** 2 + uz * uz - uz0 * uz0) < 1e-11 * uz0 * uz0
+        assert abs(ux - ur_expect * math.cos(theta)) < 1e-12 * uz0
+        assert abs(uy - ur_expect * math.sin(theta)) < 1e-12 * uz0
+        assert abs(uz - uz_expect) < 1e-12 * uz0
+        # the particle stays on its azimuth (x, y along r_hat)
+        assert abs(b["x"][0] * math.sin(theta) - b["y"][0] * math.cos(theta)) < 1e-12
+    assert ur_expect > 0.0  # outward: the sign of -q v_z B_theta
+
+
+def test_beam_push_radial_current_gives_ez_kick_sign():
+    """The longitudinal half of v x B: a charge -1 moving outwards (v_r > 0) through
+    B = b theta_hat feels F_z = q (v x B)_z = -v_r b, so with no E_z its u_z drops by about
+    b v_r dt in one step, and |u| is kept."""
+    cfg = synth.config_blowout(n_beam=1, nr=32, nxi=16)
+    b0, ur0, uz0 = 0.2, 3.0, 4.0
+    gam = math.sqrt(1.0 + ur0 * ur0 + uz0 * uz0)
+    b = _one_particle(2.0, 0.0, ur0, 0.0, uz0)
+    oracle.beam_push(cfg, b, _btheta_grid(cfg, b0))
+    dphi = 2.0 * math.atan(b0 * cfg.ds / (2.0 * gam))
+    # exact rotation of (u_r, u_z) by dphi towards +r when u_z > 0: u_z' = u_z cos - u_r sin
+    assert abs(b["uz"][0] - (uz0 * math.cos(dphi) - ur0 * math.sin(dphi))) < 1e-12 * gam
+    assert abs(b["ux"][0] - (ur0 * math.cos(dphi) + uz0 * math.sin(dphi))) < 1e-12 * gam
+    assert b["uz"][0] < uz0
+
+
+def test_beam_push_er_equals_btheta_cancels_for_ultrarelativistic():
+    """With E_r = B_theta (a pure plasma-free space-charge field of a v = c source), the
+    transverse force on a co-moving charge -1 is -(E_r - v_z B_theta) = -(1 - v_z) E_r, of
+    order E_r / (2 gamma^2): the electric and magnetic halves of the push must cancel.  At
+    gamma = 4e4 the kick per step is ~1e-9 of the electric kick alone."""
+    cfg = synth.config_blowout(n_beam=1, nr=32, nxi=16)
+    e0, gam = 0.3, 4.0e4
+    b = _one_particle(1.0, 0.0, 0.0, 0.0, gam)
+    oracle.beam_push(cfg, b, _btheta_grid(cfg, e0, er0=e0))
+    electric_only = e0 * cfg.ds  # |u_x| after one step with E_r alone
+    assert abs(b["ux"][0]) < 1e-6 * electric_only
+    # the residual force pulls the electron inwards, -(1 - v_z) E_r: u_x < 0.  At the half
+    # step the electric kick has given it u_perp = dt E_r / 2, so 1 - v_z = (1 + u_perp^2) /
+    # (2 gamma^2) there, and the step's kick is -dt E_r (1 + u_perp^2) / (2 gamma^2)
+    uh = cfg.ds * e0 / 2
+    expect = -cfg.ds * e0 * (1 + uh * uh) / (2 * gam * gam)
+    assert b["ux"][0] < 0.0
+    assert abs(b["ux"][0] - expect) < 0.01 * abs(expect)
+
+
+# ---------------------------------------------------------------------------------------
+# witness diagnostics (Sec. IV: mean energy gain and energy spread of the witness)
+# ---------------------------------------------------------------------------------------
+def _beam_with_gammas(cfg, gammas, lost=None):
+    """Beam of len(gammas) particles at rest transversely with gamma_j given exactly
+    (u_z = sqrt(gamma^2 - 1))."""
+    g = np.asarray(gammas, dtype=np.float64)
+    n = len(g)
+    b = {"x": np.zeros(n), "y": np.zeros(n), "xi": np.full(n, 5.0), "ux": np.zeros(n),
+         "uy": np.zeros(n), "uz": np.sqrt(g * g - 1.0),
+         "lost": np.zeros(n, dtype=np.uint8) if lost is None else np.asarray(lost, dtype=np.uint8)}
+    return b
+
+
+def test_diagnostics_known_witness_statistics():
+    """Witness particles at gamma_b +- a in equal numbers: mean gain 0 and rms spread a
+    exactly (population rms over N, not N - 1).  Drive particles (the first n_drive) and lost
+    particles carry other energies and must not enter the witness sums; the drive sums see
+    only the surviving drive particles."""
+    cfg = synth.config_blowout(n_beam=16, nr=16, nxi=16)
+    gb, a = cfg.gamma_b, 37.5
+    cfg.n_drive = 6
+    drive = [gb - 500.0, gb - 100.0, gb + 50.0, gb - 1000.0, gb + 7.0, gb - 3.0]
+    witness = [gb + a, gb - a] * 4 + [gb + 900.0, gb - 800.0]
+    lost = [0, 0, 0, 1, 0, 0] + [0] * 8 + [1, 1]
+    b = _beam_with_gammas(cfg, drive + witness, lost)
+    out = oracle.diagnostics(cfg, b)
+    assert out[0] == 8
+    assert abs(out[1] - gb) < 1e-9
+    assert abs(out[2] - a) < 1e-9 * a
+    assert out[3] == 5
+    live_drive = [g for g, l in zip(drive, lost[:6]) if not l]
+    assert abs(out[4] - np.mean(live_drive)) < 1e-9
+
+
+def test_witness_obs_weighted_statistics():
+    """Charge-weighted witness observables: gains +a with multiplier 3 and -a with multiplier
+    1 have weighted mean a/2 and weighted rms spread a sqrt(3)/2 (populations, exact); lost and
+    drive particles are left out; with no multipliers the mean is 0 and the spread a."""
+    cfg = synth.config_blowout(n_beam=12, nr=16, nxi=16)
+    gb, a = cfg.gamma_b, 12.0
+    cfg.n_drive = 4
+    gam = [gb + 300.0, gb - 300.0, gb + 5.0, gb - 2.0] + [gb + a, gb - a] * 3 + [gb + 400.0, gb - 400.0]
+    lost = [0] * 10 + [1, 1]
+    wmul = np.array([9.0, 9.0, 9.0, 9.0] + [3.0, 1.0] * 3 + [5.0, 5.0])
+    b = _beam_with_gammas(cfg, gam, lost)
+    m, s = oracle.witness_obs(cfg, b, wmul)
+    assert abs(m - a / 2) < 1e-9 * a
+    assert abs(s - a * math.sqrt(3) / 2) < 1e-9 * a
+    m0, s0 = oracle.witness_obs(cfg, b)
+    assert abs(m0) < 1e-9 * a
+    assert abs(s0 - a) < 1e-9 * a

@@ -89,8 +89,53 @@ def peaks():
 
 
 def fp32_peak_tflops(sm_mhz):
-    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) per clock
+    # nominal: 152 SMs x 128 FP32 lanes x 2 flop (FMA) per clock
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fma_peak_leg(local):
+    """The ALU peaks measured on this GPU in this run: FP32 and FP64 FMA throughput of the
+    package's micro-benchmark (16 independent FMA chains per thread, 8 CTAs of 256 threads per
+    SM, CUDA events), with the SM clock sampled while it runs."""
+    from paper_1411_3246_gb300 import build, peak
+    build.build_peak()
+    peak.fma_tflops(False, iters=1 << 12)  # warm-up (module load, clocks up)
+    with ClockSampler(local) as clk:
+        f32, ms32, _ = peak.fma_tflops(False)
+        f64, ms64, _ = peak.fma_tflops(True)
+    c = clk.summary()
+    return {"fp32_tflops": f32, "fp64_tflops": f64, "fp32_ms": ms32, "fp64_ms": ms64, "clocks": c,
+            "fp32_nominal_at_max_clock": fp32_peak_tflops(2070.0),
+            "how": "FMA chains (16 per thread, 256-thread CTAs, 8 per SM), an FMA = 2 flop, CUDA events"}
+
+
+def latency_leg(wake, torch, stream, nrep=20):
+    """The frozen-driver linear workload (Nr=128 over 6, Nxi=256 over 10, 4 rings/cell, cold,
+    n_b/n_p = 0.1): microseconds per xi-march (one CTA marches the whole box), FP64 and mixed,
+    averaged over nrep back-to-back marches after two untimed ones (CUDA events)."""
+    cfg = synth.config_linear()
+    out = {}
+    for name, prec in (("fp64", wake.WAKE_FP64), ("mixed", wake.WAKE_MIXED)):
+        sim = wake.Simulations([cfg], prec, stream)
+        with torch.cuda.stream(stream):
+            wake.wake_load_plasma(sim.h, 0, None)
+            for _ in range(2):
+                wake.wake_plasma_march(sim.h)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for _ in range(nrep):
+                wake.wake_plasma_march(sim.h)
+            ev[1].record(stream)
+        stream.synchronize()
+        st = sim.status(0)
+        sim.close()
+        if st != wake.WAKE_OK:
+            raise RuntimeError(f"latency leg: status {st}")
+        us = 1e3 * ev[0].elapsed_time(ev[1]) / nrep
+        out[name] = {"us_per_march": us, "plasma_pushes_per_s": plasma_pushes_per_step(cfg) / (us * 1e-6)}
+    out["workload"] = (f"linear frozen driver, Nr={cfg.nr} x Nxi={cfg.nxi}, {cfg.ppc} rings/cell, cold, one march "
+                       f"({plasma_pushes_per_step(cfg)} plasma pushes), {nrep} marches averaged")
+    return out
 
 
 class ClockSampler:
@@ -189,31 +234,73 @@ def oracle_step_rate(cfg, nsteps):
     return (time.perf_counter() - t) / nsteps
 
 
+_ORC = None
+
+
+def _orc_init(cfg):
+    """Worker set-up of the parallel oracle: the workload's plasma and beam (each worker one
+    independent copy of the same simulation)."""
+    global _ORC
+    import oracle
+    _ORC = (cfg, oracle.plasma_init(cfg, synth.plasma_normals(cfg)), oracle.beam_init(cfg, synth.beam_normals(cfg)))
+
+
+def _orc_step(_):
+    """One beam step (deposit, march, push) of the worker's copy; returns its seconds."""
+    import oracle
+    cfg, pl, bm = _ORC
+    t = time.perf_counter()
+    oracle.run(cfg, pl, bm, 1)
+    return time.perf_counter() - t
+
+
+class OraclePool:
+    """The FP64 oracle, as it stands, on the host's cores: one worker process per core (spawned,
+    never forked from a process that has touched the GPU), each advancing its own copy of the
+    workload one beam step per task.  A round is one step on every worker at once."""
+
+    def __init__(self, cfg, procs=None):
+        import multiprocessing as mp
+
+        import oracle
+        oracle.build()
+        self.procs = procs or len(os.sched_getaffinity(0))
+        self.pool = mp.get_context("spawn").Pool(self.procs, initializer=_orc_init, initargs=(cfg,))
+
+    def round(self):
+        """Wall seconds of one step on every worker."""
+        t = time.perf_counter()
+        self.pool.map(_orc_step, range(self.procs), chunksize=1)
+        return time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def run_reference(args, world, rank):
-    """--impl reference: the oracle on the host cores, same metric and workload."""
+    """--impl reference: the oracle on the host cores, same metric and workload.  Each bench
+    step is one beam step of the workload on every core at once (one independent copy per
+    core); the value is the plasma pushes of all copies over the wall time."""
     if rank != 0:
         return
     cfg = workload()
-    import oracle
-    pl = oracle.plasma_init(cfg, synth.plasma_normals(cfg))
-    bm = oracle.beam_init(cfg, synth.beam_normals(cfg))
+    pool = OraclePool(cfg)
     for _ in range(args.warmup):
-        oracle.run(cfg, pl, bm, 1)
-    times = []
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        oracle.run(cfg, pl, bm, 1)
-        times.append(time.perf_counter() - t)
+        pool.round()
+    times = [pool.round() for _ in range(args.steps)]
+    pool.close()
     tot = sum(times)
-    v = plasma_pushes_per_step(cfg) * args.steps / tot
+    v = plasma_pushes_per_step(cfg) * pool.procs * args.steps / tot
     line = {"impl": "reference", "metric": "plasma_pushes_per_s", "value": v, "unit": "pushes/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(cfg, world, BEAM_STEPS),
-            "cpu_baseline": {"value": v, "unit": "pushes/s", "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": "pushes/s", "cores": pool.procs, "kind": "oracle",
                              "sample": f"each step: one beam step (deposit, march, push) of the workload's "
-                                       f"{BEAM_STEPS}, FP64 oracle, one host thread"},
+                                       f"{BEAM_STEPS} on each of {pool.procs} processes at once (one "
+                                       f"independent copy per core), FP64 oracle"},
             "e2e": {"value": v, "unit": "pushes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -436,6 +523,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1, help="timed runs of the FP64 form (0: skip)")
+    ap.add_argument("--mixed64-steps", type=int, default=1, help="timed runs of the FP64-solve split (0: skip)")
     ap.add_argument("--beam-steps", type=int, default=BEAM_STEPS, help="beam steps per run (profiling)")
     ap.add_argument("--nr", type=int, default=0, help="override Nr (profiling a smaller case)")
     ap.add_argument("--nxi", type=int, default=0, help="override Nxi (profiling a smaller case)")
@@ -449,6 +537,7 @@ def main():
                     help="metres the Table I beam is carried in the propagation leg (0: skip)")
     ap.add_argument("--osiris-m", type=float, default=1.4,
                     help="metres the single bunch of the OSIRIS parameter set is carried (0: skip)")
+    ap.add_argument("--latency", type=int, default=1, help="time the one-march latency case (0: skip)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -521,6 +610,19 @@ def main():
                 "ms_per_step": 1e3 * t64 / args.fp64_steps, "steps": args.fp64_steps,
                 "note": "FP64 form of the same pipelined path (rings, fields and sums in FP64)"}
 
+    # --- the precision split with FP64 sums across rings, scans and tridiagonal solves ---
+    mixed64 = None
+    if args.mixed64_steps > 0:
+        r2, k2, d2 = timed_runs(wake.WAKE_MIXED64, args.mixed64_steps, 1)
+        t2 = barrier_max(sum(r2) / 1e3, world)
+        mixed64 = {"value": world * pushes * args.mixed64_steps / t2, "unit": "pushes/s",
+                   "ms_per_step": 1e3 * t2 / args.mixed64_steps, "steps": args.mixed64_steps,
+                   "kernel_ms": sum(k2) / len(k2), "cost_vs_mixed": (sum(r2) / len(r2)) / (sum(run_ms) / len(run_ms)),
+                   "witness": {"mean_gamma": d2[1], "rms_gamma": d2[2], "alive": d2[0]},
+                   "note": "WAKE_MIXED64: FP32 particle arithmetic; FP64 sums across rings, node arrays, scans and "
+                           "tridiagonal solve (charge in exact fixed point); same pipelined path, field window in "
+                           "global memory"}
+
     # --- end to end through the C ABI from pinned host buffers, one run per step ---
     e2e_steps = max(1, min(args.steps, 3))
     h2d = nm_p.numel() * 8 + nm_b.numel() * 8
@@ -565,13 +667,27 @@ def main():
     if args.osiris_m > 0:
         osiris = osiris_leg(wake, torch, args.osiris_m, rank, flush, world)
 
+    # --- the latency-bound case: one march of the linear workload, microseconds ---
+    latency = latency_leg(wake, torch, stream) if args.latency else None
+
+    # --- the ALU peaks of this GPU, measured now (the roofline's denominator) ---
+    fma = fma_peak_leg(local)
+
     # --- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only) ---
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n = 8
-        sps = oracle_step_rate(cfg, n)
-        cpu = {"value": plasma_pushes_per_step(cfg) / sps, "unit": "pushes/s", "cores": 1, "kind": "oracle",
-               "sample": f"{n} beam steps of the workload (FP64 oracle, one host thread)"}
+        pool = OraclePool(cfg)
+        pool.round()  # untimed: the workers' first step
+        n = 2
+        wall = sum(pool.round() for _ in range(n))
+        pool.close()
+        sps = oracle_step_rate(cfg, 2)
+        cpu = {"value": plasma_pushes_per_step(cfg) * pool.procs * n / wall, "unit": "pushes/s",
+               "cores": pool.procs, "kind": "oracle",
+               "sample": f"{n} rounds of one beam step of the workload on each of {pool.procs} processes (one "
+                         f"independent copy per core), after one untimed round; FP64 oracle",
+               "one_thread": {"value": plasma_pushes_per_step(cfg) / sps, "unit": "pushes/s",
+                              "sample": "2 beam steps of the workload, one host thread"}}
 
     pk, src = peaks()
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
@@ -579,13 +695,15 @@ def main():
     flops_run = nbs * (march_flops(cfg) + alive * FLOP_PER_BEAM_PUSH)
     kern_s = sum(kern_ms) / len(kern_ms) / 1e3
     achieved = flops_run / kern_s / 1e12
-    peak = fp32_peak_tflops(sm_mhz)
+    peak = fma["fp32_tflops"]
     default_workload = (cfg.nr, cfg.nxi, cfg.n_beam, nbs) == (512, 2048, 1 << 20, BEAM_STEPS)
     traffic = STEP_TRAFFIC_BYTES if default_workload and step_sources_hash() == STEP_TRAFFIC_SOURCES else None
     roof = {"kernel": "step_kernel<PolMixed>", "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
             "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-            "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (max clock of {src} peaks file)",
+            "peak_source": "measured: FP32 FMA micro-benchmark (paper_1411_3246_gb300/peak) in this run, "
+                           f"median SM clock {fma['clocks']['sm_mhz']} MHz; nominal at {sm_mhz:.0f} MHz "
+                           f"({src} peaks file's max clock): {fp32_peak_tflops(sm_mhz):.1f} TFLOP/s",
             "kernel_ms": 1e3 * kern_s, "kernel_share_of_run": kern_s * 1e3 / (sum(run_ms) / len(run_ms))}
     if rank == 0:
         line = {"metric": "plasma_pushes_per_s", "value": value, "unit": "pushes/s", "n_gpus": world,
@@ -593,11 +711,12 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic", "config": config_dict(cfg, world, nbs),
                 "beam_pushes_per_s": world * cfg.n_beam * nbs * args.steps / tot_s,
-                "fp64_gpu": fp64,
+                "fp64_gpu": fp64, "mixed64": mixed64,
                 "e2e": {"value": world * pushes * e2e_steps / e2e_s, "unit": "pushes/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 5 * 8},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "batched": batched, "adjoint": adjoint,
-                "large": large, "facet": facet, "osiris": osiris,
+                "large": large, "facet": facet, "osiris": osiris, "latency": latency, "alu_peaks": fma,
+                "host_cores": {"nproc": os.cpu_count(), "affinity": len(os.sched_getaffinity(0))},
                 "gpu_launches": KERNELS_PER_RUN * args.steps,
                 "witness": {"mean_gamma": diag[1], "rms_gamma": diag[2], "alive": diag[0]}}
         print(json.dumps(line), flush=True)

@@ -36,14 +36,19 @@ extern "C" {
 #define WAKE_EESCAPE (-6)  /* a plasma ring left [0, rmax]                           */
 #define WAKE_ESTATE (-7)   /* call out of order (e.g. push before any march)         */
 
-#define WAKE_FP64 0  /* FP64 throughout                                              */
-#define WAKE_MIXED 1 /* FP32 particle arithmetic and fields, wider deposit sums      */
+#define WAKE_FP64 0    /* FP64 throughout                                            */
+#define WAKE_MIXED 1   /* FP32 particle arithmetic and fields; charge sums in exact    */
+                       /* fixed point, scans in float-float, FP32 tridiagonal solve    */
+#define WAKE_MIXED64 2 /* FP32 particle arithmetic and fields; the sums across rings,  */
+                       /* the scans and the tridiagonal solve in FP64 (charge sums in  */
+                       /* exact fixed point)                                           */
 
 /*
  * Parameters of one simulation (Sec. II, Eq. 12, Table I notation):
  *   nr, nxi      radial and longitudinal cells of the box [0, rmax] x [0, ximax]
  *   ppc          plasma rings per radial cell (even when u_th > 0)
- *   precision    WAKE_FP64 or WAKE_MIXED (all simulations of one handle must agree)
+ *   precision    WAKE_FP64, WAKE_MIXED or WAKE_MIXED64 (all simulations of one handle must
+ *                agree)
  *   u_th         thermal momentum of the Maxwellian plasma, per component (0: cold)
  *   n_d, n_w, sigma_r, sigma_zd, sigma_zw, xi_d, xi_w
  *                the two-bunch driver density of Eq. 12
@@ -69,8 +74,10 @@ typedef struct wake_sim wake_sim; /* opaque handle: n_sims independent simulatio
  * CUDA stream `stream` (a cudaStream_t; NULL = legacy default stream).  Allocates all
  * scratch: plasma rings, beam state, the beam-density and field grids.  A simulation with
  * n_beam == 0 gets the frozen analytic driver of Eq. 12 on its nodes.
- * Errors: WAKE_EINVAL (sizes out of range: 2 <= nxi, 1 <= ppc; FP64 2 <= nr <= 1024 and
- * nr*ppc <= 8192; mixed 2 <= nr <= 2048 and nr*ppc <= 65536; precision mismatch),
+ * Errors: WAKE_EINVAL (sizes out of range: 2 <= nxi, 1 <= ppc; FP64 and WAKE_MIXED64
+ * 2 <= nr <= 1024 and nr*ppc <= 8192, WAKE_MIXED64 also within one CTA's shared memory
+ * (about 4,500 rings at nr = 512); mixed 2 <= nr <= 2048 and nr*ppc <= 65536; precision
+ * mismatch),
  * WAKE_ENOMEM, WAKE_ECUDA.
  */
 int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out);
@@ -115,6 +122,24 @@ int wake_beam_deposit(wake_sim *s);
  */
 int wake_plasma_march(wake_sim *s);
 
+/*
+ * The march of simulation `sim` alone, as wake_plasma_march does it (fields to the handle's
+ * grids), that also records the plasma rings' trajectories (Sec. IV, Figs. 4-5: electron
+ * trajectories in the cold and the warm plasma).  At every slice k = 0, every, 2 every, ...
+ * <= nxi, ring j's radius r, radial momentum u_r and Gamma = gamma - u_z (Eq. 1, at the slice's
+ * first RK2 stage) go to traj[((k / every) * 3 + q) * np + j], q = 0 (r), 1 (u_r), 2 (Gamma),
+ * np = nr * ppc, j the ring's index in the initial slice (cell-major, as wake_load_plasma
+ * lays the rings out).
+ *   every  >= 1
+ *   traj   device, (nxi / every + 1) * 3 * np doubles, caller-owned, overwritten
+ * One CTA of 512 threads runs the march, so the simulation must fit one: nr + 1 <= 1536 and
+ * its rings in shared memory (the tile form; not the wide form of wake_tile).  WAKE_FP64 and
+ * WAKE_MIXED handles only.  Asynchronous.
+ * Errors: WAKE_EINVAL (bad sim, every < 1, null traj, too large), WAKE_ESTATE (no plasma),
+ * WAKE_ECUDA.
+ */
+int wake_plasma_march_traj(wake_sim *s, int sim, int every, double *traj);
+
 /* One beam time step of length ds (Eqs. 8-11, Boris) through the fields of the last march,
  * for every simulation with a beam.  Needs a march. */
 int wake_beam_push(wake_sim *s);
@@ -132,7 +157,10 @@ int wake_beam_push(wake_sim *s);
  * that has a beam, the steps run pipelined: the beam is sorted by xi cell and one
  * cooperative launch marches up to one step per SM, each step a few slices behind the one
  * before, pushing each cell of the beam as soon as its fields are solved (same arithmetic as
- * the separate calls; only the order of the deposit sums differs).  A particle that slips
+ * the separate calls; only the order of the deposit sums differs).  A step whose wait for the
+ * step before it gives up (after WAKE_SPIN_LIMIT polls of >= 128 ns, the environment variable
+ * read by wake_init; default 2^24) leaves cleanly and raises WAKE_ETIMEOUT through wake_status.
+ * A particle that slips
  * two or more cells past the cell it was sorted into during a launch is pushed when that
  * cell's fields are solved.  The beam must slip less than a cell per step: a beam whose
  * fastest particle, measured at the start of each launch, slips more than 1/8 of a cell

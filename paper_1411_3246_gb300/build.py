@@ -9,11 +9,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libwake.so")
+PEAK_LIB = os.path.join(BUILD, "libfppeak.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # the mixed-precision marches use approximate FP32 divide and square root (a few ulp) and
 # flush denormals; every other translation unit keeps IEEE division and sqrt
 _FAST = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
-EXTRA = {"march_mixed.cu": _FAST, "march_mixed_small.cu": _FAST, "march_wide.cu": _FAST}
+EXTRA = {"march_mixed.cu": _FAST, "march_mixed_small.cu": _FAST, "march_wide.cu": _FAST, "march_traj_mixed.cu": _FAST,
+         "march_mixed64.cu": _FAST}
 
 
 def sources():
@@ -54,5 +56,20 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+def build_peak(force: bool = False) -> str:
+    """Compile the FMA-throughput micro-benchmark (peak/fp_peak.cu) into libfppeak.so."""
+    src = os.path.join(HERE, "peak", "fp_peak.cu")
+    if not force and os.path.exists(PEAK_LIB) and os.path.getmtime(PEAK_LIB) >= os.path.getmtime(src):
+        return PEAK_LIB
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = PEAK_LIB + f".tmp{os.getpid()}"
+    subprocess.check_call([nvcc, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared", "-o", tmp,
+                           src, "-lcudart"])
+    os.replace(tmp, PEAK_LIB)
+    return PEAK_LIB
+
+
 if __name__ == "__main__":
     print(build(force=True, verbose=True))
+    print(build_peak(force=True))

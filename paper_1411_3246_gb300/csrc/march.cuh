@@ -101,15 +101,19 @@ __device__ __forceinline__ W warp_excl_suffix(W v, int lane) {
 }
 
 // ---------------------------------------------------------------------------------------
-// precision policies.  R: ring and node arithmetic; Acc: current-type deposit sums; Q: charge
-// deposit sums (psi comes from the small difference rho - rho0 of two large sums, so the mixed
-// form sums exact float-float products as 64-bit integers, which makes rho - rho0 exact);
-// G: grid element type in global memory; W: scan type.  Mixed: rings in shared memory, re-sorted by cell every
-// kSortEvery slices, node coefficients computed on the fly.  FP64: rings in global memory in
-// their initial order, node coefficients from tables (FP64 division is slow on this chip).
+// precision policies.  R: ring arithmetic; N: node arrays and the radial solves; Acc:
+// current-type deposit sums across rings (a thread's own rings are summed in R first); Q:
+// charge deposit sums (psi comes from the small difference rho - rho0 of two large sums, so
+// the mixed forms sum exact float-float products as 64-bit integers, which makes rho - rho0
+// exact); G: grid element type in global memory; W: scan type.  Mixed: rings in shared
+// memory, re-sorted by cell every kSortEvery slices, node coefficients computed on the fly.
+// FP64: rings in global memory in their initial order, node coefficients from tables (FP64
+// division is slow on this chip).  kWinGlobal: the pipelined step keeps its field window in
+// global memory (its shared memory is full).
 // ---------------------------------------------------------------------------------------
 struct PolFP64 {
   using R = double;
+  using N = double;
   using Acc = double;
   using Q = double;  // charge deposit sums
   using G = double;
@@ -118,10 +122,12 @@ struct PolFP64 {
   static constexpr int kSortEvery = 0;
   static constexpr bool kSmemRings = false;
   static constexpr bool kTables = true;
+  static constexpr bool kWinGlobal = false;
   static constexpr int kScanE = 3;  // nodes per thread in the block scans: n1 <= kScanE * NT
 };
 struct PolMixed {
   using R = float;
+  using N = float;
   using Acc = float;
   using Q = long long;  // charge deposit sums: 64-bit fixed point, 2^-44 resolution
   using G = float;
@@ -130,6 +136,25 @@ struct PolMixed {
   static constexpr int kSortEvery = 2;
   static constexpr bool kSmemRings = true;
   static constexpr bool kTables = false;
+  static constexpr bool kWinGlobal = false;
+  static constexpr int kScanE = 3;
+};
+// The precision split in which only the particle arithmetic is FP32: each ring's push and its
+// deposit terms (and a thread's sum over its own few rings) in FP32; the per-slice reductions
+// across rings (current sums in FP64, charge in exact fixed point), the node arrays, the scans
+// and the tridiagonal solve in FP64.
+struct PolMixed64 {
+  using R = float;
+  using N = double;
+  using Acc = double;
+  using Q = long long;
+  using G = float;
+  using W = double;
+  static constexpr int NT = 512;
+  static constexpr int kSortEvery = 2;
+  static constexpr bool kSmemRings = true;
+  static constexpr bool kTables = false;
+  static constexpr bool kWinGlobal = true;
   static constexpr int kScanE = 3;
 };
 // The mixed arithmetic for boxes too large for one CTA's shared memory to hold the rings
@@ -137,6 +162,7 @@ struct PolMixed {
 // re-sorted by cell every two slices; block scans of up to 5 nodes per thread.
 struct PolWide {
   using R = float;
+  using N = float;
   using Acc = float;
   using Q = long long;
   using G = float;
@@ -145,19 +171,23 @@ struct PolWide {
   static constexpr int kSortEvery = 2;  // rings re-sorted by cell through a second global buffer
   static constexpr bool kSmemRings = false;
   static constexpr bool kTables = false;
+  static constexpr bool kWinGlobal = false;
   static constexpr int kScanE = 5;
 };
 
 // Ring slot arrays: cell index, offset in the cell, u_r, the constants l_z, Gamma_0, w, and
-// the stage-1 Gamma and radial force kept for the full step.
+// the stage-1 Gamma and radial force kept for the full step; with ids, each slot also carries
+// its ring's initial index (it follows the ring through the re-sorts; the trajectory dump
+// uses it).
 template <class R>
 struct RingSoA {
   int *c;
   R *f, *ur, *lz, *G0, *w, *G1, *F1;
-  __host__ __device__ static size_t bytes(int slots) {
-    return sizeof(int) * (size_t)slots + 32 + 7 * sizeof(R) * (size_t)slots;
+  int *id = nullptr;
+  __host__ __device__ static size_t bytes(int slots, bool ids = false) {
+    return sizeof(int) * (size_t)slots + 32 + 7 * sizeof(R) * (size_t)slots + (ids ? sizeof(int) * (size_t)slots + 32 : 0);
   }
-  __device__ __forceinline__ void carve(void *base, int slots) {
+  __device__ __forceinline__ void carve(void *base, int slots, bool ids = false) {
     c = (int *)base;
     R *p = (R *)(((uintptr_t)(c + slots) + 31) & ~(uintptr_t)31);
     f = p; p += slots;
@@ -167,32 +197,35 @@ struct RingSoA {
     w = p; p += slots;
     G1 = p; p += slots;
     F1 = p; p += slots;
+    id = ids ? (int *)(((uintptr_t)p + 31) & ~(uintptr_t)31) : nullptr;
   }
 };
 
 template <class Pol>
 struct MarchSmem {
   using R = typename Pol::R;
+  using N = typename Pol::N;
   using Acc = typename Pol::Acc;
   typename Pol::Q *rho0, *rho;                  // charge deposits
   Acc *jz, *chi, *T, *P, *U, *K;                // current-type deposits
-  R *psi, *dpsi, *ez, *bth;                     // node fields
+  N *psi, *dpsi, *ez, *bth;                     // node fields
   R *nb0, *nb1;                                 // beam-density rows (double buffer)
-  R *ta, *tb, *tc, *td;                         // tridiagonal rows (a, row sum, c, rhs)
-  R *invR, *invV, *alpha, *ga, *gb, *gc;        // tables (FP64 form; the mixed form keeps
+  N *ta, *tb, *tc, *td;                         // tridiagonal rows (a, row sum, c, rhs)
+  N *invR, *invV, *alpha, *ga, *gb, *gc;        // tables (FP64 form; the mixed forms keep
                                                 // invR = 1/(m dr) and ga = 1/(j + 1/2) only)
   int *cnt;                                     // re-sort counts
   typename Pol::W *wtot;                        // block-scan warp totals
   RingSoA<R> rings;                             // ring slots (mixed form)
 
-  __host__ __device__ static size_t bytes(int n1, int slots) {
-    size_t b = sizeof(typename Pol::W) * 64 + sizeof(typename Pol::Q) * 2 * (size_t)n1 + sizeof(Acc) * 6 * (size_t)n1 + sizeof(R) * 6 * (size_t)n1 + sizeof(R) * 4 * ((size_t)n1 + 32) + 256;
-    b += sizeof(R) * (Pol::kTables ? 6 : 2) * (size_t)n1;
+  __host__ __device__ static size_t bytes(int n1, int slots, bool ids = false) {
+    size_t b = sizeof(typename Pol::W) * 64 + sizeof(typename Pol::Q) * 2 * (size_t)n1 + sizeof(Acc) * 6 * (size_t)n1 +
+               sizeof(N) * 4 * (size_t)n1 + sizeof(R) * 2 * (size_t)n1 + sizeof(N) * 4 * ((size_t)n1 + 32) + 256;
+    b += sizeof(N) * (Pol::kTables ? 6 : 2) * (size_t)n1;
     if (Pol::kSortEvery > 0) b += sizeof(int) * ((size_t)n1 + 32);
-    if (Pol::kSmemRings) b += RingSoA<R>::bytes(slots) + 32;
+    if (Pol::kSmemRings) b += RingSoA<R>::bytes(slots, ids) + 32;
     return b;
   }
-  __device__ void carve(unsigned char *base, int n1, int slots) {
+  __device__ void carve(unsigned char *base, int n1, int slots, bool ids = false) {
     wtot = (typename Pol::W *)base;
     typename Pol::Q *qp = (typename Pol::Q *)(wtot + 64);
     rho0 = qp; qp += n1;
@@ -204,13 +237,11 @@ struct MarchSmem {
     P = ap; ap += n1;
     U = ap; ap += n1;
     K = ap; ap += n1;
-    R *rp = (R *)ap;
+    N *rp = (N *)ap;
     psi = rp; rp += n1;
     dpsi = rp; rp += n1;
     ez = rp; rp += n1;
     bth = rp; rp += n1;
-    nb0 = rp; rp += n1;
-    nb1 = rp; rp += n1;
     ta = rp; rp += n1 + 32;
     tb = rp; rp += n1 + 32;
     tc = rp; rp += n1 + 32;
@@ -224,13 +255,16 @@ struct MarchSmem {
       gb = rp; rp += n1;
       gc = rp; rp += n1;
     }
-    int *ip = (int *)rp;
+    R *bp = (R *)rp;
+    nb0 = bp; bp += n1;
+    nb1 = bp; bp += n1;
+    int *ip = (int *)(((uintptr_t)bp + 7) & ~(uintptr_t)7);
     cnt = nullptr;
     if (Pol::kSortEvery > 0) {
       cnt = ip;
       ip += n1 + 32;
     }
-    if (Pol::kSmemRings) rings.carve((void *)(((uintptr_t)ip + 31) & ~(uintptr_t)31), slots);
+    if (Pol::kSmemRings) rings.carve((void *)(((uintptr_t)ip + 31) & ~(uintptr_t)31), slots, ids);
   }
 };
 
@@ -244,7 +278,7 @@ __device__ __forceinline__ double div_rn(double a, double b) { return a / b; }
 
 template <class Pol>
 struct NodeGeo {
-  using R = typename Pol::R;
+  using R = typename Pol::N;  // node arithmetic
   const R *t_invR, *t_invV, *t_alpha, *t_ga, *t_gb, *t_gc;
   int nr;
   R dr, inv_dr, inv_dr2, dr_6, v_wall_inv;
@@ -286,7 +320,7 @@ struct NodeGeo {
 
 template <class Pol, int NT>
 __device__ __forceinline__ void fill_tables(MarchSmem<Pol> &sm, int nr, double dr) {
-  using R = typename Pol::R;
+  using R = typename Pol::N;
   for (int m = threadIdx.x; m <= nr; m += NT) {
     sm.invR[m] = (R)(m > 0 ? 1.0 / ((double)m * dr) : 0.0);
     if constexpr (Pol::kTables) {
@@ -332,6 +366,10 @@ template <class Q, class W>
 __device__ __forceinline__ W q_to_wide(Q d);
 template <>
 __device__ __forceinline__ double q_to_wide<double, double>(double d) { return d; }
+template <>
+__device__ __forceinline__ double q_to_wide<long long, double>(long long d) {
+  return (double)d * (1.0 / kQScale);  // exact: |d| < 2^53 and the scale is a power of two
+}
 template <>
 __device__ __forceinline__ FF q_to_wide<long long, FF>(long long d) {
   // exact split of the integer into two floats, then the exact power-of-two rescale
@@ -441,7 +479,7 @@ __device__ __forceinline__ void block_scan_fused(int n, W *wtot, In &&in, Out &&
 // psi'_m = Phi_m / r_m, psi(R) = 0, psi = inward trapezoid sum of psi'.  Ends with a barrier.
 template <class Pol, int NT>
 __device__ __forceinline__ void solve_psi(MarchSmem<Pol> &sm, const NodeGeo<Pol> &geo, typename Pol::W *wtot) {
-  using R = typename Pol::R;
+  using R = typename Pol::N;
   using W = typename Pol::W;
   const int nr = geo.nr, n1 = nr + 1;
   block_scan_fused<NT, Pol::kScanE, false, W>(
@@ -465,7 +503,7 @@ __device__ __forceinline__ void solve_psi(MarchSmem<Pol> &sm, const NodeGeo<Pol>
 template <class Pol, int NT>
 __device__ __forceinline__ void solve_fields(MarchSmem<Pol> &sm, const NodeGeo<Pol> &geo, const typename Pol::R *nbA,
                                              const typename Pol::R *nbB, typename Pol::W *wtot) {
-  using R = typename Pol::R;
+  using R = typename Pol::N;
   using W = typename Pol::W;
   using Acc = typename Pol::Acc;
   const int tid = threadIdx.x, nr = geo.nr, n1 = nr + 1;
@@ -484,7 +522,7 @@ __device__ __forceinline__ void solve_fields(MarchSmem<Pol> &sm, const NodeGeo<P
   // node densities (deposit / hat volume; J_z less the beam density averaged over the two
   // rows) read where the rows need them
   auto dens = [&](const Acc *v, int m) -> R { return (R)v[m] * geo.invV(m); };
-  auto jz_node = [&](int m) -> R { return (R)sm.jz[m] * geo.invV(m) - (R)0.5 * (nbA[m] + nbB[m]); };
+  auto jz_node = [&](int m) -> R { return (R)sm.jz[m] * geo.invV(m) - (R)0.5 * ((R)nbA[m] + (R)nbB[m]); };
   // rows q = 0..nr-1 (node i = q + 1): central differences, a half cell at the wall
   const R i2dr = (R)0.5 * inv_dr;
   for (int q = tid; q < nr; q += NT) {
@@ -690,6 +728,8 @@ struct ChargeWin<PolMixed> {
 
 template <>
 struct ChargeWin<PolWide> : ChargeWin<PolMixed> {};
+template <>
+struct ChargeWin<PolMixed64> : ChargeWin<PolMixed> {};
 
 __device__ __forceinline__ void q_atomic_add(double *p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void q_atomic_add(long long *p, long long v) {
@@ -782,13 +822,13 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
   const WarpSeg seg(acc.c0);
   const int c = acc.c0;
   const bool emit = seg.is_tail && c >= 0;
-  R tot[23];
+  Acc tot[23];  // the thread's window sums, then summed across rings in the deposit type
 #pragma unroll
   for (int q = 0; q < 5; ++q)
 #pragma unroll
-    for (int a = 0; a < 4; ++a) tot[q * 4 + a] = acc.n[a][q];
+    for (int a = 0; a < 4; ++a) tot[q * 4 + a] = (Acc)acc.n[a][q];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) tot[20 + a] = kw[a];
+  for (int a = 0; a < 3; ++a) tot[20 + a] = (Acc)kw[a];
   seg.sum_n(tot);
   Acc *arr[5] = {sm.jz, sm.chi, sm.T, sm.P, sm.U};
 #pragma unroll
@@ -806,17 +846,18 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
 // are counted in registers, combined over warp segments and take their bases with one atomic
 // per cell and segment; others take a rank with their own atomic.  The slot arrays are
 // permuted in place through registers.  Order within a cell follows the atomics.
-template <class Pol, int NT, int PPT>
+template <class Pol, int NT, int PPT, bool kIds = false>
 __device__ __forceinline__ void resort_rings(MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int np, int nr) {
   using R = typename Pol::R;
   const int t = threadIdx.x, n1 = nr + 1;
   for (int m = t; m < n1; m += NT) sm.cnt[m] = 0;
-  int rc[PPT];
+  int rc[PPT], rid[kIds ? PPT : 1];
   R rf[PPT], rur[PPT], rlz[PPT], rG0[PPT], rw[PPT];
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
     rc[p] = 0;
     rf[p] = rur[p] = rlz[p] = rG0[p] = rw[p] = (R)0;
+    if constexpr (kIds) rid[p] = 0;
     if (t * PPT + p < np) {
       const int sl = p * NT + t;
       rc[p] = rs.c[sl];
@@ -825,6 +866,7 @@ __device__ __forceinline__ void resort_rings(MarchSmem<Pol> &sm, const RingSoA<t
       rlz[p] = rs.lz[sl];
       rG0[p] = rs.G0[sl];
       rw[p] = rs.w[sl];
+      if constexpr (kIds) rid[p] = rs.id[sl];
     }
   }
   __syncthreads();
@@ -901,6 +943,7 @@ __device__ __forceinline__ void resort_rings(MarchSmem<Pol> &sm, const RingSoA<t
       rs.lz[sl] = rlz[p];
       rs.G0[sl] = rG0[p];
       rs.w[sl] = rw[p];
+      if constexpr (kIds) rs.id[sl] = rid[p];
     }
   __syncthreads();
 }
@@ -911,6 +954,10 @@ __device__ __forceinline__ void resort_rings(MarchSmem<Pol> &sm, const RingSoA<t
 //   R    nb_row(int row, int m)     beam density at node m of a row
 //   void slice_done(int k, sm)      stage-1 fields of slice k are in sm (psi, dpsi, ez, bth)
 //   void finish(sm)                 after the last slice
+//   kTraj, ring_state<NT, PPT>(k, rs, np)
+//                                   (kTraj true only) the slice-k state of the thread's own
+//                                   rings, with their stage-1 Gamma in rs.G1; the slots carry
+//                                   ring ids
 template <class Pol, int NT, int PPT, class Hooks>
 __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem_raw, Hooks &hk) {
   using R = typename Pol::R;
@@ -918,17 +965,19 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
   using Acc = typename Pol::Acc;
   const int tid = threadIdx.x, nr = d.nr, n1 = nr + 1, np = d.np, nxi = d.nxi;
   constexpr int SLOTS = NT * PPT;
+  constexpr bool kIds = Hooks::kTraj;
   MarchSmem<Pol> sm;
-  sm.carve(smem_raw, n1, SLOTS);
+  sm.carve(smem_raw, n1, SLOTS, kIds);
   RingSoA<R> rs;
   if (Pol::kSmemRings)
     rs = sm.rings;
   else
-    rs.carve(d.ring_buf, SLOTS);
+    rs.carve(d.ring_buf, SLOTS, kIds);
   const double drd = d.dr;
   const R h = (R)d.dxi, R_wall = (R)d.rmax, dR = (R)drd, inv_dr = (R)(1.0 / drd);
-  const NodeGeo<Pol> geo{sm.invR, sm.invV, sm.alpha, sm.ga, sm.gb, sm.gc, nr, dR, inv_dr, (R)(1.0 / (drd * drd)),
-                          (R)(drd / 6.0), (R)(1.0 / (0.5 * nr - 1.0 / 6.0))};
+  using N = typename Pol::N;
+  const NodeGeo<Pol> geo{sm.invR, sm.invV, sm.alpha, sm.ga, sm.gb, sm.gc, nr, (N)drd, (N)(1.0 / drd), (N)(1.0 / (drd * drd)),
+                          (N)(drd / 6.0), (N)(1.0 / (0.5 * nr - 1.0 / 6.0))};
   fill_tables<Pol, NT>(sm, nr, drd);
   for (int m = tid; m < n1; m += NT) {
     sm.rho[m] = (typename Pol::Q)0;
@@ -950,6 +999,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
       rs.lz[sl] = (R)d.lz[j];
       rs.G0[sl] = (R)d.G0[j];
       rs.w[sl] = (R)d.w[j];
+      if constexpr (kIds) rs.id[sl] = j;
     }
   }
   __syncthreads();
@@ -997,7 +1047,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
 
   R G2[PPT], F2[PPT];
   for (int k = 0; k <= nxi; ++k) {
-    if (Pol::kSortEvery > 0 && k > 0 && k % Pol::kSortEvery == 0) resort_rings<Pol, NT, PPT>(sm, rs, np, nr);
+    if (Pol::kSortEvery > 0 && k > 0 && k % Pol::kSortEvery == 0) resort_rings<Pol, NT, PPT, kIds>(sm, rs, np, nr);
     const R *nbk = (k & 1) ? sm.nb1 : sm.nb0, *nbk1 = (k & 1) ? sm.nb0 : sm.nb1;
     if (!hk.wait_rows(k)) break;
     if (k == 0)  // row 0 is first read in P2, after two barriers
@@ -1028,6 +1078,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
           rs.G1[p * NT + tid] = Gs[p];
           rs.F1[p * NT + tid] = gqs[p];
         }
+      if constexpr (Hooks::kTraj) hk.template ring_state<NT, PPT>(k, rs, np);
     }
     __syncthreads();
     solve_fields<Pol, NT>(sm, geo, nbk, nbk, sm.wtot);  // P2
@@ -1132,6 +1183,7 @@ template <class Pol, int NT>
 struct PlainHooks {
   using R = typename Pol::R;
   using G = typename Pol::G;
+  static constexpr bool kTraj = false;
   const G *nb;
   G *opsi, *oez, *oer, *obth;
   int n1;
@@ -1161,6 +1213,48 @@ __global__ void __launch_bounds__(NT, (NT < 512 ? 512 / NT : 1)) march_kernel(co
   const SimDesc &d = descs[order ? order[blockIdx.x] : blockIdx.x];
   PlainHooks<Pol, NT> hk{(const typename Pol::G *)d.nb, (typename Pol::G *)d.psi, (typename Pol::G *)d.ez,
                          (typename Pol::G *)d.er, (typename Pol::G *)d.bth, d.nr + 1, d.status};
+  march_body<Pol, NT, PPT>(d, smem_raw, hk);
+}
+
+// The plain march that also records the rings' trajectories (Sec. IV, Figs. 4-5): at every
+// slice k that is a multiple of `every`, ring j's radius, u_r and Gamma go to
+// traj[((k / every) * 3 + q) * np + j], q = 0, 1, 2 (j its index in the initial slice).
+template <class Pol, int NT>
+struct TrajHooks : PlainHooks<Pol, NT> {
+  static constexpr bool kTraj = true;
+  double *traj;
+  int every;
+  double dr;
+  template <int NT_, int PPT>
+  __device__ __forceinline__ void ring_state(int k, const RingSoA<typename Pol::R> &rs, int np) const {
+    if (k % every) return;
+    double *row = traj + (size_t)(k / every) * 3 * np;
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+      if (threadIdx.x * PPT + p < np) {
+        const int sl = p * NT_ + threadIdx.x, j = rs.id[sl];
+        row[j] = ((double)rs.c[sl] + (double)rs.f[sl]) * dr;
+        row[np + j] = (double)rs.ur[sl];
+        row[2 * (size_t)np + j] = (double)rs.G1[sl];
+      }
+  }
+};
+
+template <class Pol, int NT, int PPT>
+__global__ void __launch_bounds__(NT, 1) march_traj_kernel(const SimDesc *desc, double *traj, int every) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SimDesc &d = *desc;
+  TrajHooks<Pol, NT> hk;
+  hk.nb = (const typename Pol::G *)d.nb;
+  hk.opsi = (typename Pol::G *)d.psi;
+  hk.oez = (typename Pol::G *)d.ez;
+  hk.oer = (typename Pol::G *)d.er;
+  hk.obth = (typename Pol::G *)d.bth;
+  hk.n1 = d.nr + 1;
+  hk.status = d.status;
+  hk.traj = traj;
+  hk.every = every;
+  hk.dr = d.dr;
   march_body<Pol, NT, PPT>(d, smem_raw, hk);
 }
 

@@ -16,14 +16,15 @@ bool march_tile_fp64(int nt, int ppt, TileFns *out) {
   }
 }
 
-bool march_tile(int precision_fp64, int nt, int ppt, TileFns *out) {
-  if (precision_fp64) return march_tile_fp64(nt, ppt, out);
+bool march_tile(int form, int nt, int ppt, TileFns *out) {
+  if (form == kFormFP64) return march_tile_fp64(nt, ppt, out);
+  if (form == kFormMixed64) return march_tile_mixed64(nt, ppt, out);
   return nt == 512 ? march_tile_mixed512(nt, ppt, out) : march_tile_mixed_small(nt, ppt, out);
 }
 
-size_t ring_buf_bytes(int precision_fp64) {
+size_t ring_buf_bytes(int form) {
   // the FP64 form keeps its ring slots in global memory: room for the largest variant
-  return precision_fp64 ? RingSoA<double>::bytes(PolFP64::NT * 16) : 0;
+  return form == kFormFP64 ? RingSoA<double>::bytes(PolFP64::NT * 16, true) : 0;
 }
 
 
@@ -88,11 +89,13 @@ int step_ctas_fp64(int n1, int np) {
 cudaError_t launch_step_mixed(const PipeArgs &a, int np, int ctas, cudaStream_t stream);
 int step_ctas_mixed(int n1, int np);
 
-bool step_smem_ok(int precision_fp64, int n1, int np) { return step_max_ctas(precision_fp64, n1, np) > 0; }
-int step_max_ctas(int precision_fp64, int n1, int np) {
-  return precision_fp64 ? step_ctas_fp64(n1, np) : step_ctas_mixed(n1, np);
+bool step_smem_ok(int form, int n1, int np) { return step_max_ctas(form, n1, np) > 0; }
+int step_max_ctas(int form, int n1, int np) {
+  return form == kFormFP64 ? step_ctas_fp64(n1, np) : form == kFormMixed64 ? step_ctas_mixed64(n1, np) : step_ctas_mixed(n1, np);
 }
-cudaError_t launch_step(int precision_fp64, const PipeArgs &a, int np, int ctas, cudaStream_t stream) {
-  return precision_fp64 ? launch_step_fp64(a, np, ctas, stream) : launch_step_mixed(a, np, ctas, stream);
+size_t step_global_window_bytes(int form, int n1) { return form == kFormMixed64 ? step_window_bytes(n1) : 0; }
+cudaError_t launch_step(int form, const PipeArgs &a, int np, int ctas, cudaStream_t stream) {
+  return form == kFormFP64 ? launch_step_fp64(a, np, ctas, stream)
+                           : form == kFormMixed64 ? launch_step_mixed64(a, np, ctas, stream) : launch_step_mixed(a, np, ctas, stream);
 }
 }  // namespace wake

@@ -12,6 +12,9 @@ struct PipeArgs;
 
 constexpr size_t kMaxSmemPerCta = 227 * 1024;
 
+// Precision forms, numbered as the library's WAKE_FP64, WAKE_MIXED and WAKE_MIXED64.
+enum Form : int { kFormFP64 = 0, kFormMixed = 1, kFormMixed64 = 2 };
+
 // A compiled march tile: NT threads per CTA, PPT rings per thread (march_tiles.cuh).
 struct TileFns {
   int nt, ppt;
@@ -23,10 +26,11 @@ struct TileFns {
   int (*occupancy)(int n1);  // CTAs per SM for n1 nodes, 0 if it does not fit
 };
 // The tile (nt, ppt) of a precision form, if it is compiled.
-bool march_tile(int precision_fp64, int nt, int ppt, TileFns *out);
+bool march_tile(int form, int nt, int ppt, TileFns *out);
 bool march_tile_fp64(int nt, int ppt, TileFns *out);
 bool march_tile_mixed512(int nt, int ppt, TileFns *out);
 bool march_tile_mixed_small(int nt, int ppt, TileFns *out);
+bool march_tile_mixed64(int nt, int ppt, TileFns *out);
 // The wide mixed march (march_wide.cuh) and its ring buffer for np rings.
 TileFns march_tile_wide();
 size_t wide_ring_bytes(int np);
@@ -44,12 +48,24 @@ cudaError_t launch_batch_steps(const BatchArgs &b, int max_n1, int bnt, int ctas
 
 // Global-memory ring slot storage one simulation needs (0 when the rings live in shared
 // memory).
-size_t ring_buf_bytes(int precision_fp64);
+size_t ring_buf_bytes(int form);
 // Pipelined beam steps of one simulation (pipeline.cuh): one cooperative launch of up to
 // max_ctas CTAs.  step_smem_ok tells whether the pipelined kernel fits shared memory;
 // step_max_ctas how many CTAs can be co-resident.
-bool step_smem_ok(int precision_fp64, int n1, int np);
-int step_max_ctas(int precision_fp64, int n1, int np);
-cudaError_t launch_step(int precision_fp64, const PipeArgs &a, int np, int ctas, cudaStream_t stream);
+// Global field-window bytes per CTA the form's pipelined step needs (0: in shared memory).
+bool step_smem_ok(int form, int n1, int np);
+int step_max_ctas(int form, int n1, int np);
+size_t step_global_window_bytes(int form, int n1);
+cudaError_t launch_step(int form, const PipeArgs &a, int np, int ctas, cudaStream_t stream);
+cudaError_t launch_step_mixed64(const PipeArgs &a, int np, int ctas, cudaStream_t stream);
+int step_ctas_mixed64(int n1, int np);
+
+// The plain march with the ring trajectory dump (march_traj_kernel), one CTA of 512 threads:
+// its shared memory for n1 nodes and np rings (more than kMaxSmemPerCta: no variant fits),
+// and its launch on the descriptor d (device).
+size_t march_traj_smem_fp64(int n1, int np);
+size_t march_traj_smem_mixed(int n1, int np);
+cudaError_t launch_march_traj_fp64(const SimDesc *d, int n1, int np, double *traj, int every, cudaStream_t s);
+cudaError_t launch_march_traj_mixed(const SimDesc *d, int n1, int np, double *traj, int every, cudaStream_t s);
 
 }  // namespace wake

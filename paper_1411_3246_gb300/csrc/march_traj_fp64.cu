@@ -1,0 +1,42 @@
+// The plain march with the ring trajectory dump (march.cuh march_traj_kernel), FP64 form:
+// one CTA of 512 threads, rings in PPT = 1..16 per thread.
+#include "march.cuh"
+#include "march_launch.h"
+
+namespace wake {
+
+namespace {
+template <int PPT>
+cudaError_t go_traj(const SimDesc *d, int n1, double *traj, int every, cudaStream_t s) {
+  auto kern = march_traj_kernel<PolFP64, 512, PPT>;
+  const size_t smem = MarchSmem<PolFP64>::bytes(n1, 512 * PPT, true);
+  if (smem > kMaxSmemPerCta) return cudaErrorInvalidValue;
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<1, 512, smem, s>>>(d, traj, every);
+  return cudaGetLastError();
+}
+int traj_ppt(int np) {
+  const int ppt = (np + 511) / 512;
+  return ppt <= 1 ? 1 : ppt <= 2 ? 2 : ppt <= 4 ? 4 : ppt <= 8 ? 8 : ppt <= 16 ? 16 : 0;
+}
+}  // namespace
+
+size_t march_traj_smem_fp64(int n1, int np) {
+  const int ppt = traj_ppt(np);
+  if (ppt == 0 || n1 > 3 * 512) return (size_t)1 << 40;
+  return MarchSmem<PolFP64>::bytes(n1, 512 * ppt, true);
+}
+
+cudaError_t launch_march_traj_fp64(const SimDesc *d, int n1, int np, double *traj, int every, cudaStream_t s) {
+  switch (traj_ppt(np)) {
+    case 1: return go_traj<1>(d, n1, traj, every, s);
+    case 2: return go_traj<2>(d, n1, traj, every, s);
+    case 4: return go_traj<4>(d, n1, traj, every, s);
+    case 8: return go_traj<8>(d, n1, traj, every, s);
+    case 16: return go_traj<16>(d, n1, traj, every, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace wake

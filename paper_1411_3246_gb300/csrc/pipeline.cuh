@@ -65,6 +65,7 @@ struct PipeHooks {
   using R = typename Pol::R;
   using G = typename Pol::G;
   using BT = R;
+  static constexpr bool kTraj = false;
   const PipeArgs &a;
   int t;          // step within the launch
   R *win;         // 4 slices x (E_r, E_z, B_theta) x n1
@@ -266,8 +267,15 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(PipeArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int n1 = a.d.nr + 1;
   const size_t base = (MarchSmem<Pol>::bytes(n1, NT * PPT) + 63) & ~(size_t)63;
-  R *win = (R *)(smem_raw + base);
-  int *ctl = (int *)(win + (size_t)12 * n1);
+  R *win;
+  int *ctl;
+  if constexpr (Pol::kWinGlobal) {  // the field window in this CTA's global buffer
+    win = (R *)((unsigned char *)a.win_bufs + (size_t)blockIdx.x * a.win_stride);
+    ctl = (int *)(smem_raw + base);
+  } else {
+    win = (R *)(smem_raw + base);
+    ctl = (int *)(win + (size_t)12 * n1);
+  }
   for (int t = blockIdx.x; t < a.nsteps; t += gridDim.x) {
     if (threadIdx.x == 0) {
       ctl[0] = 0;
@@ -349,7 +357,10 @@ __global__ void __launch_bounds__(NT, (NT < 512 ? 512 / NT : 1)) batch_step_kern
 
 template <class Pol, int NT, int PPT>
 size_t step_smem_bytes(int n1) {
-  return ((MarchSmem<Pol>::bytes(n1, NT * PPT) + 63) & ~(size_t)63) + sizeof(typename Pol::R) * 12 * (size_t)n1 + 64;
+  return ((MarchSmem<Pol>::bytes(n1, NT * PPT) + 63) & ~(size_t)63) +
+         (Pol::kWinGlobal ? 0 : sizeof(typename Pol::R) * 12 * (size_t)n1) + 64;
 }
+// Global field-window bytes per CTA of the pipelined step (kWinGlobal forms).
+inline size_t step_window_bytes(int n1) { return ((sizeof(float) * 12 * (size_t)n1 + 255) / 256) * 256; }
 
 }  // namespace wake

@@ -69,7 +69,7 @@ size_t gsize(int precision) { return precision == WAKE_FP64 ? sizeof(double) : s
 // Global ring storage a simulation's march needs: FP64 form and wide form only.
 size_t sim_ring_bytes(int precision, const Sim &s) {
   if (s.wide) return wide_ring_bytes(s.np);
-  return ring_buf_bytes(precision == WAKE_FP64);
+  return ring_buf_bytes(precision);
 }
 
 // x-extent of a batched launch (blockIdx.y is the simulation): up to 64 blocks of 256 per
@@ -118,6 +118,8 @@ struct wake_sim {
   cudaGraphExec_t step_graph = nullptr;  // one batched step, captured at the first wake_step
   bool batch_pipeline = true;             // WAKE_BATCH_PIPELINE=0: batched steps by the graph
   int batch_nt = 256;                     // threads per CTA of the pipelined batch (256 or 512)
+  long long spin_limit = 1LL << 24;       // polls of >= 128 ns before a pipelined wait gives up
+                                          // (WAKE_SPIN_LIMIT)
   int step_form = 0;                      // one simulation's pipelined steps: 0 tile (or wide 512 when
                                           // no tile fits), 256 / 512 wide form (WAKE_STEP_FORM)
   void *bp_rings = nullptr, *bp_sims = nullptr, *bp_items = nullptr;  // pipelined batch scratch
@@ -137,13 +139,15 @@ void free_sim(Sim &s) {
 }
 
 int check_params(const wake_params &p, int prec0) {
-  if (p.precision != WAKE_FP64 && p.precision != WAKE_MIXED) return fail(WAKE_EINVAL, "precision must be WAKE_FP64 or WAKE_MIXED");
+  if (p.precision != WAKE_FP64 && p.precision != WAKE_MIXED && p.precision != WAKE_MIXED64)
+    return fail(WAKE_EINVAL, "precision must be WAKE_FP64, WAKE_MIXED or WAKE_MIXED64");
   if (p.precision != prec0) return fail(WAKE_EINVAL, "all simulations of one handle must share the precision");
-  const bool fp64 = p.precision == WAKE_FP64;
-  if (p.nr < 2 || p.nr > (fp64 ? 1024 : 2048)) return fail(WAKE_EINVAL, "nr must be in [2, 1024] (FP64) or [2, 2048] (mixed)");
+  const bool fp64 = p.precision != WAKE_MIXED;  // the FP64 and FP64-solve forms share the limits
+  if (p.nr < 2 || p.nr > (fp64 ? 1024 : 2048))
+    return fail(WAKE_EINVAL, "nr must be in [2, 1024] (FP64, FP64-solve) or [2, 2048] (mixed)");
   if (p.nxi < 2 || p.nxi > (1 << 20)) return fail(WAKE_EINVAL, "nxi must be in [2, 2^20]");
   if (p.ppc < 1 || (int64_t)p.nr * p.ppc > (fp64 ? 8192 : 65536))
-    return fail(WAKE_EINVAL, "need ppc >= 1 and nr*ppc <= 8192 (FP64) or 65536 (mixed)");
+    return fail(WAKE_EINVAL, "need ppc >= 1 and nr*ppc <= 8192 (FP64, FP64-solve) or 65536 (mixed)");
   if (p.u_th < 0.0 || (p.u_th > 0.0 && p.ppc % 2)) return fail(WAKE_EINVAL, "a warm plasma needs u_th > 0 and an even ppc");
   if (!(p.rmax > 0.0) || !(p.ximax > 0.0)) return fail(WAKE_EINVAL, "rmax and ximax must be positive");
   if (p.n_beam < 0 || p.n_drive < 0 || p.n_drive > p.n_beam) return fail(WAKE_EINVAL, "need 0 <= n_drive <= n_beam");
@@ -211,12 +215,12 @@ std::vector<TileFns> tile_candidates(const wake_sim *h, const Sim &s) {
   std::vector<TileFns> out;
   const int n1 = s.p.nr + 1;
   for (int nt : {128, 256, 512}) {
-    if (h->precision == WAKE_FP64 && nt != 512) continue;
+    if (h->precision != WAKE_MIXED && nt != 512) continue;
     if (h->tile_nt_forced && nt != h->tile_nt_forced) continue;  // -1: the wide form only
     if (n1 > 3 * nt) continue;
     const int ppt = pow2_at_least((s.np + nt - 1) / nt);
     TileFns f;
-    if (!march_tile(h->precision == WAKE_FP64, nt, ppt, &f)) continue;
+    if (!march_tile(h->precision, nt, ppt, &f)) continue;
     if (f.smem(n1) > kMaxSmemPerCta) continue;
     out.push_back(f);
   }
@@ -395,6 +399,7 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
   if (const char *t = std::getenv("WAKE_BATCH_PIPELINE")) h->batch_pipeline = std::atoi(t) != 0;
   if (const char *t = std::getenv("WAKE_BATCH_NT")) h->batch_nt = std::atoi(t) == 512 ? 512 : 256;
   if (const char *t = std::getenv("WAKE_STEP_FORM")) h->step_form = std::atoi(t);
+  if (const char *t = std::getenv("WAKE_SPIN_LIMIT")) h->spin_limit = std::max(0LL, std::atoll(t));
   const size_t gs = gsize(h->precision);
   int rc = WAKE_OK;
   for (int i = 0; i < n_sims && rc == WAKE_OK; ++i) {
@@ -620,6 +625,26 @@ int wake_plasma_march(wake_sim *h) {
   int rc = launch_march(h);
   if (rc) return rc;
   for (auto &s : h->sims) s.marched = true;
+  return WAKE_OK;
+}
+
+int wake_plasma_march_traj(wake_sim *h, int sim, int every, double *traj) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  if (every < 1 || !traj) return fail(WAKE_EINVAL, "wake_plasma_march_traj: every >= 1 and a trajectory buffer are needed");
+  Sim &s = h->sims[sim];
+  if (!s.plasma) return fail(WAKE_ESTATE, "wake_plasma_march_traj before wake_load_plasma");
+  const int n1 = s.p.nr + 1;
+  if (h->precision == WAKE_MIXED64) return fail(WAKE_EINVAL, "wake_plasma_march_traj: FP64 and mixed forms only");
+  const bool fp64 = h->precision == WAKE_FP64;
+  const size_t smem = fp64 ? march_traj_smem_fp64(n1, s.np) : march_traj_smem_mixed(n1, s.np);
+  if (s.wide || smem > kMaxSmemPerCta)
+    return fail(WAKE_EINVAL, "wake_plasma_march_traj: the simulation does not fit one 512-thread march CTA "
+                             "(nr + 1 <= 1536 nodes and its rings in shared memory)");
+  const cudaError_t e = fp64 ? launch_march_traj_fp64(h->d_desc + sim, n1, s.np, traj, every, h->stream)
+                             : launch_march_traj_mixed(h->d_desc + sim, n1, s.np, traj, every, h->stream);
+  if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("trajectory march launch: ") + cudaGetErrorString(e));
+  s.marched = true;
   return WAKE_OK;
 }
 
@@ -869,7 +894,7 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
       a.bin_start = s.bin_start;
       a.w = b.w;
       a.ds = s.p.ds;
-      a.spin_limit = 1LL << 24;
+      a.spin_limit = h->spin_limit;
       a.defer_cnt = s.defer_cnt;
       a.defer_list = s.defer_list;
       a.defer_cap = dcap;
@@ -981,8 +1006,8 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
   CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   const int chmax = (int)std::min<size_t>(1024, std::max<size_t>(1, free_b / 4 / gbytes - 1));
   const int wnt = wide_nt;  // 0: the tiled step kernel
-  const size_t rb = wnt ? step_wide_ring_bytes(s.np, wnt) : ring_buf_bytes(fp64);
-  const size_t wb = wnt ? step_wide_window_bytes(s.p.nr + 1) : 0;
+  const size_t rb = wnt ? step_wide_ring_bytes(s.np, wnt) : ring_buf_bytes(h->precision);
+  const size_t wb = wnt ? step_wide_window_bytes(s.p.nr + 1) : step_global_window_bytes(h->precision, s.p.nr + 1);
   int rc, done = 0, last_ch = 0;
   // the lists of slipped particles: up to 16 GB (or an eighth of the free memory) for a launch
   const size_t list_budget = std::min<size_t>((size_t)16 << 30, free_b / 8);
@@ -1096,7 +1121,7 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
     a.bin_start = s.bin_start;
     a.w = bd.w;
     a.ds = s.p.ds;
-    a.spin_limit = 1LL << 24;  // polls of >= 128 ns: a wait gives up after seconds
+    a.spin_limit = h->spin_limit;  // polls of >= 128 ns: by default a wait gives up after seconds
     a.ring_bufs = s.pring;
     a.ring_stride = rb;
     a.win_bufs = wb > 0 ? (char *)s.pring + rb * ctas : nullptr;
@@ -1115,7 +1140,7 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
       h->ev.push_back(q);
     }
     CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].first, h->stream));
-    const cudaError_t e = wnt ? launch_step_wide(a, wnt, ctas, h->stream) : launch_step(fp64, a, s.np, ctas, h->stream);
+    const cudaError_t e = wnt ? launch_step_wide(a, wnt, ctas, h->stream) : launch_step(h->precision, a, s.np, ctas, h->stream);
     if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("pipelined step launch: ") + cudaGetErrorString(e));
     CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].second, h->stream));
     ++h->ev_used;
@@ -1140,7 +1165,7 @@ int wake_step(wake_sim *h, int nsteps) {
     if (!s.beam || !s.plasma) return fail(WAKE_ESTATE, "wake_step needs wake_load_plasma and wake_load_beam");
     int wnt = s.wide ? 512 : 0;
     if (h->precision == WAKE_MIXED && (h->step_form == 256 || h->step_form == 512)) wnt = h->step_form;
-    const int ctas = wnt ? step_wide_max_ctas(s.p.nr + 1, wnt) : step_max_ctas(h->precision == WAKE_FP64, s.p.nr + 1, s.np);
+    const int ctas = wnt ? step_wide_max_ctas(s.p.nr + 1, wnt) : step_max_ctas(h->precision, s.p.nr + 1, s.np);
     if (ctas > 0) return step_pipelined(h, nsteps, ctas, wnt);
   }
   if (h->n > 1) {

@@ -7,6 +7,10 @@
   as dxi shrinks; in a warm one it tends to a limit (Sec. IV, Figs. 8 and 9).
 * Propagation: the Table I beam carried over a distance in metres; the witness energy gain
   and spectrum (Sec. III, Fig. 3; Sec. IV, Fig. 7).
+* Trajectories: the plasma electrons' paths behind the driver.  Expelled electrons fall back
+  and cross the axis where the spike forms; warm electrons, with their spread of initial
+  velocities, cross it over a broader region than cold ones, and a single bunch gives a
+  narrower crossing than two (Sec. IV, Figs. 4 and 5).
 
 The callers supply the simulations' parameters and random draws (the repository's `synth`
 module makes the paper's workloads); this module runs them and reduces the results.
@@ -108,3 +112,57 @@ def propagate(cfg, plasma_normals, beam_normals, lengths_m, precision=wake.WAKE_
                          "kernel_ms": kern_ms})
         del tp, tb
     return out
+
+
+def trajectories(cfg, plasma_normals, every=1, precision=wake.WAKE_MIXED, stream=None):
+    """One march of one simulation (frozen analytic driver when it has no beam particles) with
+    the ring trajectory dump.  Returns (xi, traj): xi the dump slices' positions and traj a
+    float64 numpy array (len(xi), 3, nr * ppc) of each ring's r, u_r and Gamma there."""
+    import torch
+    nd = cfg.nxi // every + 1
+    with wake.Simulations([cfg], precision, stream) as s:
+        tp = None if plasma_normals is None else torch.from_numpy(plasma_normals).cuda()
+        out = torch.empty((nd, 3, cfg.nr * cfg.ppc), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        wake.wake_load_plasma(s.h, 0, tp)
+        wake.wake_plasma_march_traj(s.h, 0, every, out)
+        st = s.status(0)
+        traj = out.cpu().numpy()
+        del tp
+    if st != wake.WAKE_OK:
+        raise wake.WakeError(st, wake.wake_last_error())
+    xi = np.arange(nd) * every * cfg.ximax / cfg.nxi
+    return xi, traj
+
+
+def axis_crossings(r, xi, xi_after, r_cut):
+    """Per ring (columns of r, a (len(xi), n_rings) array of radii along xi): the xi of its
+    first approach to the axis behind xi_after, i.e. the first dump after xi_after where its
+    radius has a local minimum below r_cut; NaN for a ring that has none."""
+    r = np.asarray(r)
+    n_d = r.shape[0]
+    out = np.full(r.shape[1], np.nan)
+    k = np.arange(1, n_d - 1)
+    k = k[xi[k] > xi_after]
+    if k.size == 0:
+        return out
+    mins = (r[k - 1] > r[k]) & (r[k] <= r[k + 1]) & (r[k] < r_cut)
+    has = mins.any(axis=0)
+    first = np.argmax(mins, axis=0)
+    out[has] = xi[k[first[has]]]
+    return out
+
+
+def crossing_width(xi_cross, w, lo=0.1, hi=0.9):
+    """Length in xi of the axis-crossing region: the range between the lo and hi quantiles of
+    the rings' crossing points, each ring weighted by its charge w (rings without a crossing
+    left out).  Returns (width, fraction of the charge that crossed)."""
+    ok = np.isfinite(xi_cross)
+    x, ww = xi_cross[ok], np.asarray(w, dtype=np.float64)[ok]
+    if x.size == 0:
+        return float("nan"), 0.0
+    o = np.argsort(x, kind="stable")
+    x, ww = x[o], ww[o]
+    c = np.cumsum(ww) / ww.sum()
+    q = lambda f: float(x[min(np.searchsorted(c, f), x.size - 1)])  # noqa: E731
+    return q(hi) - q(lo), float(ww.sum() / np.asarray(w, dtype=np.float64).sum())

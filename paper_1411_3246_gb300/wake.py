@@ -14,11 +14,11 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libwake.so")
 
 WAKE_OK, WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENUMERIC, WAKE_ETIMEOUT, WAKE_EESCAPE, WAKE_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
-WAKE_FP64, WAKE_MIXED = 0, 1
+WAKE_FP64, WAKE_MIXED, WAKE_MIXED64 = 0, 1, 2
 
 # every entry point the header declares
 EXPORTS = ["wake_init", "wake_load_plasma", "wake_load_beam", "wake_set_beam", "wake_beam_deposit", "wake_plasma_march",
-           "wake_beam_push", "wake_step", "wake_tile", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
+           "wake_plasma_march_traj", "wake_beam_push", "wake_step", "wake_tile", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
            "wake_diagnostics", "wake_status", "wake_beam_deposit_noalloc", "wake_adjoint_init",
            "wake_adjoint_forward", "wake_adjoint_backward", "wake_adjoint_destroy", "wake_last_error", "wake_destroy"]
 WAKE_NOALLOC_MAX_NODES = 524288
@@ -56,6 +56,7 @@ def lib():
         L.wake_set_beam.argtypes = [vp, i32, vp, vp, vp]
         for n in ("wake_beam_deposit", "wake_plasma_march", "wake_beam_push"):
             getattr(L, n).argtypes = [vp]
+        L.wake_plasma_march_traj.argtypes = [vp, i32, i32, vp]
         L.wake_step.argtypes = [vp, i32]
         L.wake_step_kernel_ms.argtypes = [vp, C.POINTER(C.c_float)]
         L.wake_tile.argtypes = [vp, i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -131,6 +132,11 @@ def wake_beam_deposit(h):
 
 def wake_plasma_march(h):
     _check(lib().wake_plasma_march(h))
+
+
+def wake_plasma_march_traj(h, sim, every, traj):
+    """traj: ((nxi // every + 1), 3, nr * ppc) float64 CUDA tensor (r, u_r, Gamma per ring)."""
+    _check(lib().wake_plasma_march_traj(h, sim, every, _ptr(traj)))
 
 
 def wake_beam_push(h):

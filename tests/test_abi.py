@@ -50,3 +50,23 @@ def test_invalid_parameters_rejected_before_any_device_work(libwake):
     odd = wake.params_of(synth.config_blowout(n_beam=0, nr=32, nxi=16), wake.WAKE_FP64)
     odd.ppc = 3
     assert wake.lib().wake_init(C.byref(odd), 1, None, C.byref(h)) == wake.WAKE_EINVAL
+
+
+def test_corrupt_parameters_rejected(libwake):
+    """Non-finite or inconsistent parameters return WAKE_EINVAL from wake_init before any CUDA
+    call (runs without a GPU)."""
+    import math
+
+    import synth
+    from paper_1411_3246_gb300 import wake
+    h = C.c_void_p()
+    base = synth.config_blowout(n_beam=1024, nr=32, nxi=16)
+    for field, value in (("rmax", math.nan), ("ximax", -1.0), ("ds", math.nan), ("gamma_b", 0.5),
+                         ("sigma_r", math.nan), ("u_th", -0.1), ("n_drive", 2048), ("nxi", 1)):
+        p = wake.params_of(base, wake.WAKE_MIXED)
+        setattr(p, field, value)
+        assert wake.lib().wake_init(C.byref(p), 1, None, C.byref(h)) == wake.WAKE_EINVAL, field
+        assert not h.value
+    good = wake.params_of(base, wake.WAKE_MIXED)
+    mixed = (wake.wake_params * 2)(good, wake.params_of(base, wake.WAKE_FP64))
+    assert wake.lib().wake_init(mixed, 2, None, C.byref(h)) == wake.WAKE_EINVAL

@@ -56,3 +56,32 @@ def test_facet_config_splits_particles_by_charge():
     assert abs(n_w / cfg.n_drive - q_ratio) < 1e-5
     assert cfg.eps_n == 0.0 and abs(cfg.u_th - math.sqrt(5.0 / 511.0e3)) < 1e-15
     assert abs(cfg.gamma_b * 0.511e-3 - 23.0) < 1e-9
+
+
+def test_axis_crossings_of_constructed_trajectories():
+    """Rings whose radii dip to a known minimum at known slices: the first minimum behind
+    xi_after and below r_cut is found; a ring that stays away from the axis has none; a dip
+    ahead of xi_after does not count."""
+    xi = np.linspace(0.0, 10.0, 101)
+    r = np.empty((101, 4))
+    r[:, 0] = np.abs(xi - 6.0) + 0.0          # V-shaped crossing at xi = 6
+    r[:, 1] = np.abs(xi - 6.5) * 0.5 + 0.01   # crossing at 6.5, minimum radius 0.01
+    r[:, 2] = 2.0 + 0.1 * np.sin(xi)          # never near the axis
+    r[:, 3] = np.minimum(np.abs(xi - 1.0), np.abs(xi - 7.0))  # dips at 1 (ahead) and at 7
+    xc = studies.axis_crossings(r, xi, xi_after=3.0, r_cut=0.05)
+    assert xc[0] == xi[60] and xc[1] == xi[65] and np.isnan(xc[2]) and xc[3] == xi[70]
+
+
+def test_crossing_width_weighted_quantiles():
+    """Charge-weighted 10-90% range: uniform crossings over [2, 4] with equal weights give a
+    width of 1.6; giving all weight to one point gives 0; uncrossed rings are left out."""
+    x = np.linspace(2.0, 4.0, 2001)
+    w = np.ones_like(x)
+    width, frac = studies.crossing_width(x, w)
+    assert abs(width - 1.6) < 2e-3 and frac == 1.0
+    x2 = np.concatenate([x, [np.nan] * 2001])
+    width2, frac2 = studies.crossing_width(x2, np.ones_like(x2))
+    assert abs(width2 - 1.6) < 2e-3 and abs(frac2 - 0.5) < 1e-12
+    w3 = np.zeros_like(x)
+    w3[1000] = 1.0
+    assert studies.crossing_width(x, w3)[0] == 0.0

@@ -477,15 +477,10 @@ def osiris_leg(wake, torch, length_m, rank, flush, world):
 
 
 def adjoint_case(nsteps, rank):
-    """The differentiation workload: the linear-driver grid (Nr=128 over 6, 4 rings/cell) at
-    Nxi=1024 over 10, two bunches (witness at the batched sweep's first delay), 262,144 beam
-    particles, u_th = 0.005, a 64-bin witness profile."""
-    cfg = synth.config_batch(n_sims=1, seed=replica_seed(synth.SEED_BASE + 4, rank))[0]
-    cfg.nr, cfg.nxi, cfg.ppc = 128, 1024, 4
-    cfg = synth.two_bunch(cfg, 0.3, cfg.xi_w - cfg.xi_d, 262144)
-    cfg.u_th = 0.005
-    cfg.n_steps = nsteps
-    return cfg
+    """The differentiation workload (synth.config_adjoint): the linear-driver grid (Nr=128 over
+    6, 4 rings/cell) at Nxi=1024 over 10, two bunches, 262,144 beam particles, u_th = 0.005;
+    the bench adds a 64-bin witness profile."""
+    return synth.config_adjoint(nsteps, seed=replica_seed(synth.SEED_BASE + 4, rank))
 
 
 def adjoint_leg(wake, torch, nsteps, rank, world):

@@ -153,6 +153,18 @@ def config_batch(n_sims=256, n_steps=50, seed=SEED_BASE + 3) -> list[WakeConfig]
     return out
 
 
+def config_adjoint(n_steps=100, seed=SEED_BASE + 4) -> WakeConfig:
+    """Differentiation workload: the linear-driver grid (Nr=128 over 6, 4 particles per cell)
+    at Nxi=1024 over 10, the batched sweep's first witness delay, 262,144 beam
+    macroparticles split by charge, u_th = 0.005, n_steps beam steps of 5."""
+    cfg = config_batch(n_sims=1, seed=seed)[0]
+    cfg.nr, cfg.nxi, cfg.ppc = 128, 1024, 4
+    cfg = two_bunch(cfg, 0.3, cfg.xi_w - cfg.xi_d, 262144)
+    cfg.u_th = 0.005
+    cfg.n_steps = n_steps
+    return cfg
+
+
 def plasma_normals(cfg: WakeConfig) -> np.ndarray | None:
     """Standard normals for the warm-plasma momenta, shape (np_plasma, 3) holding
     (u_r, u_theta, u_z) draws, mirrored in pairs.  None for a cold plasma."""

@@ -80,3 +80,43 @@ def test_autograd_function_gives_the_adjoint_gradient(wk):
     got = np.concatenate([th.grad.cpu().numpy(), pr.grad.cpu().numpy()])
     np.testing.assert_allclose(got, g, rtol=1e-12)
     assert_grad_close(got, fd)
+
+
+def test_adjoint_bench_size_against_oracle(wk):
+    """The differentiation workload the benchmark times (128 x 1024, 262,144 beam particles,
+    100 steps, 64 profile bins): the forward observables against the oracle's to 1e-9, and
+    gradient components against central differences of the oracle (h = 1e-4 relative; the
+    oracle runs in worker processes).  The mean-gain components to 5e-3 (their differences at
+    h = 1e-3 and 1e-4 agree to 1e-3 at worst, a profile bin's).  The spread is
+    piecewise smooth only (the linear hats' kinks under a quarter million particles):
+    differences at h = 1e-3, 1e-4 and 1e-5 of its n_w component spread by 1.3%, so its
+    components are held to 3e-2.  The u_th components are not compared here: there every ring
+    moves, and the difference quotients at those three h disagree by a factor of six."""
+    import oracle_jobs
+    cfg = synth.config_adjoint()
+    nsteps, nbins = cfg.n_steps, 64
+    theta, prof = theta_of(cfg), np.ones(nbins)
+    x0 = np.concatenate([theta, prof])
+    comps = [0, 1, 4 + 20, 4 + 32]  # n_w, delay and two profile bins
+    jobs = [(x0[:4], x0[4:])]
+    steps = []
+    for i in comps:
+        h = 1e-4 * max(abs(x0[i]), 1e-3)
+        steps.append(h)
+        for sgn in (1.0, -1.0):
+            x = x0.copy()
+            x[i] += sgn * h
+            jobs.append((x[:4], x[4:]))
+    with oracle_jobs.pool(len(jobs)) as pool:
+        res = [pool.apply_async(oracle_jobs.witness_objective, (cfg, th, pr, nsteps)) for th, pr in jobs]
+        with _adj(wk, cfg, nsteps, nbins) as a:
+            obs = np.array(a.forward(theta, prof))
+            g_mean = np.array(a.backward([1.0, 0.0]))
+            g_spread = np.array(a.backward([0.0, 1.0]))
+        vals = [np.array(r.get(timeout=1800)) for r in res]
+    np.testing.assert_allclose(obs, vals[0], rtol=1e-9)
+    for n, (i, h) in enumerate(zip(comps, steps)):
+        fd = (vals[1 + 2 * n] - vals[2 + 2 * n]) / (2 * h)
+        print(f"component {i}: adjoint {g_mean[i]:.6g}, {g_spread[i]:.6g}; oracle differences {fd[0]:.6g}, {fd[1]:.6g}")
+        assert abs(g_mean[i] - fd[0]) <= 5e-3 * abs(fd[0]), (i, g_mean[i], fd[0])
+        assert abs(g_spread[i] - fd[1]) <= 3e-2 * abs(fd[1]), (i, g_spread[i], fd[1])

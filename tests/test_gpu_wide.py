@@ -113,3 +113,41 @@ def test_wide_form_pipelined_matches_separate_steps(wk, monkeypatch):
     assert np.abs(ea - eb).max() <= 2e-3 * np.abs(eb).max()
     g0 = cfg.gamma_b
     assert abs((da[1] - g0) - (db[1] - g0)) <= 1e-3 * abs(db[1] - g0)
+
+
+def test_large_configuration_full_size_one_step(wk):
+    """The large configuration at full size (Nr=2048 over 10, Nxi=8192 over 16, 65,536 rings
+    per slice at u_th=0.02, 2^24 beam particles): one beam step (deposit, march, push) by the
+    pipelined path the benchmark times, against the oracle's (about a minute of one host core,
+    in a worker process).  Peak on-axis E_z within 1%, the fields of the whole box within 1% of
+    it (a long warm box: ~1e-3 is expected), the witness mean energy gain and rms spread within
+    0.5%, surviving counts equal."""
+    import torch
+
+    import oracle_jobs
+    cfg = synth.config_large()
+    assert (cfg.nr, cfg.nxi, cfg.nr * cfg.ppc, cfg.n_beam) == (2048, 8192, 65536, 1 << 24)
+    with oracle_jobs.pool(1) as pool:
+        job = pool.apply_async(oracle_jobs.run_steps, (cfg, 1))
+        with wk.Simulations([cfg], wk.WAKE_MIXED) as s:
+            wk.wake_load_plasma(s.h, 0, torch.from_numpy(synth.plasma_normals(cfg)).cuda())
+            wk.wake_load_beam(s.h, 0, torch.from_numpy(synth.beam_normals(cfg)).cuda())
+            d0 = s.diagnostics()[0]
+            wk.wake_step(s.h, 1)
+            assert wk.wake_step_kernel_ms(s.h) > 0.0  # the pipelined launch ran
+            ez = s.fields(0)["ez"].cpu().numpy()
+            d = s.diagnostics()[0]
+            assert s.status(0) == wk.WAKE_OK, wk.wake_last_error()
+        ref = job.get(timeout=1800)
+    pk_ref = np.abs(ref["ez_axis"]).max()
+    pk = np.abs(ez[:, 0]).max()
+    node = np.abs(ez - ref["ez"]).max() / pk_ref
+    gain, g_ref = d[1] - d0[1], ref["d"][1] - ref["d0"][1]
+    print(f"large, one step: peak E_z {pk:.6f} vs {pk_ref:.6f}; node error / peak {node:.2e}; witness gain "
+          f"{gain:.5f} vs {g_ref:.5f}, spread {d[2]:.5f} vs {ref['d'][2]:.5f}")
+    assert abs(pk - pk_ref) <= 0.01 * pk_ref
+    assert node <= 0.01
+    assert d[0] == ref["d"][0] and d[3] == ref["d"][3]
+    assert abs(g_ref) > 0.5
+    assert abs(gain - g_ref) <= 0.005 * abs(g_ref)
+    assert abs(d[2] - ref["d"][2]) <= 0.005 * ref["d"][2]

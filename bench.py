@@ -502,12 +502,30 @@ def adjoint_leg(wake, torch, nsteps, rank, world):
     fwd = barrier_max(t1 - t0, world)
     bwd = barrier_max(t2 - t1, world)
     pushes = cfg.nr * cfg.ppc * (cfg.nxi + 1) * nsteps
+    # the library's plain FP64 path on the same workload (wake_step, pipelined), for comparison
+    sim = wake.Simulations([cfg], wake.WAKE_FP64)
+    wake.wake_load_plasma(sim.h, 0, nm_p)
+    wake.wake_load_beam(sim.h, 0, nm_b)
+    wake.wake_step(sim.h, 1)
+    wake.wake_load_beam(sim.h, 0, nm_b)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    wake.wake_step(sim.h, nsteps)
+    torch.cuda.synchronize()
+    t4 = time.perf_counter()
+    sim.close()
+    plain = barrier_max(t4 - t3, world)
     return {"adjoint_over_forward": bwd / fwd, "forward_s": fwd, "backward_s": bwd,
-            "forward_plasma_pushes_per_s": world * pushes / fwd, "dtype": "f64",
+            "forward_plasma_pushes_per_s": world * pushes / fwd,
+            "fp64_step_plasma_pushes_per_s": world * pushes / plain, "fp64_step_s": plain, "dtype": "f64",
             "workload": f"Nr={cfg.nr} x Nxi={cfg.nxi}, {cfg.ppc} rings/cell, {cfg.n_beam} beam particles, "
                         f"{nsteps} beam steps, gradients w.r.t. n_w, delay, sigma_zd, u_th and {nbins} profile bins",
             "observables": obs, "grad_scalars": g[:4],
-            "checkpoints": "ring state every round(sqrt(Nxi+1)) slices; beam, density and fields of every step"}
+            "tape": "every slice's intermediates kept by the forward when they fit a quarter of the free device "
+                    "memory (this workload: ~12.8 GB), else the ring state every round(sqrt(Nxi+1)) slices, "
+                    "recomputed by the reverse; beam, density and fields of every step",
+            "form": "pipelined: one CTA per beam step, each a few slices behind the previous (forward) or the "
+                    "next (reverse) step"}
 
 
 def main():

@@ -259,23 +259,33 @@ int wake_beam_deposit_noalloc(const wake_params *p, const double *xyz, const uin
  *   theta[3] = u_th         plasma temperature (Sec. II.A Maxwellian)
  * and nbins multipliers of the witness current profile: witness macroparticle j carries
  * weight n_w-bunch weight x profile[b], b its bin of xi_w +- 3 sigma_zw (from its initial
- * draw).  FP64 throughout; the march is plain (no tiles, one CTA) and is reversed with
- * checkpoints every ~sqrt(Nxi + 1) slices.  The paper differentiates nothing: this form
- * serves the parameter studies of its Sec. IV.
+ * draw).  FP64 throughout.  The paper differentiates nothing: this form serves the parameter
+ * studies of its Sec. IV.
+ * The beam steps run pipelined (unless WAKE_ADJOINT_PIPELINE=0, or a beam slips fast enough to
+ * cross a xi cell within the run, or fewer than two steps fit): one CTA marches each step, a
+ * few slices behind the step before, pushing each xi cell of the beam as soon as its fields
+ * are solved; the reverse runs the same way in -xi, each step a few slices behind the step
+ * after it.  The reverse needs every slice's intermediates: the forward keeps them all when
+ * they take at most a quarter of the free device memory at wake_adjoint_init (about
+ * nsteps x (Nxi + 1) x (2 x 13 (Nr + 1) + 23 Np) x 8 bytes; WAKE_ADJOINT_FULL_TAPE=0 declines),
+ * else it keeps the ring state every ~sqrt(Nxi + 1) slices and the reverse recomputes each
+ * block from it.  The waits are bounded (WAKE_SPIN_LIMIT polls of >= 128 ns; a wait that gives
+ * up returns WAKE_ETIMEOUT).
  *
  * wake_adjoint_init: p gives the grid, box, bunches (n_d, sigma_r, sigma_zw, xi_d, gamma_b,
  * eps_n, ds, n_beam, n_drive; the theta entries of p are ignored).  Needs nr <= 256, an even
  * ppc, 0 < n_drive < n_beam, 0 <= nbins <= 1024.  Allocates everything (beam states, densities
  * and fields of every step: about (nsteps + 1) x 49 x n_beam + nsteps x 32 x (Nxi+1)(Nr+1)
- * bytes).
+ * bytes, plus the tape above and per-CTA scratch).
  * wake_adjoint_forward: theta (host, 4), profile (host, nbins; NULL if nbins == 0),
  * plasma_normals (device, nr*ppc*3 mirrored pairs as wake_load_plasma takes them) and
  * beam_normals (device, 5 x n_beam as wake_load_beam takes them; both must stay valid until
  * the next forward) -> obs (host, 2): mean gain, rms spread.  Synchronous.
  * wake_adjoint_backward: dobs (host, 2) = dL/dobs -> grad (host, 4 + nbins) = dL/dtheta,
  * dL/dprofile, for the last forward.  Synchronous.
- * Errors: WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENUMERIC, WAKE_EESCAPE, WAKE_ESTATE (no
- * surviving witness, or backward before forward).
+ * Errors: WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENUMERIC, WAKE_EESCAPE, WAKE_ETIMEOUT,
+ * WAKE_ESTATE (no surviving witness, backward before forward, or a beam particle that slipped
+ * more than one xi cell during a pipelined run).
  */
 typedef struct wake_adj wake_adj;
 int wake_adjoint_init(const wake_params *p, int nsteps, int nbins, void *stream, wake_adj **out);

@@ -33,6 +33,23 @@ struct Par {
 // v is finite (not NaN or infinite): v - v is 0 exactly then.
 ADJ_HD inline bool finite(double v) { return v - v == 0.0; }
 
+// A load of a value another CTA may have written in the same launch (the pipelined steps):
+// from L2 on the device (never a stale L1 line), a plain load on the host.
+ADJ_HD inline double rd(const double *p) {
+#ifdef __CUDA_ARCH__
+  return __ldcg(p);
+#else
+  return *p;
+#endif
+}
+ADJ_HD inline uint8_t rd(const uint8_t *p) {
+#ifdef __CUDA_ARCH__
+  return __ldcg(p);
+#else
+  return *p;
+#endif
+}
+
 ADJ_HD inline void add_to(double *p, double v) {
 #ifdef __CUDA_ARCH__
   atomicAdd(p, v);
@@ -814,14 +831,26 @@ ADJ_HD inline SliceTape slice_tape(double *base, int s, int n1, int np) {
   return t;
 }
 
+// No-op hooks of the march bodies (the sequential form and the host build).
+struct NoHook {
+  template <class... A>
+  ADJ_HD bool operator()(A &&...) const {
+    return true;
+  }
+};
+
 // Forward slices k0 .. k1-1 starting from the state in T[0].R1 (r, u_r), each slice's
 // intermediates in tape slot k - k0 when keep, else all in slot 0.  Writes the stage-1 output
-// fields when a.ez is set and checkpoints when ckpt_out.
-ADJ_HD inline void march_slices(const Par &P, const MarchArgs &a, Work &W, int k0, int k1, bool keep, bool outputs,
-                             bool ckpt_out, int *bad) {
+// fields when a.ez is set and checkpoints when ckpt_out.  before(k) runs at the start of
+// slice k (false: stop, block-uniform), after(k) once slice k's output fields are written.
+// Returns false if before() stopped the march.
+template <class Before = NoHook, class After = NoHook>
+ADJ_HD inline bool march_slices(const Par &P, const MarchArgs &a, Work &W, int k0, int k1, bool keep, bool outputs,
+                                bool ckpt_out, int *bad, Before &&before = Before(), After &&after = After()) {
   const Dims &g = a.g;
   const int n1 = g.nr + 1, np = g.np;
   for (int k = k0; k < k1; ++k) {
+    if (!before(k)) return false;
     const int s = keep ? k - k0 : 0;
     SliceTape T = slice_tape(a.tape, s, n1, np);
     if (ckpt_out && k % a.B == 0) {
@@ -842,6 +871,7 @@ ADJ_HD inline void march_slices(const Par &P, const MarchArgs &a, Work &W, int k
         a.er[(size_t)k * n1 + i] = i > 0 ? T.S1.bth[i] - T.S1.dpsi[i] : 0.0;
       }
     P.sync();
+    after(k);
     if (k == g.nxi) break;
     midpoint(P, g, T.R1, T.M, T.R2, bad);
     for (int i = P.tid; i < n1; i += P.nt) a.nbh[i] = 0.5 * (a.nb[(size_t)k * n1 + i] + a.nb[(size_t)(k + 1) * n1 + i]);
@@ -863,18 +893,23 @@ ADJ_HD inline void march_slices(const Par &P, const MarchArgs &a, Work &W, int k
     }
     P.sync();
   }
+  return true;
 }
 
 // Forward march of one beam step: fields of every slice to a.ez/a.er/a.bth, checkpoints of
-// the ring state every a.B slices.  W is the caller's scratch (Work::kCount x n1).
-ADJ_HD inline void march_forward_body(const Par &P, const MarchArgs &a, Work &W, int *bad) {
+// the ring state every a.B slices, or (full_tape) every slice's intermediates on the tape,
+// a.tape then holding Nxi + 1 slices.  W is the caller's scratch (Work::kCount x n1).  Hooks as
+// march_slices; returns false if before() stopped the march.
+template <class Before = NoHook, class After = NoHook>
+ADJ_HD inline bool march_forward_body(const Par &P, const MarchArgs &a, Work &W, int *bad, Before &&before = Before(),
+                                      After &&after = After(), bool full_tape = false) {
   SliceTape T = slice_tape(a.tape, 0, a.g.nr + 1, a.g.np);
   for (int j = P.tid; j < a.g.np; j += P.nt) {
     T.R1.r[j] = a.r0[j];
     T.R1.ur[j] = a.ur0[j];
   }
   P.sync();
-  march_slices(P, a, W, 0, a.g.nxi + 1, false, true, true, bad);
+  return march_slices(P, a, W, 0, a.g.nxi + 1, full_tape, true, !full_tape, bad, before, after);
 }
 
 // Per-ring adjoint scratch rows in a.lring.
@@ -886,8 +921,18 @@ enum {
 // Reverse march of one beam step (the adjoints of its output fields in a.lez/a.ler/a.lbth):
 // block by block from the last, each recomputed from its checkpoint with its intermediates on
 // the tape, then reversed slice by slice.  Adds the beam-density adjoint to a.lnb and the
-// ring-constant adjoints to a.lG0, a.lw, a.ll, a.lur0, a.lrho0.
-ADJ_HD inline void march_reverse_body(const Par &P, const MarchArgs &a, Work &W, int *bad) {
+// ring-constant adjoints to a.lG0, a.lw, a.ll, a.lur0, a.lrho0.  pre(k) runs before slice k
+// is reversed (false: stop, block-uniform; the field adjoints of slice k must be complete
+// when it returns true), post(k) once it is (rows >= k + 1 of a.lnb are then final).  Returns
+// false if pre() stopped it.  With a second tape buffer tape2, pre(k, idle) is also given
+// idle(): a block-uniform call that recomputes the block below into the other buffer (once;
+// it returns false when there is nothing left to do), for a pre() that would otherwise wait;
+// without one, or if idle() was not called, the block below is recomputed after the current
+// one is reversed.  full_tape: the forward kept every slice on a.tape (march_forward_body's
+// full_tape); nothing is recomputed.
+template <class Pre = NoHook, class Post = NoHook>
+ADJ_HD inline bool march_reverse_body(const Par &P, const MarchArgs &a, Work &W, int *bad, Pre &&pre = Pre(),
+                                      Post &&post = Post(), double *tape2 = nullptr, bool full_tape = false) {
   const Dims &g = a.g;
   const int n1 = g.nr + 1, np = g.np;
   double *L[LR_ZERO + 1];
@@ -897,20 +942,37 @@ ADJ_HD inline void march_reverse_body(const Par &P, const MarchArgs &a, Work &W,
     L[LR_ZERO][j] = 0.0;
   }
   P.sync();
-  for (int blk = a.nblk - 1; blk >= 0; --blk) {
+  double *bufs[2] = {a.tape, tape2 ? tape2 : a.tape};
+  // recompute block blk from its checkpoint into tape buffer buf
+  auto recompute = [&](int blk, double *buf) {
     const int k0 = blk * a.B, k1 = k0 + a.B < g.nxi + 1 ? k0 + a.B : g.nxi + 1;
-    {
-      SliceTape T0 = slice_tape(a.tape, 0, n1, np);
-      const double *ck = a.ckpt + (size_t)blk * 2 * np;
-      for (int j = P.tid; j < np; j += P.nt) {
-        T0.R1.r[j] = ck[j];
-        T0.R1.ur[j] = ck[np + j];
-      }
-      P.sync();
+    MarchArgs ab = a;
+    ab.tape = buf;
+    SliceTape T0 = slice_tape(buf, 0, n1, np);
+    const double *ck = a.ckpt + (size_t)blk * 2 * np;
+    for (int j = P.tid; j < np; j += P.nt) {
+      T0.R1.r[j] = ck[j];
+      T0.R1.ur[j] = ck[np + j];
     }
-    march_slices(P, a, W, k0, k1, true, false, false, bad);
+    P.sync();
+    march_slices(P, ab, W, k0, k1, true, false, false, bad);
+  };
+  int cur = 0;
+  const int nblk = full_tape ? 1 : a.nblk;
+  if (!full_tape) recompute(a.nblk - 1, bufs[cur]);
+  for (int blk = nblk - 1; blk >= 0; --blk) {
+    const int k0 = full_tape ? 0 : blk * a.B;
+    const int k1 = full_tape ? g.nxi + 1 : (k0 + a.B < g.nxi + 1 ? k0 + a.B : g.nxi + 1);
+    bool below_done = false;
+    auto idle = [&]() -> bool {
+      if (blk == 0 || below_done || !tape2) return false;
+      recompute(blk - 1, bufs[cur ^ 1]);
+      below_done = true;
+      return true;
+    };
     for (int k = k1 - 1; k >= k0; --k) {
-      SliceTape T = slice_tape(a.tape, k - k0, n1, np);
+      if (!pre(k, idle)) return false;
+      SliceTape T = slice_tape(bufs[cur], k - k0, n1, np);
       for (int j = P.tid; j < np; j += P.nt) L[LR_LR][j] = L[LR_LUR][j] = L[LR_LUT][j] = 0.0;
       P.sync();
       const double *lG1 = L[LR_ZERO], *lF1 = L[LR_ZERO];
@@ -947,11 +1009,17 @@ ADJ_HD inline void march_reverse_body(const Par &P, const MarchArgs &a, Work &W,
         L[LR_LURN][j] = L[LR_LUR][j];
       }
       P.sync();
+      post(k);
+    }
+    if (blk > 0) {
+      if (!below_done) recompute(blk - 1, bufs[cur ^ 1]);
+      cur ^= 1;
     }
   }
   // slice 0 starts from (r0, u_r0): r0 is fixed, u_r0 = u_th n_r
   for (int j = P.tid; j < np; j += P.nt) a.lur0[j] += L[LR_LURN][j];
   P.sync();
+  return true;
 }
 
 
@@ -1039,8 +1107,8 @@ ADJ_HD inline void gather3(const BoundsRZ &b, const double *er, const double *ez
 // Particle j from state s0 to s1: gather, Boris step, lost check.
 ADJ_HD inline void push_one(const BeamConst &c, const Beam &s0, Beam s1, const double *er, const double *ez,
                             const double *bt, int64_t j) {
-  double x = s0.x[j], y = s0.y[j], ux = s0.ux[j], uy = s0.uy[j], uz = s0.uz[j], xi = s0.xi[j];
-  uint8_t lost = s0.lost[j];
+  double x = rd(s0.x + j), y = rd(s0.y + j), ux = rd(s0.ux + j), uy = rd(s0.uy + j), uz = rd(s0.uz + j), xi = rd(s0.xi + j);
+  uint8_t lost = rd(s0.lost + j);
   if (!lost) {
     int cr, k;
     double f, gx, Er, Ez, Bt;
@@ -1102,7 +1170,8 @@ ADJ_HD inline void push_reverse_one(const BeamConst &c, const Beam &s0, const do
   double f, gx, Er, Ez, Bt;
   cell_rz(c.b, r, xi, cr, f, k, gx);
   gather3(c.b, er, ez, bt, cr, f, k, gx, Er, Ez, Bt);
-  double lx = lam.x[j], ly = lam.y[j], lux = lam.ux[j], luy = lam.uy[j], luz = lam.uz[j], lxi = lam.xi[j];
+  double lx = rd(lam.x + j), ly = rd(lam.y + j), lux = rd(lam.ux + j), luy = rd(lam.uy + j), luz = rd(lam.uz + j),
+         lxi = rd(lam.xi + j);
   double lEr = 0.0, lEz = 0.0, lBt = 0.0;
   boris_reverse(x, y, s0.ux[j], s0.uy[j], s0.uz[j], Er, Ez, Bt, c.dt, lx, ly, lux, luy, luz, lxi, lEr, lEz, lBt);
   const size_t i0 = (size_t)k * n1 + cr;
@@ -1155,14 +1224,31 @@ ADJ_HD inline void deposit_reverse_one(const BeamConst &c, const Beam &s, const 
                L10 = lnb[i0 + n1] * node_scale(c.b, k + 1, cr),
                L11 = lnb[i0 + n1 + 1] * node_scale(c.b, k + 1, cr + 1);
   const double w = wgt[j];
-  lw[j] += L00 * (1.0 - f) * (1.0 - gx) + L01 * f * (1.0 - gx) + L10 * (1.0 - f) * gx + L11 * f * gx;
+  lw[j] = rd(lw + j) + (L00 * (1.0 - f) * (1.0 - gx) + L01 * f * (1.0 - gx) + L10 * (1.0 - f) * gx + L11 * f * gx);
   const double lf = w * ((1.0 - gx) * (L01 - L00) + gx * (L11 - L10));
   const double lg = w * ((1.0 - f) * (L10 - L00) + f * (L11 - L01));
   if (r > 0.0) {
-    lam.x[j] += lf / c.b.dr * x / r;
-    lam.y[j] += lf / c.b.dr * y / r;
+    lam.x[j] = rd(lam.x + j) + lf / c.b.dr * x / r;
+    lam.y[j] = rd(lam.y + j) + lf / c.b.dr * y / r;
   }
-  lam.xi[j] += lg / c.b.dxi;
+  lam.xi[j] = rd(lam.xi + j) + lg / c.b.dxi;
+}
+
+// deposit_one with the division by the hats' volumes folded in (node_scale per node): the
+// normalised density in one pass, for the pipelined steps that deposit into the next step's
+// grid as each cell of the beam is pushed.
+ADJ_HD inline void deposit_scaled_one(const BeamConst &c, const Beam &s, const double *wgt, double *nb, int64_t j) {
+  if (s.lost[j]) return;
+  const int n1 = c.b.nr + 1;
+  int cr, k;
+  double f, gx;
+  cell_rz(c.b, sqrt(s.x[j] * s.x[j] + s.y[j] * s.y[j]), s.xi[j], cr, f, k, gx);
+  double *row = nb + (size_t)k * n1 + cr;
+  const double w = wgt[j];
+  add_to(row, w * (1.0 - f) * (1.0 - gx) * node_scale(c.b, k, cr));
+  add_to(row + 1, w * f * (1.0 - gx) * node_scale(c.b, k, cr + 1));
+  add_to(row + n1, w * (1.0 - f) * gx * node_scale(c.b, k + 1, cr));
+  add_to(row + n1 + 1, w * f * gx * node_scale(c.b, k + 1, cr + 1));
 }
 
 // Initial plasma slice, ring j (Sec. II.A, warm Maxwellian): cell c = j / ppc holds ppc/2

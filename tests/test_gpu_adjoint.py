@@ -120,3 +120,43 @@ def test_adjoint_bench_size_against_oracle(wk):
         print(f"component {i}: adjoint {g_mean[i]:.6g}, {g_spread[i]:.6g}; oracle differences {fd[0]:.6g}, {fd[1]:.6g}")
         assert abs(g_mean[i] - fd[0]) <= 5e-3 * abs(fd[0]), (i, g_mean[i], fd[0])
         assert abs(g_spread[i] - fd[1]) <= 3e-2 * abs(fd[1]), (i, g_spread[i], fd[1])
+
+
+@pytest.mark.parametrize("full_tape", ["1", "0"])
+def test_pipelined_adjoint_equals_sequential(wk, monkeypatch, full_tape):
+    """The pipelined adjoint (one CTA per beam step, many steps at once; the default), with
+    every slice kept on the tape (the default when it fits) or with checkpoints every
+    ~sqrt(Nxi) slices recomputed in the reverse (WAKE_ADJOINT_FULL_TAPE=0), against the same
+    handle run one step at a time (WAKE_ADJOINT_PIPELINE=0); both variables are read by
+    wake_adjoint_init.  The observables and the gradient agree to rounding (only the order of
+    the atomic sums differs)."""
+    cfg = adjoint_case(nr=32, nxi=128, n_beam=8192)
+    theta, prof = theta_of(cfg), np.linspace(0.8, 1.2, 8)
+    out = []
+    monkeypatch.setenv("WAKE_ADJOINT_FULL_TAPE", full_tape)
+    for pipe in ("1", "0"):
+        monkeypatch.setenv("WAKE_ADJOINT_PIPELINE", pipe)
+        with _adj(wk, cfg, 12, 8) as a:
+            o = np.array(a.forward(theta, prof))
+            g = np.array(a.backward([1.0, -0.5]))
+        out.append((o, g))
+    (o1, g1), (o0, g0) = out
+    np.testing.assert_allclose(o1, o0, rtol=1e-11)
+    assert np.abs(g1 - g0).max() <= 1e-9 * np.abs(g0).max(), (g1, g0)
+
+
+def test_adjoint_pipeline_wait_runs_out(wk, monkeypatch):
+    """WAKE_SPIN_LIMIT=0 makes each wait of the pipelined adjoint poll once: the forward
+    reports WAKE_ETIMEOUT and leaves cleanly; a fresh handle with the default limit runs."""
+    cfg = adjoint_case(nr=32, nxi=256, n_beam=4096)
+    theta, prof = theta_of(cfg), np.ones(4)
+    monkeypatch.setenv("WAKE_SPIN_LIMIT", "0")
+    with _adj(wk, cfg, 8, 4) as a:
+        with pytest.raises(wk.WakeError) as e:
+            a.forward(theta, prof)
+        assert e.value.code == wk.WAKE_ETIMEOUT
+    monkeypatch.delenv("WAKE_SPIN_LIMIT")
+    with _adj(wk, cfg, 8, 4) as a:
+        obs = np.array(a.forward(theta, prof))
+        assert np.isfinite(obs).all()
+        assert np.isfinite(np.array(a.backward([1.0, 0.0]))).all()

@@ -39,11 +39,12 @@ import numpy as np  # noqa: E402
 
 import synth  # noqa: E402
 
-# Algorithmic FP32 operations (an FMA counts 2, a divide or square root 1): per plasma push
-# (one ring advanced one slice: two field stages and two Cartesian moves), per grid node and
-# field stage (the radial solves), and per beam push (bilinear gather, Boris step, deposit
-# into the next step's grid).
-FLOP_PER_PUSH = 236.0
+# Algorithmic FP32 operations (an FMA counts 2, a divide or square root 1, a hat deposit two
+# nodes per value): per plasma push (one ring advanced one slice: stage-1 ring quantities and
+# current deposits 66, the move to the midpoint and its charge 51, stage 2 63, the full step and
+# its charge 70), per grid node and field stage (the radial solves, a Thomas-equivalent count),
+# and per beam push (bilinear gather, Boris step, deposit into the next step's grid).
+FLOP_PER_PUSH = 250.0
 FLOP_PER_NODE_STAGE = 62.0
 FLOP_PER_BEAM_PUSH = 140.0
 BEAM_STEPS = 200

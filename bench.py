@@ -398,6 +398,43 @@ def large_leg(wake, torch, nsteps, rank, flush, world):
             "form": "wide march (rings in global memory, chunks of 512 x 8 slots), pipelined", "dtype": "f32"}
 
 
+def large_fp64_leg(wake, torch, nsteps, nslices, rank, world):
+    """The plain FP64 path on the large configuration, a bounded sample: its radial grid,
+    plasma (Nr=2048, 65,536 rings per slice, u_th=0.02) and two-bunch beam over the whole box,
+    cut into nslices slices instead of 8192 (the per-slice work of the march is the same), 2^20
+    beam particles, nsteps pipelined steps after one untimed step.  The FP64 wide form keeps
+    its node arrays in global memory; the whole configuration would take hours."""
+    cfg = synth.config_large(n_beam=1 << 20)
+    cfg.seed = replica_seed(cfg.seed, rank)
+    cfg.nxi = nslices
+    stream = torch.cuda.Stream()
+    sim = wake.Simulations([cfg], wake.WAKE_FP64, stream)
+    with torch.cuda.stream(stream):
+        dp = torch.from_numpy(synth.plasma_normals(cfg)).cuda()
+        db = torch.from_numpy(synth.beam_normals(cfg)).cuda()
+        wake.wake_load_plasma(sim.h, 0, dp)
+        wake.wake_load_beam(sim.h, 0, db)
+        wake.wake_step(sim.h, 1)
+        wake.wake_load_beam(sim.h, 0, db)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        wake.wake_step(sim.h, nsteps)
+        ev[1].record(stream)
+    stream.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    st = sim.status(0)
+    sim.close()
+    if st != wake.WAKE_OK:
+        raise RuntimeError(f"large FP64 leg: simulation status {st}: {wake.wake_last_error()}")
+    pushes = plasma_pushes_per_step(cfg) * nsteps
+    t = barrier_max(ms / 1e3, world)
+    return {"value": world * pushes / t, "unit": "pushes/s", "ms_per_run": 1e3 * t, "beam_steps": nsteps,
+            "workload": f"the large configuration's radial grid, plasma (Nr={cfg.nr}, {cfg.nr * cfg.ppc} rings per "
+                        f"slice) and beam over its whole box in {nslices} slices (the configuration has 8192), 2^20 "
+                        f"beam particles, {nsteps} pipelined steps", "dtype": "f64",
+            "form": "FP64 wide march: rings and node arrays in global memory"}
+
+
 def facet_leg(wake, torch, length_m, rank, flush, world):
     """The Table I two-bunch beam (2^20 particles, zero emittance) carried length_m metres
     through a 5 eV plasma (Nr=256 over 6, Nxi=1024 over 16, 8 rings/cell): one wake_step call
@@ -547,6 +584,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=100, help="beam steps of the adjoint leg (0: skip)")
     ap.add_argument("--large-steps", type=int, default=304,
                     help="beam steps of the large-configuration leg (0: skip; the configuration has 1000)")
+    ap.add_argument("--large-fp64-steps", type=int, default=152,
+                    help="pipelined FP64 steps of the large configuration's first 256 slices (0: skip)")
     ap.add_argument("--facet-m", type=float, default=1.49,
                     help="metres the Table I beam is carried in the propagation leg (0: skip)")
     ap.add_argument("--osiris-m", type=float, default=1.4,
@@ -672,6 +711,10 @@ def main():
     if args.large_steps > 0:
         large = large_leg(wake, torch, args.large_steps, rank, flush, world)
 
+    large_fp64 = None
+    if args.large_fp64_steps > 0:
+        large_fp64 = large_fp64_leg(wake, torch, args.large_fp64_steps, 256, rank, world)
+
     # --- propagation: the Table I beam carried 1.49 m (the paper's FACET run) ---
     facet = None
     if args.facet_m > 0:
@@ -729,7 +772,7 @@ def main():
                 "e2e": {"value": world * pushes * e2e_steps / e2e_s, "unit": "pushes/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 5 * 8},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "batched": batched, "adjoint": adjoint,
-                "large": large, "facet": facet, "osiris": osiris, "latency": latency, "alu_peaks": fma,
+                "large": large, "large_fp64": large_fp64, "facet": facet, "osiris": osiris, "latency": latency, "alu_peaks": fma,
                 "host_cores": {"nproc": os.cpu_count(), "affinity": len(os.sched_getaffinity(0))},
                 "gpu_launches": KERNELS_PER_RUN * args.steps,
                 "witness": {"mean_gamma": diag[1], "rms_gamma": diag[2], "alive": diag[0]}}

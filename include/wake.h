@@ -74,10 +74,10 @@ typedef struct wake_sim wake_sim; /* opaque handle: n_sims independent simulatio
  * CUDA stream `stream` (a cudaStream_t; NULL = legacy default stream).  Allocates all
  * scratch: plasma rings, beam state, the beam-density and field grids.  A simulation with
  * n_beam == 0 gets the frozen analytic driver of Eq. 12 on its nodes.
- * Errors: WAKE_EINVAL (sizes out of range: 2 <= nxi, 1 <= ppc; FP64 and WAKE_MIXED64
- * 2 <= nr <= 1024 and nr*ppc <= 8192, WAKE_MIXED64 also within one CTA's shared memory
- * (about 4,500 rings at nr = 512); mixed 2 <= nr <= 2048 and nr*ppc <= 65536; precision
- * mismatch),
+ * Errors: WAKE_EINVAL (sizes out of range: 2 <= nxi, 1 <= ppc; FP64 and mixed 2 <= nr <= 2048
+ * and nr*ppc <= 65536 (beyond 1,024 cells or 8,192 rings the FP64 form marches in its wide
+ * form, node arrays in global memory, far slower); WAKE_MIXED64 2 <= nr <= 1024, nr*ppc <= 8192
+ * and within one CTA's shared memory (about 4,500 rings at nr = 512); precision mismatch),
  * WAKE_ENOMEM, WAKE_ECUDA.
  */
 int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out);

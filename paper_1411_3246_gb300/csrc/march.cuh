@@ -175,6 +175,24 @@ struct PolWide {
   static constexpr int kScanE = 5;
 };
 
+// The FP64 arithmetic for boxes too large for one CTA's shared memory (the wide form): rings in
+// global memory as PolWide, and the node arrays too (in FP64 they exceed shared memory at
+// 2,049 nodes), in a per-CTA global buffer the wide kernels of march_wide64.cu carve.
+struct PolWideFP64 {
+  using R = double;
+  using N = double;
+  using Acc = double;
+  using Q = double;
+  using G = double;
+  using W = double;
+  static constexpr int NT = 512;
+  static constexpr int kSortEvery = 2;
+  static constexpr bool kSmemRings = false;
+  static constexpr bool kTables = false;
+  static constexpr bool kWinGlobal = false;
+  static constexpr int kScanE = 5;
+};
+
 // Ring slot arrays: cell index, offset in the cell, u_r, the constants l_z, Gamma_0, w, and
 // the stage-1 Gamma and radial force kept for the full step; with ids, each slot also carries
 // its ring's initial index (it follows the ring through the re-sorts; the trajectory dump
@@ -730,6 +748,8 @@ template <>
 struct ChargeWin<PolWide> : ChargeWin<PolMixed> {};
 template <>
 struct ChargeWin<PolMixed64> : ChargeWin<PolMixed> {};
+template <>
+struct ChargeWin<PolWideFP64> : ChargeWin<PolFP64> {};
 
 __device__ __forceinline__ void q_atomic_add(double *p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void q_atomic_add(long long *p, long long v) {

@@ -40,6 +40,13 @@ int step_wide_max_ctas(int n1, int nt);
 size_t step_wide_window_bytes(int n1);
 size_t step_wide_ring_bytes(int np, int nt);
 cudaError_t launch_step_wide(const PipeArgs &a, int nt, int ctas, cudaStream_t stream);
+// The FP64 wide form (march_wide64.cu): its plain tile, the global bytes one simulation or
+// one pipelined CTA needs (ring slots and node arrays), and its pipelined steps.
+TileFns march_tile_wide_fp64();
+size_t wide_fp64_ring_bytes(int np, int n1);
+size_t step_wide_fp64_window_bytes(int n1);
+int step_wide_fp64_max_ctas(int n1);
+cudaError_t launch_step_wide_fp64(const PipeArgs &a, int ctas, cudaStream_t stream);
 // Pipelined steps of many simulations (pipeline.cuh batch_step_kernel), wide form.
 struct BatchArgs;
 int batch_step_max_ctas(int max_n1, int bnt);

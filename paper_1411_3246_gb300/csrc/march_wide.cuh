@@ -26,6 +26,13 @@ struct WideRings {
   }
 };
 
+// A ring's rank in its cell, kept for the scatter in a spare slot array of the ring type:
+// stored and read back as raw bits (no arithmetic, so nothing is flushed or rounded).
+__device__ __forceinline__ void rank_store(float *p, int v) { *p = __int_as_float(v); }
+__device__ __forceinline__ int rank_load(const float *p) { return __float_as_int(*p); }
+__device__ __forceinline__ void rank_store(double *p, int v) { *p = __longlong_as_double((long long)v); }
+__device__ __forceinline__ int rank_load(const double *p) { return (int)__double_as_longlong(*p); }
+
 // Re-sort the rings of a wide march by cell (counting sort through the second buffer, then
 // the buffers swap): rank r goes to chunk r / SLOTS, thread (r % SLOTS) / PPT, ring
 // (r % SLOTS) % PPT, so each thread's rings are consecutive in radius again.  Ends with a
@@ -43,7 +50,7 @@ __device__ __forceinline__ void resort_rings_wide(MarchSmem<Pol> &sm, WideRings<
     for (int p = 0; p < PPT; ++p)
       if (t * PPT + p < npc) {
         const int sl = base + p * NT + t;
-        wr.alt.G1[sl] = __int_as_float(atomicAdd(&sm.cnt[wr.s.c[sl]], 1));  // rank in its cell
+        rank_store(&wr.alt.G1[sl], atomicAdd(&sm.cnt[wr.s.c[sl]], 1));  // rank in its cell
       }
   }
   __syncthreads();
@@ -72,7 +79,7 @@ __device__ __forceinline__ void resort_rings_wide(MarchSmem<Pol> &sm, WideRings<
       if (t * PPT + p < npc) {
         const int sl = base + p * NT + t;
         const int c = wr.s.c[sl];
-        const int r = sm.cnt[c] + __float_as_int(wr.alt.G1[sl]);
+        const int r = sm.cnt[c] + rank_load(&wr.alt.G1[sl]);
         const int rr = r % SLOTS;
         const int dl = (r - rr) + (rr % PPT) * NT + rr / PPT;
         wr.alt.c[dl] = c;

@@ -68,7 +68,7 @@ size_t gsize(int precision) { return precision == WAKE_FP64 ? sizeof(double) : s
 
 // Global ring storage a simulation's march needs: FP64 form and wide form only.
 size_t sim_ring_bytes(int precision, const Sim &s) {
-  if (s.wide) return wide_ring_bytes(s.np);
+  if (s.wide) return precision == WAKE_FP64 ? wide_fp64_ring_bytes(s.np, s.p.nr + 1) : wide_ring_bytes(s.np);
   return ring_buf_bytes(precision);
 }
 
@@ -142,12 +142,12 @@ int check_params(const wake_params &p, int prec0) {
   if (p.precision != WAKE_FP64 && p.precision != WAKE_MIXED && p.precision != WAKE_MIXED64)
     return fail(WAKE_EINVAL, "precision must be WAKE_FP64, WAKE_MIXED or WAKE_MIXED64");
   if (p.precision != prec0) return fail(WAKE_EINVAL, "all simulations of one handle must share the precision");
-  const bool fp64 = p.precision != WAKE_MIXED;  // the FP64 and FP64-solve forms share the limits
-  if (p.nr < 2 || p.nr > (fp64 ? 1024 : 2048))
-    return fail(WAKE_EINVAL, "nr must be in [2, 1024] (FP64, FP64-solve) or [2, 2048] (mixed)");
+  const bool small = p.precision == WAKE_MIXED64;  // the FP64-solve split has no wide form
+  if (p.nr < 2 || p.nr > (small ? 1024 : 2048))
+    return fail(WAKE_EINVAL, "nr must be in [2, 1024] (FP64-solve) or [2, 2048] (FP64, mixed)");
   if (p.nxi < 2 || p.nxi > (1 << 20)) return fail(WAKE_EINVAL, "nxi must be in [2, 2^20]");
-  if (p.ppc < 1 || (int64_t)p.nr * p.ppc > (fp64 ? 8192 : 65536))
-    return fail(WAKE_EINVAL, "need ppc >= 1 and nr*ppc <= 8192 (FP64, FP64-solve) or 65536 (mixed)");
+  if (p.ppc < 1 || (int64_t)p.nr * p.ppc > (small ? 8192 : 65536))
+    return fail(WAKE_EINVAL, "need ppc >= 1 and nr*ppc <= 8192 (FP64-solve) or 65536 (FP64, mixed)");
   if (p.u_th < 0.0 || (p.u_th > 0.0 && p.ppc % 2)) return fail(WAKE_EINVAL, "a warm plasma needs u_th > 0 and an even ppc");
   if (!(p.rmax > 0.0) || !(p.ximax > 0.0)) return fail(WAKE_EINVAL, "rmax and ximax must be positive");
   if (p.n_beam < 0 || p.n_drive < 0 || p.n_drive > p.n_beam) return fail(WAKE_EINVAL, "need 0 <= n_drive <= n_beam");
@@ -227,6 +227,10 @@ std::vector<TileFns> tile_candidates(const wake_sim *h, const Sim &s) {
   if (out.empty() && h->precision == WAKE_MIXED && (!h->tile_nt_forced || h->tile_nt_forced == -1)) {
     const TileFns f = march_tile_wide();
     if (n1 <= 5 * f.nt && f.smem(n1) <= kMaxSmemPerCta) out.push_back(f);
+  }
+  if (out.empty() && h->precision == WAKE_FP64 && (!h->tile_nt_forced || h->tile_nt_forced == -1)) {
+    const TileFns f = march_tile_wide_fp64();  // node arrays in global memory
+    if (n1 <= 5 * f.nt) out.push_back(f);
   }
   return out;
 }
@@ -1006,8 +1010,11 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
   CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   const int chmax = (int)std::min<size_t>(1024, std::max<size_t>(1, free_b / 4 / gbytes - 1));
   const int wnt = wide_nt;  // 0: the tiled step kernel
-  const size_t rb = wnt ? step_wide_ring_bytes(s.np, wnt) : ring_buf_bytes(h->precision);
-  const size_t wb = wnt ? step_wide_window_bytes(s.p.nr + 1) : step_global_window_bytes(h->precision, s.p.nr + 1);
+  const bool wide64 = wnt && fp64;  // the FP64 wide form: node arrays in the ring buffer
+  const size_t rb = wide64 ? wide_fp64_ring_bytes(s.np, s.p.nr + 1)
+                           : (wnt ? step_wide_ring_bytes(s.np, wnt) : ring_buf_bytes(h->precision));
+  const size_t wb = wide64 ? step_wide_fp64_window_bytes(s.p.nr + 1)
+                           : (wnt ? step_wide_window_bytes(s.p.nr + 1) : step_global_window_bytes(h->precision, s.p.nr + 1));
   int rc, done = 0, last_ch = 0;
   // the lists of slipped particles: up to 16 GB (or an eighth of the free memory) for a launch
   const size_t list_budget = std::min<size_t>((size_t)16 << 30, free_b / 8);
@@ -1140,7 +1147,8 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
       h->ev.push_back(q);
     }
     CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].first, h->stream));
-    const cudaError_t e = wnt ? launch_step_wide(a, wnt, ctas, h->stream) : launch_step(h->precision, a, s.np, ctas, h->stream);
+    const cudaError_t e = wide64 ? launch_step_wide_fp64(a, ctas, h->stream)
+                                 : (wnt ? launch_step_wide(a, wnt, ctas, h->stream) : launch_step(h->precision, a, s.np, ctas, h->stream));
     if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("pipelined step launch: ") + cudaGetErrorString(e));
     CUDA_TRY(cudaEventRecord(h->ev[h->ev_used].second, h->stream));
     ++h->ev_used;
@@ -1165,7 +1173,8 @@ int wake_step(wake_sim *h, int nsteps) {
     if (!s.beam || !s.plasma) return fail(WAKE_ESTATE, "wake_step needs wake_load_plasma and wake_load_beam");
     int wnt = s.wide ? 512 : 0;
     if (h->precision == WAKE_MIXED && (h->step_form == 256 || h->step_form == 512)) wnt = h->step_form;
-    const int ctas = wnt ? step_wide_max_ctas(s.p.nr + 1, wnt) : step_max_ctas(h->precision, s.p.nr + 1, s.np);
+    const int ctas = (wnt && h->precision == WAKE_FP64) ? step_wide_fp64_max_ctas(s.p.nr + 1)
+                     : wnt ? step_wide_max_ctas(s.p.nr + 1, wnt) : step_max_ctas(h->precision, s.p.nr + 1, s.np);
     if (ctas > 0) return step_pipelined(h, nsteps, ctas, wnt);
   }
   if (h->n > 1) {

@@ -151,3 +151,47 @@ def test_large_configuration_full_size_one_step(wk):
     assert abs(g_ref) > 0.5
     assert abs(gain - g_ref) <= 0.005 * abs(g_ref)
     assert abs(d[2] - ref["d"][2]) <= 0.005 * ref["d"][2]
+
+
+def test_fp64_wide_form_linear_matches_oracle(wk, monkeypatch):
+    """The FP64 wide form (node arrays in global memory) forced on the linear case: every
+    field node to 1e-10 of peak |E_z|, as the FP64 tiles."""
+    monkeypatch.setenv("WAKE_TILE_NT", "-1")
+    cfg = synth.config_linear(nr=128, nxi=256)
+    with wk.Simulations([cfg], wk.WAKE_FP64) as s:
+        wk.wake_load_plasma(s.h, 0, None)
+        wk.wake_plasma_march(s.h)
+        got = {k: v.cpu().numpy() for k, v in s.fields(0).items()}
+        assert s.status(0) == wk.WAKE_OK, wk.wake_last_error()
+        assert wk.wake_tile(s.h, 0) == (512, 8)
+    ref = oracle.march(cfg, oracle.plasma_init(cfg, None), oracle.nb_analytic(cfg))
+    scale = np.abs(ref["ez"]).max()
+    for k in ("psi", "ez", "er", "bth"):
+        assert np.abs(got[k] - ref[k]).max() <= 1e-10 * scale, k
+
+
+def test_fp64_wide_form_large_radial_grid_steps(wk):
+    """The large configuration's radial grid and plasma (Nr=2048, 65,536 rings, u_th=0.02) on a
+    shortened box, in FP64 (the wide form, beyond the FP64 tiles): two pipelined beam steps
+    against the oracle's, fields to 1e-8 of peak and every beam coordinate to 1e-9."""
+    import torch
+    cfg = large_short(nxi=256, n_beam=1 << 16)
+    nm_p, nm_b = synth.plasma_normals(cfg), synth.beam_normals(cfg)
+    pl, bm = oracle.plasma_init(cfg, nm_p), oracle.beam_init(cfg, nm_b)
+    ref = oracle.run(cfg, pl, bm, 2)
+    with wk.Simulations([cfg], wk.WAKE_FP64) as s:
+        wk.wake_load_plasma(s.h, 0, torch.from_numpy(nm_p).cuda())
+        wk.wake_load_beam(s.h, 0, torch.from_numpy(nm_b).cuda())
+        wk.wake_step(s.h, 2)
+        assert wk.wake_step_kernel_ms(s.h) > 0.0  # pipelined
+        f = {k: v.cpu().numpy() for k, v in s.fields(0).items()}
+        xyz, lost = s.beam(0)
+        assert s.status(0) == wk.WAKE_OK, wk.wake_last_error()
+    scale = np.abs(ref["ez"]).max()
+    for k in ("psi", "ez", "er", "bth"):
+        assert np.abs(f[k] - ref[k]).max() <= 1e-8 * scale, k
+    xyz = xyz.cpu().numpy()
+    assert np.array_equal(lost.cpu().numpy(), bm["lost"])
+    keep = bm["lost"] == 0
+    for row, key in enumerate(("x", "y", "xi", "ux", "uy", "uz")):
+        assert np.abs(xyz[row][keep] - bm[key][keep]).max() <= 1e-9 * max(np.abs(bm[key][keep]).max(), 1.0), key

@@ -84,6 +84,14 @@ def lib():
                                     pd, pd, pd, pd, pd]
             L.orc_run_w.restype = i32
             L.orc_witness_obs.argtypes = [pp, pd, pd, pd, pu8, pd, pd]
+            pi32 = P(C.c_int)
+            L.orc_march_trap.argtypes = [pp, pd, pd, pd, pd, pd, pd, d, pd, pd, pd, pd, pd, pd, i32, pi32]
+            L.orc_march_trap.restype = i32
+            L.orc_beam_deposit_wt.argtypes = [pp, i64, pd, pd, pd, pu8, pd, pd]
+            pi64 = P(C.c_int64)
+            L.orc_run_trap.argtypes = [pp, i32, pd, pd, pd, pd, pd, d, i64, pi64, pd, pd, pd, pd, pd, pd, pu8,
+                                       pd, pu8, pi64, pd, pd, pd, pd]
+            L.orc_run_trap.restype = i32
             L.orc_beam_deposit_w.argtypes = [pp, pd, pd, pd, pu8, pd, pd]
             _lib = L
     return _lib
@@ -285,3 +293,51 @@ def witness_objective(cfg, theta, profile, plasma_normals, beam_normals, nsteps)
         wm[c.n_drive:] = np.asarray(profile, dtype=np.float64)[b]
     run(c, pl, bm, nsteps, wm)
     return witness_obs(c, bm, wm)
+
+
+def march_trap(cfg, plasma, nb, gamma_t, traj=False):
+    """The xi-march with trapping (Sec. I: plasma particles past a threshold become beam
+    particles): rings whose Gamma falls below gamma_t leave the plasma.  Returns the fields (and
+    trajectories if traj) and "trap", an (n, 7) array of (ring, slice, r, u_r, u_theta, Gamma,
+    weight) per promotion."""
+    p = params(cfg)
+    shape = (cfg.nxi + 1, cfg.nr + 1)
+    out = {k: np.zeros(shape) for k in ("psi", "ez", "er", "bth")}
+    nb = np.ascontiguousarray(nb, dtype=np.float64)
+    n = cfg.nr * cfg.ppc
+    tr = np.zeros((cfg.nxi + 1, 3, n)) if traj else None
+    trap = np.zeros((n, 7))
+    nt = C.c_int(0)
+    _check(lib().orc_march_trap(C.byref(p), _p(plasma["r0"]), _p(plasma["ur0"]), _p(plasma["l"]), _p(plasma["G0"]),
+                                _p(plasma["w"]), _p(nb), float(gamma_t), _p(out["psi"]), _p(out["ez"]), _p(out["er"]),
+                                _p(out["bth"]), _p(tr), _p(trap), n, C.byref(nt)), "march_trap")
+    out["trap"] = trap[:min(nt.value, n)].copy()
+    out["n_promoted"] = nt.value
+    if traj:
+        out["traj"] = tr
+    return out
+
+
+def run_trap(cfg, plasma, beam, nsteps, gamma_t, cap):
+    """nsteps beam steps with trapping (orc_run_trap): beam (oracle.beam_init's dict) grows to at
+    most cap particles.  Returns (fields of the last march, beam dict of cap entries with "wt"
+    weights and "tag" 0 drive / 1 witness / 2 promoted, particles in use, dropped promotions)."""
+    p = params(cfg)
+    n0 = cfg.n_beam
+    b = {k: np.zeros(cap) for k in ("x", "y", "xi", "ux", "uy", "uz", "wt")}
+    b["lost"] = np.ones(cap, dtype=np.uint8)
+    b["tag"] = np.zeros(cap, dtype=np.uint8)
+    for k in ("x", "y", "xi", "ux", "uy", "uz"):
+        b[k][:n0] = beam[k]
+    b["lost"][:n0] = beam["lost"]
+    wd, ww = beam_weights(cfg)
+    b["wt"][:n0] = np.where(np.arange(n0) < cfg.n_drive, wd, ww)
+    b["tag"][:n0] = np.where(np.arange(n0) < cfg.n_drive, 0, 1)
+    shape = (cfg.nxi + 1, cfg.nr + 1)
+    out = {k: np.zeros(shape) for k in ("psi", "ez", "er", "bth")}
+    n_cur, dropped = C.c_int64(n0), C.c_int64(0)
+    _check(lib().orc_run_trap(C.byref(p), nsteps, _p(plasma["r0"]), _p(plasma["ur0"]), _p(plasma["l"]),
+                              _p(plasma["G0"]), _p(plasma["w"]), float(gamma_t), cap, C.byref(n_cur),
+                              *[_p(b[k]) for k in ("x", "y", "xi", "ux", "uy", "uz", "lost", "wt", "tag")],
+                              C.byref(dropped), _p(out["psi"]), _p(out["ez"]), _p(out["er"]), _p(out["bth"])), "run_trap")
+    return out, b, n_cur.value, dropped.value

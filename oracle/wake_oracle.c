@@ -289,8 +289,14 @@ int orc_solve_slice(const orc_params *p, int np, const double *r, const double *
     psi[nr] = 0.0;
     for (int m = nr - 1; m >= 0; --m) psi[m] = psi[m + 1] - 0.5 * dr * (dpsi[m] + dpsi[m + 1]);
   }
-  /* per-ring QS quantities (Eqs. 1-3) and the current-type deposits */
+  /* per-ring QS quantities (Eqs. 1-3) and the current-type deposits; a ring of zero weight (a
+   * ring promoted to a beam particle by the trapping of orc_march_trap) takes no part */
   for (int j = 0; j < np; ++j) {
+    if (w[j] == 0.0) {
+      Gp[j] = 1.0;
+      ga[j] = 1.0;
+      continue;
+    }
     const double Gam = G0[j] + interp(psi, r[j], dr, nr);
     if (!(Gam > 0.0)) {
       status = ORC_ENUMERIC;
@@ -391,7 +397,7 @@ int orc_solve_slice(const orc_params *p, int np, const double *r, const double *
     const double dp = interp(dpsi, r[j], dr, nr);
     const double b = interp(bth, r[j], dr, nr);
     if (Gam_out) Gam_out[j] = Gp[j];
-    if (Fc_out) Fc_out[j] = (ga[j] / Gp[j]) * dp - b;
+    if (Fc_out) Fc_out[j] = w[j] == 0.0 ? 0.0 : (ga[j] / Gp[j]) * dp - b;
   }
 done:
   free(P);
@@ -440,9 +446,30 @@ void orc_deposit_charge(const orc_params *p, int np, const double *r, const doub
  * which is Eqs. 4-5 with the centrifugal term carried by the frame; afterwards
  * r = |x_perp|, u_r = x_perp . u_perp / r and u_theta = l / r.
  */
+/*
+ * orc_march with plasma-particle trapping (Sec. I: plasma particles that meet a threshold
+ * condition are promoted to beam particles, which then follow the full equations of motion).
+ * Reading (the paper cites the conditions to earlier work and gives none): a ring whose
+ * stage-1 Gamma = gamma - u_z = Gamma_0 + psi (Eq. 1) at slice k is below gamma_t moves almost
+ * with the wake (1 - v_z = Gamma/gamma) and leaves the quasi-static plasma there: it still
+ * counts in slice k's fields, then its weight drops to zero and it no longer moves.  Each
+ * promotion is recorded in trap[7 * t ..] = (ring j, slice k, r, u_r, u_theta, Gamma, w_j),
+ * at most max_trap of them (*ntrap counts all).  gamma_t <= 0: no trapping (orc_march).
+ */
+int orc_march_trap(const orc_params *p, const double *r0, const double *ur0, const double *l,
+                   const double *G0, const double *w_in, const double *nb, double gamma_t, double *psi,
+                   double *ez, double *er, double *bth, double *traj, double *trap, int max_trap,
+                   int *ntrap);
 int orc_march(const orc_params *p, const double *r0, const double *ur0, const double *l,
               const double *G0, const double *w, const double *nb, double *psi, double *ez,
               double *er, double *bth, double *traj) {
+  int nt = 0;
+  return orc_march_trap(p, r0, ur0, l, G0, w, nb, 0.0, psi, ez, er, bth, traj, NULL, 0, &nt);
+}
+int orc_march_trap(const orc_params *p, const double *r0, const double *ur0, const double *l,
+                   const double *G0, const double *w_in, const double *nb, double gamma_t, double *psi,
+                   double *ez, double *er, double *bth, double *traj, double *trap, int max_trap,
+                   int *ntrap) {
   const int nr = p->nr, nxi = p->nxi, n1 = nr + 1;
   const int np = p->nr * p->ppc;
   const double dr = p->rmax / nr, dxi = p->ximax / nxi, R = p->rmax;
@@ -464,14 +491,17 @@ int orc_march(const orc_params *p, const double *r0, const double *ur0, const do
   double *rho0 = (double *)malloc(sizeof(double) * n1);
   double *nbh = (double *)malloc(sizeof(double) * n1);
   double *sl = (double *)malloc(sizeof(double) * SL_COUNT * n1);
+  double *w = (double *)malloc(sizeof(double) * np); /* weights; zero once a ring is promoted */
+  *ntrap = 0;
   if (!r || !ur || !ut || !rh || !urh || !uth || !xh || !yh || !uxh || !uyh || !G1 || !F1 ||
-      !G2 || !F2 || !rho0 || !nbh || !sl) {
+      !G2 || !F2 || !rho0 || !nbh || !sl || !w) {
     status = ORC_ENOMEM;
     goto done;
   }
   for (int j = 0; j < np; ++j) {
     r[j] = r0[j];
     ur[j] = ur0[j];
+    w[j] = w_in[j];
   }
   orc_deposit_charge(p, np, r0, w, rho0);
 
@@ -490,10 +520,36 @@ int orc_march(const orc_params *p, const double *r0, const double *ur0, const do
         traj[((size_t)k * 3 + 1) * np + j] = ur[j];
         traj[((size_t)k * 3 + 2) * np + j] = G1[j];
       }
+    /* promotion of the rings that fell below the threshold at this slice */
+    for (int j = 0; j < np; ++j)
+      if (w[j] != 0.0 && G1[j] < gamma_t) {
+        if (*ntrap < max_trap) {
+          double *e = trap + 7 * (size_t)(*ntrap);
+          e[0] = (double)j;
+          e[1] = (double)k;
+          e[2] = r[j];
+          e[3] = ur[j];
+          e[4] = ut[j];
+          e[5] = G1[j];
+          e[6] = w[j];
+        }
+        ++*ntrap;
+        w[j] = 0.0;
+      }
     if (k == nxi) break;
 
-    /* midpoint state */
+    /* midpoint state (a promoted ring stays where it is) */
     for (int j = 0; j < np; ++j) {
+      if (w[j] == 0.0) {
+        rh[j] = r[j];
+        urh[j] = ur[j];
+        uth[j] = ut[j];
+        xh[j] = r[j];
+        yh[j] = 0.0;
+        uxh[j] = ur[j];
+        uyh[j] = ut[j];
+        continue;
+      }
       xh[j] = r[j] + 0.5 * dxi * ur[j] / G1[j];
       yh[j] = 0.5 * dxi * ut[j] / G1[j];
       uxh[j] = ur[j] + 0.5 * dxi * F1[j];
@@ -525,6 +581,7 @@ int orc_march(const orc_params *p, const double *r0, const double *ur0, const do
     if (status != ORC_OK) goto done;
     /* full step */
     for (int j = 0; j < np; ++j) {
+      if (w[j] == 0.0) continue;
       double ex = 1.0, ey = 0.0;
       const double rr = sqrt(xh[j] * xh[j] + yh[j] * yh[j]);
       if (rr > 0.0) {
@@ -567,6 +624,7 @@ done:
   free(rho0);
   free(nbh);
   free(sl);
+  free(w);
   return status;
 }
 
@@ -778,5 +836,101 @@ done:
   free(fer);
   free(fez);
   free(fbt);
+  return status;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Trapping: promoted plasma particles as beam particles (Sec. I)                         */
+/* ------------------------------------------------------------------------------------ */
+
+/* Beam density with explicit per-particle weights (charge per 2 pi), for n particles: the
+ * bilinear hats of orc_beam_deposit_w divided by the hats' volumes. */
+void orc_beam_deposit_wt(const orc_params *p, int64_t n, const double *x, const double *y,
+                         const double *xi, const uint8_t *lost, const double *wt, double *nb) {
+  const int nr = p->nr, nxi = p->nxi, n1 = nr + 1;
+  const double dr = p->rmax / nr, dxi = p->ximax / nxi;
+  memset(nb, 0, sizeof(double) * (size_t)(nxi + 1) * n1);
+  for (int64_t j = 0; j < n; ++j) {
+    if (lost[j]) continue;
+    const double r = sqrt(x[j] * x[j] + y[j] * y[j]);
+    int c, k;
+    double f, g;
+    locate(r, dr, nr, &c, &f);
+    locate(xi[j], dxi, nxi, &k, &g);
+    nb[(size_t)k * n1 + c] += wt[j] * (1 - f) * (1 - g);
+    nb[(size_t)k * n1 + c + 1] += wt[j] * f * (1 - g);
+    nb[(size_t)(k + 1) * n1 + c] += wt[j] * (1 - f) * g;
+    nb[(size_t)(k + 1) * n1 + c + 1] += wt[j] * f * g;
+  }
+  for (int k = 0; k <= nxi; ++k) {
+    const double vx = (k == 0 || k == nxi) ? 0.5 * dxi : dxi;
+    for (int i = 0; i <= nr; ++i) nb[(size_t)k * n1 + i] /= node_volume(i, nr, dr) * vx;
+  }
+}
+
+/*
+ * nsteps beam steps with trapping.  The beam has room for cap particles, *n_cur of them in
+ * use (the first p->n_beam are the bunches; tag 0 drive, 1 witness), with weights wt.  Each
+ * step: deposit the beam, march with orc_march_trap, append one beam particle per promoted ring
+ * - at (x, y) = (r, 0), xi = xi_k, momentum (u_r, u_theta, u_z) with u_z from Eqs. 2-3 for its
+ * Gamma, weight w_j ds (the ring's flux through a xi plane over one beam step), tag 2; lost if
+ * it is outside the box, dropped (counted in *n_dropped) once the beam is full - then push all
+ * particles in use (Eqs. 8-11).  The fields of the last march are left in psi, ez, er, bth.
+ */
+int orc_run_trap(const orc_params *p, int nsteps, const double *r0, const double *ur0,
+                 const double *l, const double *G0, const double *w, double gamma_t, int64_t cap,
+                 int64_t *n_cur, double *x, double *y, double *xi, double *ux, double *uy,
+                 double *uz, uint8_t *lost, double *wt, uint8_t *tag, int64_t *n_dropped,
+                 double *psi, double *ez, double *er, double *bth) {
+  const size_t ng = (size_t)(p->nxi + 1) * (p->nr + 1);
+  const int np = p->nr * p->ppc;
+  const double dxi = p->ximax / p->nxi;
+  double *nb = (double *)malloc(sizeof(double) * ng);
+  double *fer = (double *)malloc(sizeof(double) * ng);
+  double *fez = (double *)malloc(sizeof(double) * ng);
+  double *fbt = (double *)malloc(sizeof(double) * ng);
+  double *trap = (double *)malloc(sizeof(double) * 7 * (size_t)np);
+  int status = ORC_OK;
+  *n_dropped = 0;
+  if (!nb || !fer || !fez || !fbt || !trap) {
+    status = ORC_ENOMEM;
+    goto done;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    orc_beam_deposit_wt(p, *n_cur, x, y, xi, lost, wt, nb);
+    int nt = 0;
+    status = orc_march_trap(p, r0, ur0, l, G0, w, nb, gamma_t, psi, fez, fer, fbt, NULL, trap, np, &nt);
+    if (status != ORC_OK) goto done;
+    for (int t = 0; t < nt; ++t) {
+      const double *e = trap + 7 * (size_t)t;
+      if (*n_cur >= cap) {
+        ++*n_dropped;
+        continue;
+      }
+      const int64_t q = (*n_cur)++;
+      const double G = e[5], up2 = e[3] * e[3] + e[4] * e[4];
+      x[q] = e[2];
+      y[q] = 0.0;
+      xi[q] = e[1] * dxi;
+      ux[q] = e[3];
+      uy[q] = e[4];
+      uz[q] = (1.0 + up2 - G * G) / (2.0 * G); /* Eq. 3 */
+      lost[q] = !(xi[q] >= 0.0 && xi[q] < p->ximax && e[2] < p->rmax);
+      wt[q] = e[6] * p->ds;
+      tag[q] = 2;
+    }
+    orc_params pn = *p;
+    pn.n_beam = *n_cur;
+    orc_beam_push(&pn, x, y, xi, ux, uy, uz, lost, fer, fez, fbt);
+  }
+  if (ez) memcpy(ez, fez, sizeof(double) * ng);
+  if (er) memcpy(er, fer, sizeof(double) * ng);
+  if (bth) memcpy(bth, fbt, sizeof(double) * ng);
+done:
+  free(nb);
+  free(fer);
+  free(fez);
+  free(fbt);
+  free(trap);
   return status;
 }

@@ -523,3 +523,133 @@ def test_witness_obs_weighted_statistics():
     m0, s0 = oracle.witness_obs(cfg, b)
     assert abs(m0) < 1e-9 * a
     assert abs(s0 - a) < 1e-9 * a
+
+
+# ---------------------------------------------------------------------------------------
+# trapping (Sec. I: plasma particles past a threshold become beam particles)
+# ---------------------------------------------------------------------------------------
+def _trap_case():
+    cfg = synth.config_blowout(n_beam=0, nr=64, nxi=256)  # warm blowout, driver frozen
+    nm = synth.plasma_normals(cfg)
+    return cfg, oracle.plasma_init(cfg, nm), oracle.nb_analytic(cfg)
+
+
+def test_trapping_below_every_gamma_changes_nothing():
+    """A threshold below the smallest Gamma any ring reaches promotes no ring, and the fields
+    are those of the plain march, node for node."""
+    cfg, pl, nb = _trap_case()
+    plain = oracle.march(cfg, pl, nb, traj=True)
+    gmin = plain["traj"][:, 2].min()
+    out = oracle.march_trap(cfg, pl, nb, 0.99 * gmin)
+    assert len(out["trap"]) == 0
+    for k in ("psi", "ez", "er", "bth"):
+        assert np.array_equal(out[k], plain[k]), k
+
+
+def test_trapping_promotes_exactly_the_rings_below_threshold():
+    """Every promotion (ring j at slice k) is the first slice at which the ring's Gamma fell
+    below the threshold; no other ring ever fell below it; the plain march agrees with the
+    trapping march up to the first promotion, and a promoted ring stays where it was."""
+    cfg, pl, nb = _trap_case()
+    gt = 0.9
+    out = oracle.march_trap(cfg, pl, nb, gt, traj=True)
+    trap, traj = out["trap"], out["traj"]
+    assert len(trap) >= 10
+    promoted = {int(e[0]): int(e[1]) for e in trap}
+    assert len(promoted) == len(trap)  # at most once per march
+    G = traj[:, 2]
+    for j, k in promoted.items():
+        assert G[k, j] < gt and (G[:k, j] >= gt).all()
+        assert traj[k, 0, j] == trap[[int(e[0]) for e in trap].index(j), 2]
+        assert (traj[k:, 0, j] == traj[k, 0, j]).all()  # frozen from then on
+    others = [j for j in range(G.shape[1]) if j not in promoted]
+    assert (G[:, others] >= gt).all()
+    k0 = min(promoted.values())
+    plain = oracle.march(cfg, pl, nb)
+    assert np.array_equal(out["ez"][:k0 + 1], plain["ez"][:k0 + 1])
+
+
+def test_trapping_gauss_at_the_wall():
+    """Gauss's law at the wall: the enclosed charge there, R psi'(R) = R (B_theta - E_r)(R), is
+    zero while every electron is in the plasma and drops by each promoted ring's weight from the
+    slice after its promotion on (the ions it leaves behind)."""
+    cfg, pl, nb = _trap_case()
+    out = oracle.march_trap(cfg, pl, nb, 0.9)
+    R = cfg.rmax
+    flux = R * (out["bth"][:, -1] - out["er"][:, -1])
+    missing = np.zeros(cfg.nxi + 1)
+    for e in out["trap"]:
+        missing[int(e[1]) + 1:] += e[6]
+    scale = pl["w"].sum()
+    assert np.abs(flux + missing).max() <= 1e-12 * scale
+    assert missing[-1] > 0
+
+
+def test_run_with_trapping_appends_beam_particles():
+    """One beam step with trapping: every promoted ring becomes one beam particle (tag 2) at
+    its ring's radius and slice, weight w ds, with gamma and u_z on Eqs. 2-3's mass shell and
+    gamma - u_z = Gamma (Eq. 1) before its first push; the bunches are untouched by the
+    promotion, and a zero threshold reproduces orc_run."""
+    cfg = synth.config_blowout(n_beam=2048, nr=64, nxi=256)
+    nm_p, nm_b = synth.plasma_normals(cfg), synth.beam_normals(cfg)
+    pl = oracle.plasma_init(cfg, nm_p)
+    # the promotions of the first march, from the same deposit
+    bm = oracle.beam_init(cfg, nm_b)
+    march = oracle.march_trap(cfg, pl, oracle.beam_deposit(cfg, bm), 0.9)
+    cap = cfg.n_beam + 100
+    out, b, n_cur, dropped = oracle.run_trap(cfg, pl, oracle.beam_init(cfg, nm_b), 1, 0.9, cap)
+    nt = len(march["trap"])
+    assert nt > 0 and n_cur == cfg.n_beam + nt and dropped == 0
+    assert (b["tag"][cfg.n_beam:n_cur] == 2).all()
+    np.testing.assert_allclose(b["wt"][cfg.n_beam:n_cur], march["trap"][:, 6] * cfg.ds, rtol=1e-15)
+    # after their first push the promoted particles are physical (gamma >= 1); at promotion,
+    # Eq. 3's u_z for the recorded Gamma satisfies the invariant gamma - u_z = Gamma (Eq. 1)
+    up2 = b["ux"][cfg.n_beam:n_cur] ** 2 + b["uy"][cfg.n_beam:n_cur] ** 2
+    g = np.sqrt(1 + up2 + b["uz"][cfg.n_beam:n_cur] ** 2)
+    assert np.isfinite(g).all() and (g >= 1).all()
+    G = march["trap"][:, 5]
+    u2 = march["trap"][:, 3] ** 2 + march["trap"][:, 4] ** 2
+    uz0 = (1 + u2 - G * G) / (2 * G)
+    g0 = np.sqrt(1 + u2 + uz0 * uz0)
+    np.testing.assert_allclose(g0 - uz0, G, rtol=1e-12)
+    # a threshold of zero is the plain run
+    ref = oracle.run(cfg, pl, bm2 := oracle.beam_init(cfg, nm_b), 1)
+    out0, b0, n0, _ = oracle.run_trap(cfg, pl, oracle.beam_init(cfg, nm_b), 1, 0.0, cap)
+    assert n0 == cfg.n_beam
+    assert np.array_equal(out0["ez"], ref["ez"])
+    np.testing.assert_array_equal(b0["uz"][:cfg.n_beam], bm2["uz"])
+
+
+def test_trapping_above_every_gamma_promotes_each_ring_once():
+    """A threshold above every ring's Gamma promotes every ring at the first slice, each once;
+    the plasma is then empty and every later slice is the field of the uncompensated ions."""
+    cfg, pl, nb = _trap_case()
+    out = oracle.march_trap(cfg, pl, nb, 1.5)
+    trap = out["trap"]
+    assert len(trap) == cfg.nr * cfg.ppc and out["n_promoted"] == cfg.nr * cfg.ppc
+    assert sorted(trap[:, 0].astype(int)) == list(range(cfg.nr * cfg.ppc))
+    assert (trap[:, 1] == 0).all()
+
+
+def test_promoted_particles_start_from_their_rings():
+    """The particles a step appends start at their ring's radius and slice with (u_r, u_theta,
+    u_z(Gamma)) of Eqs. 2-3 and weight w ds: pushing that state once through the step's fields
+    gives the beam run_trap returns."""
+    cfg = synth.config_blowout(n_beam=2048, nr=64, nxi=256)
+    nm_p, nm_b = synth.plasma_normals(cfg), synth.beam_normals(cfg)
+    pl = oracle.plasma_init(cfg, nm_p)
+    cap = cfg.n_beam + 100
+    out, b, n_cur, _ = oracle.run_trap(cfg, pl, oracle.beam_init(cfg, nm_b), 1, 0.9, cap)
+    trap = oracle.march_trap(cfg, pl, oracle.beam_deposit(cfg, oracle.beam_init(cfg, nm_b)), 0.9)["trap"]
+    n = len(trap)
+    G, ur, ut = trap[:, 5], trap[:, 3], trap[:, 4]
+    up2 = ur * ur + ut * ut
+    uz = (1 + up2 - G * G) / (2 * G)
+    xi = trap[:, 1] * (cfg.ximax / cfg.nxi)
+    lost = ((xi < 0) | (xi >= cfg.ximax) | (trap[:, 2] >= cfg.rmax)).astype(np.uint8)
+    mine = {"x": trap[:, 2].copy(), "y": np.zeros(n), "xi": xi, "ux": ur.copy(), "uy": ut.copy(), "uz": uz,
+            "lost": lost}
+    c = synth.config_blowout(n_beam=n, nr=64, nxi=256)
+    oracle.beam_push(c, mine, out)
+    for k in ("x", "y", "xi", "ux", "uy", "uz"):
+        np.testing.assert_allclose(b[k][cfg.n_beam:n_cur], mine[k], rtol=1e-13, atol=1e-15, err_msg=k)

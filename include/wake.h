@@ -190,6 +190,37 @@ int wake_tile(wake_sim *s, int sim, int *nt, int *ppt);
  */
 int wake_step_kernel_ms(wake_sim *s, float *ms);
 
+/*
+ * Plasma-particle trapping for simulation `sim` (Sec. I: plasma particles that meet a
+ * threshold condition are promoted to beam particles, which then follow the full equations
+ * of motion, Eqs. 8-11).  The paper gives no condition; the library's reading: after the first
+ * RK2 stage of a slice, a ring whose Gamma = gamma - u_z = Gamma_0 + psi (Eq. 1) is below
+ * gamma_t moves almost with the wake (1 - v_z = Gamma / gamma) and leaves the quasi-static
+ * plasma (it still counts in that slice's fields; its weight is zero from then on).  Before
+ * the next push, each promoted ring becomes one beam particle: at (x, y) = (r, 0), xi = the
+ * slice's, momentum (u_r, u_theta, u_z) with u_z from Eqs. 2-3 for its Gamma, charge weight
+ * w ds (the ring's flux over one beam step), neither drive nor witness (wake_diagnostics
+ * leaves it out); in the field equations it is a beam particle like the bunches.  The beam's
+ * arrays get room for `capacity` promoted particles; promotions beyond it are counted and
+ * dropped.  The same plasma is marched every step, so a ring may be promoted at every step.
+ *   gamma_t   threshold (> 0; 0 keeps the arrays but promotes nothing)
+ *   capacity  promoted particles the beam can hold (>= 0)
+ * Needs a handle of one simulation with a particle beam, FP64 or WAKE_MIXED, that fits one
+ * 512-thread march CTA; call it before wake_load_beam / wake_set_beam (the beam's arrays are
+ * reallocated).  With trapping on, wake_step takes the separate calls (deposit, march, push).
+ * Errors: WAKE_EINVAL, WAKE_ESTATE (beam already loaded), WAKE_ENOMEM, WAKE_ECUDA.
+ */
+int wake_set_trapping(wake_sim *s, int sim, double gamma_t, int64_t capacity);
+
+/*
+ * The particles promoted so far in simulation `sim`, in the order they were promoted (by beam
+ * step, then slice, then ring): *count of them (host), and *dropped promotions that found no
+ * room (host).  Any of xyz (6 x capacity doubles, rows x, y, xi, u_x, u_y, u_z), w (capacity
+ * charge weights) and lost (capacity bytes) may be NULL; the first *count entries of each are
+ * written (device arrays).  Synchronous.
+ */
+int wake_trapped(wake_sim *s, int sim, double *xyz, double *w, uint8_t *lost, int64_t *count, int64_t *dropped);
+
 /* Copy the last march's fields of `sim` to caller-owned device arrays of (nxi+1)*(nr+1)
  * doubles each (any pointer may be NULL). */
 int wake_get_fields(wake_sim *s, int sim, double *psi, double *ez, double *er, double *bth);

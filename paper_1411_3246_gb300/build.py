@@ -14,7 +14,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # the mixed-precision marches use approximate FP32 divide and square root (a few ulp) and
 # flush denormals; every other translation unit keeps IEEE division and sqrt
 _FAST = ["--prec-div=false", "--prec-sqrt=false", "--ftz=true"]
-EXTRA = {"march_mixed.cu": _FAST, "march_mixed_small.cu": _FAST, "march_wide.cu": _FAST, "march_traj_mixed.cu": _FAST,
+EXTRA = {"march_mixed.cu": _FAST, "march_mixed_small.cu": _FAST, "march_wide.cu": _FAST, "march_ext_mixed.cu": _FAST,
          "march_mixed64.cu": _FAST}
 
 

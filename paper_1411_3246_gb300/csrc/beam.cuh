@@ -4,8 +4,10 @@
 // Beam state is SoA: x, y, u_x, u_y in the policy's type BT (float in the mixed form),
 // xi and u_z always in FP64 (u_z ~ gamma_b = 4e4 changes by O(1) per step and xi slips by
 // ~1e-9 per step: both are accumulated in FP64, the kicks themselves computed in BT).  A
-// flag byte per particle holds bit 0 = lost and bit 1 = witness; orig holds the particle's
-// index in the caller's order (the beam is kept sorted by xi cell for the pipelined step).
+// flag byte per particle holds bit 0 = lost, bit 1 = witness and bit 2 = a plasma particle
+// promoted by trapping; orig holds the particle's index in the caller's order (the beam is
+// kept sorted by xi cell for the pipelined step).  With trapping the arrays have room for
+// n_cap >= n particles: the bunches' n, then the promoted particles (the unused slots lost).
 #pragma once
 
 #include "wake_common.cuh"
@@ -14,12 +16,13 @@ namespace wake {
 
 struct BeamDesc {
   int64_t n, n_drive;
+  int64_t n_cap;           // slots in the arrays (n plus room for promoted particles)
   int nr, nxi;
   double rmax, ximax, dr, dxi, ds, gamma_b;
   double wd, ww;           // macroparticle weights of the drive and witness bunches
   void *x, *y, *ux, *uy;   // BT
   double *xi, *uz;
-  uint8_t *lost;           // flags: bit 0 lost, bit 1 witness
+  uint8_t *lost;           // flags: bit 0 lost, bit 1 witness, bit 2 promoted (trapping)
   int *orig;               // index in the caller's order
   void *w;                 // per-particle weight (BT): charge per 2 pi
   void *nb;                // beam-density grid (G)
@@ -30,6 +33,20 @@ struct BeamDesc {
 struct BunchInit {
   double sigma_r, eps_n, xi_d, sigma_zd, xi_w, sigma_zw, gamma_b;
 };
+
+// The slots past the bunches (room for promoted particles): empty, that is lost.
+template <class BT>
+__device__ __forceinline__ void clear_tail(const BeamDesc &b) {
+  for (int64_t j = b.n + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    ((BT *)b.x)[j] = ((BT *)b.y)[j] = ((BT *)b.ux)[j] = ((BT *)b.uy)[j] = (BT)0;
+    b.xi[j] = 0.0;
+    b.uz[j] = 0.0;
+    b.lost[j] = 1;
+    b.orig[j] = (int)j;
+    ((BT *)b.w)[j] = (BT)0;
+  }
+}
 
 // Eq. 12 bunches from standard normals (rows x, y, u_x, u_y, xi of a 5 x n array).
 template <class BT>
@@ -50,6 +67,7 @@ __global__ void beam_init_kernel(BeamDesc b, BunchInit q, const double *__restri
     b.orig[j] = (int)j;
     ((BT *)b.w)[j] = (BT)(drive ? b.wd : b.ww);
   }
+  clear_tail<BT>(b);
 }
 
 // A beam given by the caller: xyz rows x, y, xi, u_x, u_y, u_z (6 x n, FP64), weights w (NULL:
@@ -72,6 +90,7 @@ __global__ void beam_set_kernel(BeamDesc b, const double *__restrict__ xyz, cons
     b.orig[j] = (int)j;
     ((BT *)b.w)[j] = (BT)(w ? w[j] : (witness ? b.ww : b.wd));
   }
+  clear_tail<BT>(b);
 }
 
 // Raw bilinear deposit of the beam weights on the (r, xi) nodes (grid zeroed beforehand):
@@ -82,7 +101,7 @@ __device__ __forceinline__ void deposit_range(const BeamDesc &b, int64_t j0, int
   const int n1 = b.nr + 1;
   const BT inv_dr = (BT)(1.0 / b.dr);
   const double inv_dxi = 1.0 / b.dxi;
-  for (int64_t j = j0; j < b.n; j += stride) {
+  for (int64_t j = j0; j < b.n_cap; j += stride) {
     const uint8_t fl = b.lost[j];
     if (fl & 1) continue;
     const BT x = ((const BT *)b.x)[j], y = ((const BT *)b.y)[j];
@@ -173,7 +192,7 @@ __device__ __forceinline__ void push_range(const BeamDesc &b, int64_t j0, int64_
   const int n1 = b.nr + 1;
   const BT inv_dr = (BT)(1.0 / b.dr), dt = (BT)b.ds, Rw = (BT)b.rmax;
   const double inv_dxi = 1.0 / b.dxi;
-  for (int64_t j = j0; j < b.n; j += stride) {
+  for (int64_t j = j0; j < b.n_cap; j += stride) {
     if (b.lost[j] & 1) continue;
     BT x = X[j], y = Y[j], ux = UX[j], uy = UY[j];
     double xi = b.xi[j], uzd = b.uz[j];
@@ -238,8 +257,8 @@ template <class BT>
 __global__ void beam_diag_kernel(BeamDesc b) {
   const BT *UX = (const BT *)b.ux, *UY = (const BT *)b.uy;
   double nw = 0, sw = 0, sw2 = 0, nd = 0, sd = 0;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
-    if (b.lost[j] & 1) continue;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap; j += (int64_t)gridDim.x * blockDim.x) {
+    if (b.lost[j] & 5) continue;  // lost, or a promoted plasma particle (neither bunch)
     const double ux = UX[j], uy = UY[j], uz = b.uz[j];
     const double g = sqrt(1.0 + ux * ux + uy * uy + uz * uz) - b.gamma_b;
     if (b.lost[j] & 2) {
@@ -306,7 +325,7 @@ __global__ void beam_slip_kernel(BeamDesc b, double span, unsigned long long *ou
   for (int q = threadIdx.x; q < 64; q += blockDim.x) sh[q] = 0;
   __syncthreads();
   double m = 0.0;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap; j += (int64_t)gridDim.x * blockDim.x) {
     if (b.lost[j] & 1) continue;
     const double ux = ((const BT *)b.ux)[j], uy = ((const BT *)b.uy)[j], uz = b.uz[j];
     const double up2 = ux * ux + uy * uy, g = sqrt(1.0 + up2 + uz * uz);
@@ -323,7 +342,7 @@ __global__ void beam_slip_kernel(BeamDesc b, double span, unsigned long long *ou
     if (sh[q]) atomicAdd(&hist[q], sh[q]);
 }
 static __global__ void bin_count_kernel(BeamDesc b, int *count) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap; j += (int64_t)gridDim.x * blockDim.x)
     atomicAdd(&count[beam_bin(b, j)], 1);
 }
 // exclusive scan of nbins counts into start[0..nbins] (one block of 1024 threads)
@@ -350,7 +369,7 @@ static __global__ void bin_scan_kernel(const int *count, int *start, int *cursor
 }
 template <class BT>
 __global__ void bin_scatter_kernel(BeamDesc b, BeamDesc dst, int *cursor) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap; j += (int64_t)gridDim.x * blockDim.x) {
     const int64_t q = atomicAdd(&cursor[beam_bin(b, j)], 1);
     ((BT *)dst.x)[q] = ((const BT *)b.x)[j];
     ((BT *)dst.y)[q] = ((const BT *)b.y)[j];
@@ -366,8 +385,9 @@ __global__ void bin_scatter_kernel(BeamDesc b, BeamDesc dst, int *cursor) {
 // Scatter the beam back to the caller's order: out rows x, y, xi, u_x, u_y, u_z (6 x n).
 template <class BT>
 __global__ void beam_unpermute_kernel(BeamDesc b, double *xyz, uint8_t *lost) {
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap; j += (int64_t)gridDim.x * blockDim.x) {
     const int64_t o = b.orig[j];
+    if (o >= b.n) continue;  // a promoted particle (wake_trapped returns those)
     if (xyz) {
       xyz[0 * b.n + o] = (double)((const BT *)b.x)[j];
       xyz[1 * b.n + o] = (double)((const BT *)b.y)[j];
@@ -377,6 +397,67 @@ __global__ void beam_unpermute_kernel(BeamDesc b, double *xyz, uint8_t *lost) {
       xyz[5 * b.n + o] = b.uz[j];
     }
     if (lost) lost[o] = b.lost[j] & 1;
+  }
+}
+
+// Promoted plasma particles into the beam (trapping, Sec. I): entry q of the march's list
+// (ring j, slice k, r, u_r, u_theta, Gamma, w) becomes the particle in slot n + *used + rank_q,
+// rank_q the entry's place in (k, j) order, so that the slots do not depend on the order the
+// march's atomics produced: at (x, y) = (r, 0), xi = k dxi, momentum (u_r, u_theta, u_z) with
+// u_z = (1 + u_perp^2 - Gamma^2) / (2 Gamma) (Eqs. 2-3), weight w ds (the ring's flux over one
+// beam step), flags promoted (and lost outside the box).  Entries that do not fit the arrays
+// are counted in *dropped.  One block; *used advances by the entries placed.
+template <class BT>
+__global__ void trap_append_kernel(BeamDesc b, const double *__restrict__ list, const int *__restrict__ count, int cap,
+                                   int64_t *used, int64_t *dropped) {
+  const int nl = min(*count, cap);
+  const int64_t base = *used, room = b.n_cap - b.n - base;
+  for (int q = threadIdx.x; q < nl; q += blockDim.x) {
+    const double *e = list + 7 * (size_t)q;
+    const double key = e[1] * 1e9 + e[0];  // slice-major, then ring
+    int rank = 0;
+    for (int m = 0; m < nl; ++m) {
+      const double km = list[7 * (size_t)m + 1] * 1e9 + list[7 * (size_t)m];
+      rank += km < key;
+    }
+    if (rank >= room) continue;
+    const int64_t j = b.n + base + rank;
+    const double r = e[2], ur = e[3], ut = e[4], G = e[5], up2 = ur * ur + ut * ut;
+    const double xi = e[1] * b.dxi;
+    ((BT *)b.x)[j] = (BT)r;
+    ((BT *)b.y)[j] = (BT)0;
+    ((BT *)b.ux)[j] = (BT)ur;
+    ((BT *)b.uy)[j] = (BT)ut;
+    b.uz[j] = (1.0 + up2 - G * G) / (2.0 * G);
+    b.xi[j] = xi;
+    b.lost[j] = (uint8_t)4 | (uint8_t)((xi >= 0.0 && xi < b.ximax && r < b.rmax) ? 0 : 1);
+    b.orig[j] = (int)j;
+    ((BT *)b.w)[j] = (BT)(e[6] * b.ds);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int64_t placed = nl < room ? nl : (room > 0 ? room : 0);
+    *used = base + placed;
+    *dropped += (int64_t)(*count) - placed;
+  }
+}
+
+// The promoted particles (slots n .. n + used - 1) to caller arrays: xyz rows x, y, xi, u_x,
+// u_y, u_z of stride cap_out (FP64), weights w, lost flags.
+template <class BT>
+__global__ void trapped_out_kernel(BeamDesc b, int64_t used, int64_t cap_out, double *xyz, double *w, uint8_t *lost) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < used; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = b.n + q;
+    if (xyz) {
+      xyz[0 * cap_out + q] = (double)((const BT *)b.x)[j];
+      xyz[1 * cap_out + q] = (double)((const BT *)b.y)[j];
+      xyz[2 * cap_out + q] = b.xi[j];
+      xyz[3 * cap_out + q] = (double)((const BT *)b.ux)[j];
+      xyz[4 * cap_out + q] = (double)((const BT *)b.uy)[j];
+      xyz[5 * cap_out + q] = b.uz[j];
+    }
+    if (w) w[q] = (double)((const BT *)b.w)[j];
+    if (lost) lost[q] = b.lost[j] & 1;
   }
 }
 

@@ -784,7 +784,7 @@ __device__ __forceinline__ void add_charge(MarchSmem<Pol> &sm, ChargeWin<Pol> &a
 
 // Pass B: ring quantities at the position given by pos(sl, c, f, u_r, u_theta) and the
 // current-type deposits.  Gam[p] = Gamma, gq[p] = (gamma/Gamma) psi'(r).  All threads call.
-template <class Pol, int NT, int PPT, class Pos>
+template <class Pol, int NT, int PPT, bool kTrap = false, class Pos>
 __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int np,
                                               int nr, typename Pol::R dr, int *status, Pos &&pos,
                                               typename Pol::R (&Gam)[PPT], typename Pol::R (&gq)[PPT]) {
@@ -807,6 +807,8 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
       else
         pos(sl, c, f, u_r, u_t);
       if (p == 0) acc.init(c);
+      if constexpr (kTrap)
+        if (rs.w[sl] == (R)0) continue;  // promoted to a beam particle: no longer in the plasma
       const R rp = ((R)c + f) * dr;
       const R G = rs.G0[sl] + interp(sm.psi, c, f);
       if (!(G > (R)0)) flag(status, ST_NUMERIC);
@@ -978,6 +980,10 @@ __device__ __forceinline__ void resort_rings(MarchSmem<Pol> &sm, const RingSoA<t
 //                                   (kTraj true only) the slice-k state of the thread's own
 //                                   rings, with their stage-1 Gamma in rs.G1; the slots carry
 //                                   ring ids
+//   kTrap, trap_rings<NT, PPT>(k, rs, np)
+//                                   (kTrap true only) after slice k's stage-1 pass: the hook may
+//                                   promote the thread's own rings (their weight set to zero);
+//                                   a ring of zero weight no longer takes part or moves
 template <class Pol, int NT, int PPT, class Hooks>
 __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem_raw, Hooks &hk) {
   using R = typename Pol::R;
@@ -985,7 +991,8 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
   using Acc = typename Pol::Acc;
   const int tid = threadIdx.x, nr = d.nr, n1 = nr + 1, np = d.np, nxi = d.nxi;
   constexpr int SLOTS = NT * PPT;
-  constexpr bool kIds = Hooks::kTraj;
+  constexpr bool kTrap = Hooks::kTrap;
+  constexpr bool kIds = Hooks::kTraj || kTrap;
   MarchSmem<Pol> sm;
   sm.carve(smem_raw, n1, SLOTS, kIds);
   RingSoA<R> rs;
@@ -1091,7 +1098,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
     for (int i = tid; i < n1; i += NT) sm.rho[i] = (typename Pol::Q)0;
     {
       R Gs[PPT], gqs[PPT];
-      pass_currents<Pol, NT, PPT>(sm, rs, np, nr, dR, d.status, state_pos, Gs, gqs);
+      pass_currents<Pol, NT, PPT, kTrap>(sm, rs, np, nr, dR, d.status, state_pos, Gs, gqs);
 #pragma unroll
       for (int p = 0; p < PPT; ++p)
         if (tid * PPT + p < np) {
@@ -1099,6 +1106,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
           rs.F1[p * NT + tid] = gqs[p];
         }
       if constexpr (Hooks::kTraj) hk.template ring_state<NT, PPT>(k, rs, np);
+      if constexpr (kTrap) hk.template trap_rings<NT, PPT>(k, rs, np);
     }
     __syncthreads();
     solve_fields<Pol, NT>(sm, geo, nbk, nbk, sm.wtot);  // P2
@@ -1125,7 +1133,13 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
           rs.F1[sl] = rs.F1[sl] - interp(sm.bth, rs.c[sl], rs.f[sl]);
           int c;
           R f, u_r, u_t;
-          const R rr = midpoint(sl, c, f, u_r, u_t);
+          R rr;
+          if (kTrap && rs.w[sl] == (R)0) {  // a promoted ring stays where it is
+            state_pos(sl, c, f, u_r, u_t);
+            rr = ((R)c + f) * dR;
+          } else {
+            rr = midpoint(sl, c, f, u_r, u_t);
+          }
           if (!(rr >= (R)0 && rr <= R_wall)) flag(d.status, ST_ESCAPE);
           MC[p] = c;
           MF[p] = f;
@@ -1141,7 +1155,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
     solve_psi<Pol, NT>(sm, geo, sm.wtot);  // P0
     __syncthreads();
     for (int i = tid; i < n1; i += NT) sm.rho[i] = (typename Pol::Q)0;  // P1
-    pass_currents<Pol, NT, PPT>(sm, rs, np, nr, dR, d.status,
+    pass_currents<Pol, NT, PPT, kTrap>(sm, rs, np, nr, dR, d.status,
                                 [&](int p, int, int &c, R &f, R &u_r, R &u_t) {
                                   c = MC[p];
                                   f = MF[p];
@@ -1162,6 +1176,10 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
       for (int p = 0; p < PPT; ++p) {
         if (tid * PPT + p < np) {
           const int sl = p * NT + tid;
+          if (kTrap && rs.w[sl] == (R)0) {  // a promoted ring: no move, no charge
+            add_charge<Pol>(sm, acc, p, rs.c[sl], rs.f[sl], (R)0);
+            continue;
+          }
           const R F2b = F2[p] - interp(sm.bth, MC[p], MF[p]);  // at the midpoint
           const int c0 = rs.c[sl];
           const R f0 = rs.f[sl], ur0 = rs.ur[sl], G1v = rs.G1[sl], F1v = rs.F1[sl];
@@ -1204,6 +1222,7 @@ struct PlainHooks {
   using R = typename Pol::R;
   using G = typename Pol::G;
   static constexpr bool kTraj = false;
+  static constexpr bool kTrap = false;
   const G *nb;
   G *opsi, *oez, *oer, *obth;
   int n1;
@@ -1259,6 +1278,66 @@ struct TrajHooks : PlainHooks<Pol, NT> {
       }
   }
 };
+
+// The plain march with plasma-particle trapping (Sec. I: plasma particles past a threshold
+// become beam particles).  After slice k's stage-1 pass every ring of nonzero weight whose
+// Gamma = Gamma_0 + psi (Eq. 1) is below gamma_t is promoted: its weight drops to zero (it
+// still counted in slice k's fields) and an entry (ring j, slice k, r, u_r, u_theta, Gamma, w)
+// goes to list[7 q], q taken from *count (entries past cap are counted, not written).
+template <class Pol, int NT>
+struct TrapHooks : PlainHooks<Pol, NT> {
+  using R = typename Pol::R;
+  static constexpr bool kTrap = true;
+  double gamma_t;
+  double *list;
+  int *count;
+  int cap;
+  double dr;
+  template <int NT_, int PPT>
+  __device__ __forceinline__ void trap_rings(int k, const RingSoA<R> &rs, int np) const {
+#pragma unroll
+    for (int p = 0; p < PPT; ++p)
+      if (threadIdx.x * PPT + p < np) {
+        const int sl = p * NT_ + threadIdx.x;
+        const R w = rs.w[sl];
+        if (w != (R)0 && (double)rs.G1[sl] < gamma_t) {
+          const int q = atomicAdd(count, 1);
+          if (q < cap) {
+            const double r = ((double)rs.c[sl] + (double)rs.f[sl]) * dr;
+            double *e = list + 7 * (size_t)q;
+            e[0] = (double)rs.id[sl];
+            e[1] = (double)k;
+            e[2] = r;
+            e[3] = (double)rs.ur[sl];
+            e[4] = r > 0.0 ? (double)rs.lz[sl] / r : 0.0;
+            e[5] = (double)rs.G1[sl];
+            e[6] = (double)w;
+          }
+          rs.w[sl] = (R)0;
+        }
+      }
+  }
+};
+
+template <class Pol, int NT, int PPT>
+__global__ void __launch_bounds__(NT, 1) march_trap_kernel(const SimDesc *desc) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const SimDesc &d = *desc;
+  TrapHooks<Pol, NT> hk;
+  hk.nb = (const typename Pol::G *)d.nb;
+  hk.opsi = (typename Pol::G *)d.psi;
+  hk.oez = (typename Pol::G *)d.ez;
+  hk.oer = (typename Pol::G *)d.er;
+  hk.obth = (typename Pol::G *)d.bth;
+  hk.n1 = d.nr + 1;
+  hk.status = d.status;
+  hk.gamma_t = d.gamma_t;
+  hk.list = d.trap;
+  hk.count = d.trap_count;
+  hk.cap = d.trap_cap;
+  hk.dr = d.dr;
+  march_body<Pol, NT, PPT>(d, smem_raw, hk);
+}
 
 template <class Pol, int NT, int PPT>
 __global__ void __launch_bounds__(NT, 1) march_traj_kernel(const SimDesc *desc, double *traj, int every) {

@@ -74,5 +74,8 @@ size_t march_traj_smem_fp64(int n1, int np);
 size_t march_traj_smem_mixed(int n1, int np);
 cudaError_t launch_march_traj_fp64(const SimDesc *d, int n1, int np, double *traj, int every, cudaStream_t s);
 cudaError_t launch_march_traj_mixed(const SimDesc *d, int n1, int np, double *traj, int every, cudaStream_t s);
+// The plain march with trapping (march_trap_kernel) on descriptor d (device); same shared memory.
+cudaError_t launch_march_trap_fp64(const SimDesc *d, int n1, int np, cudaStream_t s);
+cudaError_t launch_march_trap_mixed(const SimDesc *d, int n1, int np, cudaStream_t s);
 
 }  // namespace wake

@@ -66,6 +66,7 @@ struct PipeHooks {
   using G = typename Pol::G;
   using BT = R;
   static constexpr bool kTraj = false;
+  static constexpr bool kTrap = false;
   const PipeArgs &a;
   int t;          // step within the launch
   R *win;         // 4 slices x (E_r, E_z, B_theta) x n1

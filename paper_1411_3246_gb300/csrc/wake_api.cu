@@ -60,6 +60,13 @@ struct Sim {
   int2 *defer_list = nullptr;
   size_t defer_bytes = 0;
   int *status = nullptr;
+  // trapping (wake_set_trapping): beam slots for promoted particles, the march's promotions
+  int64_t n_cap = 0;            // beam slots: n_beam, plus room for promoted particles
+  double trap_gamma = 0.0;      // promotion threshold on Gamma (0: no trapping)
+  double *trap_list = nullptr;  // one march's promotions: np entries of 7 doubles
+  int *trap_count = nullptr;
+  int64_t *trap_used = nullptr;  // [0] promoted particles in the beam, [1] promotions dropped
+  bool trap_pending = false;     // a march's promotions not yet appended to the beam
   bool plasma = false, beam = false, marched = false;
   bool wide = false;  // marched by the wide form (rings in a global buffer)
 };
@@ -92,6 +99,7 @@ struct wake_sim {
   int n = 0, precision = 0;
   cudaStream_t stream = nullptr;
   std::vector<Sim> sims;
+  std::vector<SimDesc> h_desc;  // host copy of d_desc
   SimDesc *d_desc = nullptr;
   int *d_order = nullptr;
   double *d_diag = nullptr;
@@ -132,7 +140,7 @@ void free_sim(Sim &s) {
   void *ptrs[] = {s.r0, s.ur0, s.lz, s.G0, s.w, s.ring_buf, s.nb, s.psi, s.ez, s.er, s.bth, s.bx, s.by, s.bux, s.buy,
                   s.bxi, s.buz, s.blost, s.status, s.orig, s.bx2, s.by2, s.bux2, s.buy2, s.bxi2, s.buz2, s.blost2,
                   s.orig2, s.bin_count, s.bin_start, s.bin_cursor, s.slip, s.pgrids, s.progress, s.pring,
-                  s.defer_cnt, s.target, s.defer_list, s.bwt, s.bwt2};
+                  s.defer_cnt, s.target, s.defer_list, s.bwt, s.bwt2, s.trap_list, s.trap_count, s.trap_used};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   s = Sim();
@@ -164,11 +172,40 @@ int dalloc(T **p, size_t bytes) {
   return WAKE_OK;
 }
 
+// The beam arrays of simulation s for s.n_cap particles (any earlier ones freed).
+int alloc_beam(wake_sim *h, Sim &s) {
+  void **old[] = {&s.bx, &s.by, &s.bux, &s.buy, (void **)&s.bxi, (void **)&s.buz, (void **)&s.blost, (void **)&s.orig,
+                  &s.bx2, &s.by2, &s.bux2, &s.buy2, (void **)&s.bxi2, (void **)&s.buz2, (void **)&s.blost2,
+                  (void **)&s.orig2, (void **)&s.bin_count, (void **)&s.bin_start, (void **)&s.bin_cursor,
+                  (void **)&s.slip, &s.bwt, &s.bwt2};
+  for (void **q : old)
+    if (*q) {
+      cudaFree(*q);
+      *q = nullptr;
+    }
+  const size_t bt = gsize(h->precision) * (size_t)s.n_cap, nbm = (size_t)s.n_cap;
+  int rc;
+  if ((rc = dalloc(&s.bx, bt)) || (rc = dalloc(&s.by, bt)) || (rc = dalloc(&s.bux, bt)) || (rc = dalloc(&s.buy, bt)) ||
+      (rc = dalloc(&s.bxi, sizeof(double) * nbm)) || (rc = dalloc(&s.buz, sizeof(double) * nbm)) ||
+      (rc = dalloc(&s.blost, nbm)) || (rc = dalloc(&s.orig, sizeof(int) * nbm)) || (rc = dalloc(&s.bx2, bt)) ||
+      (rc = dalloc(&s.by2, bt)) || (rc = dalloc(&s.bux2, bt)) || (rc = dalloc(&s.buy2, bt)) ||
+      (rc = dalloc(&s.bxi2, sizeof(double) * nbm)) || (rc = dalloc(&s.buz2, sizeof(double) * nbm)) ||
+      (rc = dalloc(&s.blost2, nbm)) || (rc = dalloc(&s.orig2, sizeof(int) * nbm)) ||
+      (rc = dalloc(&s.bin_count, sizeof(int) * (s.p.nxi + 2))) ||
+      (rc = dalloc(&s.bin_start, sizeof(int) * (s.p.nxi + 2))) ||
+      (rc = dalloc(&s.bin_cursor, sizeof(int) * (s.p.nxi + 2))) ||
+      (rc = dalloc(&s.slip, sizeof(unsigned long long) + 64 * sizeof(int))) || (rc = dalloc(&s.bwt, bt)) ||
+      (rc = dalloc(&s.bwt2, bt)))
+    return rc;
+  return WAKE_OK;
+}
+
 BeamDesc beam_desc(const Sim &s, double *diag) {
   BeamDesc b{};
   const wake_params &p = s.p;
   b.n = p.n_beam;
   b.n_drive = p.n_drive;
+  b.n_cap = s.n_cap > p.n_beam ? s.n_cap : p.n_beam;
   b.nr = p.nr;
   b.nxi = p.nxi;
   b.rmax = p.rmax;
@@ -430,20 +467,8 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
       break;
     }
     if (p[i].n_beam > 0) {
-      const size_t bt = gsize(h->precision) * p[i].n_beam;
-      const size_t nbm = (size_t)p[i].n_beam;
-      if ((rc = dalloc(&s.bx, bt)) || (rc = dalloc(&s.by, bt)) || (rc = dalloc(&s.bux, bt)) || (rc = dalloc(&s.buy, bt)) ||
-          (rc = dalloc(&s.bxi, sizeof(double) * nbm)) || (rc = dalloc(&s.buz, sizeof(double) * nbm)) ||
-          (rc = dalloc(&s.blost, nbm)) || (rc = dalloc(&s.orig, sizeof(int) * nbm)) || (rc = dalloc(&s.bx2, bt)) ||
-          (rc = dalloc(&s.by2, bt)) || (rc = dalloc(&s.bux2, bt)) || (rc = dalloc(&s.buy2, bt)) ||
-          (rc = dalloc(&s.bxi2, sizeof(double) * nbm)) || (rc = dalloc(&s.buz2, sizeof(double) * nbm)) ||
-          (rc = dalloc(&s.blost2, nbm)) || (rc = dalloc(&s.orig2, sizeof(int) * nbm)) ||
-          (rc = dalloc(&s.bin_count, sizeof(int) * (p[i].nxi + 2))) ||
-          (rc = dalloc(&s.bin_start, sizeof(int) * (p[i].nxi + 2))) ||
-          (rc = dalloc(&s.bin_cursor, sizeof(int) * (p[i].nxi + 2))) ||
-          (rc = dalloc(&s.slip, sizeof(unsigned long long) + 64 * sizeof(int))) || (rc = dalloc(&s.bwt, bt)) ||
-          (rc = dalloc(&s.bwt2, bt)))
-        break;
+      s.n_cap = p[i].n_beam;
+      if ((rc = alloc_beam(h, s))) break;
     } else {
       // frozen analytic driver (Eq. 12) on the nodes
       const double dr = p[i].rmax / p[i].nr, dxi = p[i].ximax / p[i].nxi;
@@ -518,6 +543,7 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
       return (double)desc[a].np * desc[a].nxi > (double)desc[b].np * desc[b].nxi;
     });
+    h->h_desc = desc;
     if ((rc = dalloc(&h->d_desc, sizeof(SimDesc) * n_sims)) == WAKE_OK &&
         (rc = dalloc(&h->d_order, sizeof(int) * n_sims)) == WAKE_OK &&
         (rc = dalloc(&h->d_diag, sizeof(double) * 5 * n_sims)) == WAKE_OK) {
@@ -622,10 +648,76 @@ int wake_beam_deposit(wake_sim *h) {
   return WAKE_OK;
 }
 
+int wake_set_trapping(wake_sim *h, int sim, double gamma_t, int64_t capacity) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  Sim &s = h->sims[sim];
+  if (h->n != 1) return fail(WAKE_EINVAL, "wake_set_trapping: trapping needs a handle of one simulation");
+  if (s.p.n_beam == 0) return fail(WAKE_EINVAL, "wake_set_trapping: trapping needs a particle beam (n_beam > 0)");
+  if (!(gamma_t >= 0.0) || capacity < 0 || s.p.n_beam + capacity > ((int64_t)1 << 31) - 1)
+    return fail(WAKE_EINVAL, "wake_set_trapping: need gamma_t >= 0 and 0 <= capacity < 2^31 - n_beam");
+  if (s.beam) return fail(WAKE_ESTATE, "wake_set_trapping: call it before wake_load_beam / wake_set_beam");
+  const int n1 = s.p.nr + 1;
+  const size_t smem = h->precision == WAKE_FP64 ? march_traj_smem_fp64(n1, s.np) : march_traj_smem_mixed(n1, s.np);
+  if (h->precision == WAKE_MIXED64 || s.wide || smem > kMaxSmemPerCta)
+    return fail(WAKE_EINVAL, "wake_set_trapping: FP64 and mixed handles whose simulation fits one 512-thread march CTA");
+  s.n_cap = s.p.n_beam + capacity;
+  if ((rc = alloc_beam(h, s))) return rc;
+  if (!s.trap_list && ((rc = dalloc(&s.trap_list, sizeof(double) * 7 * (size_t)s.np)) ||
+                       (rc = dalloc(&s.trap_count, sizeof(int))) || (rc = dalloc(&s.trap_used, 2 * sizeof(int64_t)))))
+    return rc;
+  CUDA_TRY(cudaMemsetAsync(s.trap_count, 0, sizeof(int), h->stream));
+  CUDA_TRY(cudaMemsetAsync(s.trap_used, 0, 2 * sizeof(int64_t), h->stream));
+  s.trap_gamma = gamma_t;
+  s.trap_pending = false;
+  SimDesc &d = h->h_desc[sim];
+  d.gamma_t = gamma_t;
+  d.trap = s.trap_list;
+  d.trap_count = s.trap_count;
+  d.trap_cap = s.np;
+  CUDA_TRY(cudaMemcpyAsync(h->d_desc + sim, &d, sizeof(SimDesc), cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));  // d is host memory that may change
+  return WAKE_OK;
+}
+
+int wake_trapped(wake_sim *h, int sim, double *xyz, double *w, uint8_t *lost, int64_t *count, int64_t *dropped) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  Sim &s = h->sims[sim];
+  if (!s.trap_used) return fail(WAKE_ESTATE, "wake_trapped: trapping is not set (wake_set_trapping)");
+  int64_t u[2] = {0, 0};
+  CUDA_TRY(cudaMemcpyAsync(u, s.trap_used, sizeof(u), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(cudaStreamSynchronize(h->stream));
+  if (count) *count = u[0];
+  if (dropped) *dropped = u[1];
+  if (u[0] > 0 && (xyz || w || lost)) {
+    const BeamDesc b = beam_desc(s, nullptr);
+    const int64_t cap = s.n_cap - s.p.n_beam;
+    const int nb = grid_blocks(u[0], 256);
+    if (h->precision == WAKE_FP64)
+      trapped_out_kernel<double><<<nb, 256, 0, h->stream>>>(b, u[0], cap, xyz, w, lost);
+    else
+      trapped_out_kernel<float><<<nb, 256, 0, h->stream>>>(b, u[0], cap, xyz, w, lost);
+    CUDA_TRY(cudaGetLastError());
+  }
+  return WAKE_OK;
+}
+
 int wake_plasma_march(wake_sim *h) {
   if (!h) return fail(WAKE_EINVAL, "null handle");
   for (auto &s : h->sims)
     if (!s.plasma) return fail(WAKE_ESTATE, "wake_plasma_march before wake_load_plasma");
+  if (h->n == 1 && h->sims[0].trap_gamma > 0.0) {  // the march that promotes rings
+    Sim &s = h->sims[0];
+    CUDA_TRY(cudaMemsetAsync(s.trap_count, 0, sizeof(int), h->stream));
+    const int n1 = s.p.nr + 1;
+    const cudaError_t e = h->precision == WAKE_FP64 ? launch_march_trap_fp64(h->d_desc, n1, s.np, h->stream)
+                                                    : launch_march_trap_mixed(h->d_desc, n1, s.np, h->stream);
+    if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("trapping march launch: ") + cudaGetErrorString(e));
+    s.trap_pending = true;
+    s.marched = true;
+    return WAKE_OK;
+  }
   int rc = launch_march(h);
   if (rc) return rc;
   for (auto &s : h->sims) s.marched = true;
@@ -672,7 +764,17 @@ int wake_beam_push(wake_sim *h) {
     if (s.p.n_beam == 0) continue;
     if (!s.beam || !s.marched) return fail(WAKE_ESTATE, "wake_beam_push needs a loaded beam and a march");
     BeamDesc b = beam_desc(s, nullptr);
-    const int nb = grid_blocks(s.p.n_beam, 256);
+    if (s.trap_pending) {  // the last march's promoted rings join the beam before the push
+      if (h->precision == WAKE_FP64)
+        trap_append_kernel<double><<<1, 1024, 0, h->stream>>>(b, s.trap_list, s.trap_count, s.np, s.trap_used,
+                                                             s.trap_used + 1);
+      else
+        trap_append_kernel<float><<<1, 1024, 0, h->stream>>>(b, s.trap_list, s.trap_count, s.np, s.trap_used,
+                                                            s.trap_used + 1);
+      CUDA_TRY(cudaGetLastError());
+      s.trap_pending = false;
+    }
+    const int nb = grid_blocks(b.n_cap, 256);
     if (h->precision == WAKE_FP64)
       beam_push_kernel<double, double><<<nb, 256, 0, h->stream>>>(b);
     else
@@ -1168,6 +1270,7 @@ int wake_step(wake_sim *h, int nsteps) {
   if (!h || nsteps < 0) return fail(WAKE_EINVAL, "wake_step: null handle or nsteps < 0");
   h->ev_used = 0;
   if (nsteps == 0) return WAKE_OK;
+  if (h->n == 1 && h->sims[0].trap_gamma > 0.0) return step_sequential(h, nsteps);  // trapping: step by step
   if (h->n == 1 && h->sims[0].p.n_beam > 0) {
     Sim &s = h->sims[0];
     if (!s.beam || !s.plasma) return fail(WAKE_ESTATE, "wake_step needs wake_load_plasma and wake_load_beam");

@@ -25,6 +25,11 @@ struct SimDesc {
   const void *nb;                        // beam density n_b on the nodes
   void *psi, *ez, *er, *bth;             // march output
   int *status;
+  // trapping (march_trap_kernel): threshold, promotion list of trap_cap entries of 7 doubles
+  double gamma_t;
+  double *trap;
+  int *trap_count;
+  int trap_cap;
 };
 
 // Cell index c in [0, nr-1] and offset f = r/dr - c (f in [0,1] for 0 <= r <= rmax).

@@ -19,7 +19,7 @@ WAKE_FP64, WAKE_MIXED, WAKE_MIXED64 = 0, 1, 2
 # every entry point the header declares
 EXPORTS = ["wake_init", "wake_load_plasma", "wake_load_beam", "wake_set_beam", "wake_beam_deposit", "wake_plasma_march",
            "wake_plasma_march_traj", "wake_beam_push", "wake_step", "wake_tile", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
-           "wake_diagnostics", "wake_status", "wake_beam_deposit_noalloc", "wake_adjoint_init",
+           "wake_diagnostics", "wake_status", "wake_set_trapping", "wake_trapped", "wake_beam_deposit_noalloc", "wake_adjoint_init",
            "wake_adjoint_forward", "wake_adjoint_backward", "wake_adjoint_destroy", "wake_last_error", "wake_destroy"]
 WAKE_NOALLOC_MAX_NODES = 524288
 
@@ -65,6 +65,8 @@ def lib():
         L.wake_get_beam.argtypes = [vp, i32, vp, vp]
         L.wake_diagnostics.argtypes = [vp, pd]
         L.wake_status.argtypes = [vp, i32]
+        L.wake_set_trapping.argtypes = [vp, i32, C.c_double, C.c_int64]
+        L.wake_trapped.argtypes = [vp, i32, vp, vp, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.wake_beam_deposit_noalloc.argtypes = [C.POINTER(wake_params), vp, vp, vp, vp]
         L.wake_adjoint_init.argtypes = [C.POINTER(wake_params), i32, i32, vp, C.POINTER(vp)]
         L.wake_adjoint_forward.argtypes = [vp, pd, pd, vp, vp, pd]
@@ -185,6 +187,18 @@ def wake_beam_deposit_noalloc(params, xyz, lost, nb, stream=None):
         stream = torch.cuda.current_stream()
     _check(lib().wake_beam_deposit_noalloc(C.byref(params), _ptr(xyz), _ptr(lost),
                                            C.c_void_p(stream.cuda_stream), _ptr(nb)))
+
+
+def wake_set_trapping(h, sim, gamma_t, capacity):
+    _check(lib().wake_set_trapping(h, sim, float(gamma_t), int(capacity)))
+
+
+def wake_trapped(h, sim, xyz=None, w=None, lost=None):
+    """Returns (count, dropped); xyz (6, capacity), w (capacity,), lost (capacity,) float64 /
+    uint8 CUDA tensors, or None, receive the promoted particles."""
+    count, dropped = C.c_int64(), C.c_int64()
+    _check(lib().wake_trapped(h, sim, _ptr(xyz), _ptr(w), _ptr(lost), C.byref(count), C.byref(dropped)))
+    return count.value, dropped.value
 
 
 def wake_status(h, sim):

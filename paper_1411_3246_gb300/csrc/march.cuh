@@ -57,6 +57,8 @@ __device__ __forceinline__ FF wide_shfl_up(FF a, int o) {
   return FF{__shfl_up_sync(kFull, a.h, o), __shfl_up_sync(kFull, a.l, o)};
 }
 __device__ __forceinline__ double wide_shfl_down(double a, int o) { return __shfl_down_sync(kFull, a, o); }
+__device__ __forceinline__ double wide_shfl_idx(double a, int l) { return __shfl_sync(kFull, a, l); }
+__device__ __forceinline__ FF wide_shfl_idx(FF a, int l) { return FF{__shfl_sync(kFull, a.h, l), __shfl_sync(kFull, a.l, l)}; }
 __device__ __forceinline__ FF wide_shfl_down(FF a, int o) {
   return FF{__shfl_down_sync(kFull, a.h, o), __shfl_down_sync(kFull, a.l, o)};
 }
@@ -232,6 +234,7 @@ struct MarchSmem {
   N *invR, *invV, *alpha, *ga, *gb, *gc;        // tables (FP64 form; the mixed forms keep
                                                 // invR = 1/(m dr) and ga = 1/(j + 1/2) only)
   int *cnt;                                     // re-sort counts
+  int *qn;                                      // entries in the out-of-window ring queue
   typename Pol::W *wtot;                        // block-scan warp totals
   RingSoA<R> rings;                             // ring slots (mixed form)
 
@@ -241,7 +244,7 @@ struct MarchSmem {
     b += sizeof(N) * (Pol::kTables ? 6 : 2) * (size_t)n1;
     if (Pol::kSortEvery > 0) b += sizeof(int) * ((size_t)n1 + 32);
     if (Pol::kSmemRings) b += RingSoA<R>::bytes(slots, ids) + 32;
-    return b;
+    return b + 64;
   }
   __device__ void carve(unsigned char *base, int n1, int slots, bool ids = false) {
     wtot = (typename Pol::W *)base;
@@ -282,8 +285,14 @@ struct MarchSmem {
       cnt = ip;
       ip += n1 + 32;
     }
+    qn = ip;
+    ip += 16;
     if (Pol::kSmemRings) rings.carve((void *)(((uintptr_t)ip + 31) & ~(uintptr_t)31), slots, ids);
   }
+  // The out-of-window ring queue: slot ids in the tridiagonal rows, which are free from the end
+  // of one solve to the start of the next (a ring pass and the deposits that follow it)
+  __device__ __forceinline__ int *queue() const { return (int *)ta; }
+  __device__ __forceinline__ int queue_cap(int n1) const { return (int)(4 * ((size_t)n1 + 32) * sizeof(N) / sizeof(int)); }
 };
 
 // ---------------------------------------------------------------------------------------
@@ -402,11 +411,20 @@ __device__ __forceinline__ FF q_to_wide<long long, FF>(long long d) {
 // row sum s' = s - k1 s_{q-k} - k2 s_{q+k} (k1 = a_q/b_{q-k}, k2 = c_q/b_{q+k}, both <= 0)
 // adds terms of one sign, so the margin of diagonal dominance is never lost to cancellation;
 // b = s - a - c likewise.  After ceil(log2 n) doublings a = c = 0 and x_q = d_q / s_q.
-// Double-buffered; returns the buffer holding the result.  Ends with a barrier.
-template <int NT, class S>
-__device__ __forceinline__ int pcr_rowsum(S *a0, S *s0, S *c0, S *d0, S *a1, S *s1, S *c1, S *d1, int n) {
+//
+// The first doublings (strides 1 .. ns/2) run over the block, double-buffered, one barrier
+// each.  They leave ns independent systems, rows r, r + ns, r + 2 ns, ... (ns the smallest
+// power of two >= NT/32 with n <= 32 ns); each is finished by one warp, lane l holding row
+// r + ns l, with the remaining doublings (lane strides 1 .. 16) done by shuffles.  The
+// arithmetic is that of the block form, stride for stride.  out(q, x_q) receives the solution.
+template <int NT, class S, class Out>
+__device__ __forceinline__ void pcr_rowsum_solve(S *a0, S *s0, S *c0, S *d0, S *a1, S *s1, S *c1, S *d1, int n,
+                                                 Out &&out) {
+  constexpr int W = NT / 32;
+  int ns = W;
+  while (32 * ns < n) ns <<= 1;
   int cur = 0;
-  for (int k = 1; k < n; k <<= 1) {
+  for (int k = 1; k < ns && k < n; k <<= 1) {
     const S *a = cur ? a1 : a0, *sm_ = cur ? s1 : s0, *c = cur ? c1 : c0, *d = cur ? d1 : d0;
     S *an = cur ? a0 : a1, *sn = cur ? s0 : s1, *cn = cur ? c0 : c1, *dn = cur ? d0 : d1;
     for (int q = threadIdx.x; q < n; q += NT) {
@@ -434,7 +452,40 @@ __device__ __forceinline__ int pcr_rowsum(S *a0, S *s0, S *c0, S *d0, S *a1, S *
     __syncthreads();
     cur ^= 1;
   }
-  return cur;
+  const S *a = cur ? a1 : a0, *sm_ = cur ? s1 : s0, *c = cur ? c1 : c0, *d = cur ? d1 : d0;
+  const int lane = threadIdx.x & 31;
+  for (int r = threadIdx.x >> 5; r < ns; r += W) {
+    const int q = r + ns * lane;
+    const bool on = q < n;  // rows past n: the identity (their neighbours' couplings to them are zero)
+    S aq = on ? a[q] : (S)0, sq = on ? sm_[q] : (S)1, cq = on ? c[q] : (S)0, dq = on ? d[q] : (S)0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const S am = __shfl_up_sync(kFull, aq, o), smm = __shfl_up_sync(kFull, sq, o);
+      const S cm = __shfl_up_sync(kFull, cq, o), dm = __shfl_up_sync(kFull, dq, o);
+      const S ap = __shfl_down_sync(kFull, aq, o), spp = __shfl_down_sync(kFull, sq, o);
+      const S cp = __shfl_down_sync(kFull, cq, o), dp = __shfl_down_sync(kFull, dq, o);
+      S s2 = sq, d2 = dq, na = (S)0, nc = (S)0;
+      if (lane >= o) {
+        const S bm = smm - am - cm;
+        const S k1 = aq / bm;
+        s2 -= k1 * smm;
+        d2 -= k1 * dm;
+        na = -am * k1;
+      }
+      if (lane + o < 32) {
+        const S bp = spp - ap - cp;
+        const S k2 = cq / bp;
+        s2 -= k2 * spp;
+        d2 -= k2 * dp;
+        nc = -cp * k2;
+      }
+      aq = na;
+      sq = s2;
+      cq = nc;
+      dq = d2;
+    }
+    if (on) out(q, dq / sq);
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -443,11 +494,14 @@ __device__ __forceinline__ int pcr_rowsum(S *a0, S *s0, S *c0, S *d0, S *a1, S *
 
 // Block-wide inclusive scan (suffix scan if Reverse) of n values, fused with its producer and
 // consumer: in(m) gives element m, out(m, s) receives the scan at m.  Each thread holds up to
-// EMAX consecutive elements in registers; warps scan the thread totals with shuffles and warp
-// 0 scans the warp totals.  Contains two barriers and ends with one.
+// EMAX consecutive elements in registers; warps scan the thread totals with shuffles, and
+// after one barrier every warp scans the NT/32 warp totals itself for its offset.  Contains
+// one barrier and ends with another.
 template <int NT, int EMAX, bool Reverse, class W, class In, class Out>
 __device__ __forceinline__ void block_scan_fused(int n, W *wtot, In &&in, Out &&out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = NT / 32;
+  static_assert(NW <= 32, "one warp scans the warp totals");
   const int E = (n + NT - 1) / NT;  // <= EMAX
   const int beg = tid * E;
   W v[EMAX];
@@ -469,17 +523,11 @@ __device__ __forceinline__ void block_scan_fused(int n, W *wtot, In &&in, Out &&
   }
   if (lane == 31) wtot[warp] = incl;
   __syncthreads();
-  if (warp == 0) {
-    W t = lane < NT / 32 ? wtot[lane] : wide_zero<W>();
+  // this warp's offset: the sum of the totals of the warps before it
+  W t = lane < warp ? wtot[lane] : wide_zero<W>();
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const W u = wide_shfl_up(t, o);
-      if (lane >= o) t = wide_add(t, u);
-    }
-    if (lane < NT / 32) wtot[NT / 32 + lane] = t;
-  }
-  __syncthreads();
-  W run = warp > 0 ? wtot[NT / 32 + warp - 1] : wide_zero<W>();
+  for (int o = 1; o < NW; o <<= 1) t = wide_add(t, wide_shfl_down(t, o));
+  W run = wide_shfl_idx(t, 0);
   const W below = wide_shfl_up(incl, 1);
   if (lane > 0) run = wide_add(run, below);
 #pragma unroll
@@ -564,9 +612,9 @@ __device__ __forceinline__ void solve_fields(MarchSmem<Pol> &sm, const NodeGeo<P
   // parallel cyclic reduction (on row sums); the second buffer reuses the deposit arrays J_z, chi, T, P,
   // which are dead once the rows are set up (they are zeroed before the next pass B)
   static_assert(sizeof(Acc) == sizeof(R), "PCR buffer reuses deposit arrays");
-  const int cur = pcr_rowsum<NT, R>(sm.ta, sm.tb, sm.tc, sm.td, (R *)sm.jz, (R *)sm.chi, (R *)sm.T, (R *)sm.P, nr);
-  const R *bb = cur ? (const R *)sm.chi : sm.tb, *dd = cur ? (const R *)sm.P : sm.td;  // row sum = diagonal now
-  for (int m = tid; m < n1; m += NT) sm.bth[m] = m > 0 ? dd[m - 1] / bb[m - 1] : (R)0;
+  pcr_rowsum_solve<NT, R>(sm.ta, sm.tb, sm.tc, sm.td, (R *)sm.jz, (R *)sm.chi, (R *)sm.T, (R *)sm.P, nr,
+                          [&](int q, R x) { sm.bth[q + 1] = x; });  // row q is node q + 1
+  if (tid == 0) sm.bth[0] = (R)0;
   __syncthreads();
 }
 
@@ -751,6 +799,7 @@ struct ChargeWin<PolMixed64> : ChargeWin<PolMixed> {};
 template <>
 struct ChargeWin<PolWideFP64> : ChargeWin<PolFP64> {};
 
+
 __device__ __forceinline__ void q_atomic_add(double *p, double v) { atomicAdd(p, v); }
 __device__ __forceinline__ void q_atomic_add(long long *p, long long v) {
   atomicAdd((unsigned long long *)p, (unsigned long long)v);
@@ -777,16 +826,167 @@ __device__ __forceinline__ void add_charge(MarchSmem<Pol> &sm, ChargeWin<Pol> &a
   if (p == 0) acc.init(c);
   if (!acc.add(c, f, w)) ChargeWin<Pol>::direct(sm.rho, c, f, w);
 }
+// Charge deposit of ring p through the window; a ring outside it is marked in miss (bit p) and
+// left to warp_misses.
+template <class Pol>
+__device__ __forceinline__ void add_charge_mark(ChargeWin<Pol> &acc, int p, int c, typename Pol::R f,
+                                                typename Pol::R w, unsigned &miss) {
+  if (p == 0) acc.init(c);
+  if (!acc.add(c, f, w)) miss |= 1u << p;
+}
 
 // ---------------------------------------------------------------------------------------
 // ring passes
 // ---------------------------------------------------------------------------------------
 
+// The i-th (from 0) out-of-window ring of the warp, counted ring index p first and lane second,
+// when mp[p] holds the lanes that marked ring p: returns its slot.
+template <int NT, int PPT>
+__device__ __forceinline__ int warp_miss_slot(const unsigned (&mp)[PPT], int i) {
+  int before = 0, pp = 0, rank = 0;
+  unsigned m = 0u;
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    const int n = __popc(mp[p]);
+    if (i >= before && i < before + n) {
+      pp = p;
+      rank = i - before;
+      m = mp[p];
+    }
+    before += n;
+  }
+  for (int r = 0; r < rank; ++r) m &= m - 1u;  // drop the rank lowest lanes
+  return pp * NT + (int)(threadIdx.x & ~31u) + (__ffs(m) - 1);
+}
+
+// Marks of the thread's out-of-window rings (bit p: ring p), shared over the warp: lane l
+// handles the warp's l-th, (l+32)-th, ... marked ring through fn(slot).  All lanes call.
+template <int NT, int PPT, class Fn>
+__device__ __forceinline__ void warp_misses(unsigned miss, Fn &&fn) {
+  unsigned mp[PPT];
+  int tot = 0;
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    mp[p] = __ballot_sync(kFull, (miss >> p) & 1u);
+    tot += __popc(mp[p]);
+  }
+  if (tot == 0) return;
+  __syncwarp();  // the slots the owners wrote in the pass are visible to the warp
+  const int lane = threadIdx.x & 31;
+  for (int i0 = 0; i0 < tot; i0 += 32)
+    if (i0 + lane < tot) fn(warp_miss_slot<NT, PPT>(mp, i0 + lane));
+}
+
+// The same marks handed to the whole CTA: the warp reserves entries of the queue (one shared
+// atomic) and stores the marked rings' slots; drain_queue, after the pass's barrier, spreads
+// them over all warps.  Rings past the queue's capacity are handled by the warp through
+// fn(slot).  All lanes call.
+template <int NT, int PPT, class Pol, class Fn>
+__device__ __forceinline__ void queue_misses(MarchSmem<Pol> &sm, int n1, unsigned miss, Fn &&fn) {
+  unsigned mp[PPT];
+  int tot = 0;
+#pragma unroll
+  for (int p = 0; p < PPT; ++p) {
+    mp[p] = __ballot_sync(kFull, (miss >> p) & 1u);
+    tot += __popc(mp[p]);
+  }
+  if (tot == 0) return;
+  const int lane = threadIdx.x & 31, cap = sm.queue_cap(n1);
+  int base = 0;
+  if (lane == 0) base = atomicAdd(sm.qn, tot);
+  base = __shfl_sync(kFull, base, 0);
+  int *q = sm.queue();
+  __syncwarp();
+  for (int i0 = 0; i0 < tot; i0 += 32) {
+    const int i = i0 + lane;
+    if (i < tot) {
+      const int sl = warp_miss_slot<NT, PPT>(mp, i);
+      if (base + i < cap)
+        q[base + i] = sl;
+      else
+        fn(sl);
+    }
+  }
+}
+
+// Take the queue's entries over all threads (entry i to warp i mod (NT/32), so that a burst
+// of entries from one warp is spread over the CTA), then empty it.  Call after the barrier that
+// ends the pass; contains a barrier when the queue is not empty.
+template <int NT, class Pol, class Fn>
+__device__ __forceinline__ void drain_queue(MarchSmem<Pol> &sm, int n1, Fn &&fn) {
+  const int n = min(*sm.qn, sm.queue_cap(n1));
+  if (n == 0) return;  // block-uniform
+  constexpr int W = NT / 32;
+  const int *q = sm.queue();
+  for (int i = (threadIdx.x & 31) * W + (threadIdx.x >> 5); i < n; i += NT) fn(q[i]);
+  __syncthreads();
+  if (threadIdx.x == 0) *sm.qn = 0;
+}
+
+// One ring's current-type deposit values (the source terms of Eqs. 4-7: J_z, chi, T, P, U and
+// the K share), its Gamma and (gamma/Gamma) psi', at cell c, offset f, momenta (u_r, u_theta).
+template <class Pol>
+__device__ __forceinline__ void current_values(const MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int sl,
+                                               int c, typename Pol::R f, typename Pol::R u_r, typename Pol::R u_t,
+                                               typename Pol::R dr, int *status, typename Pol::R (&v)[5],
+                                               typename Pol::R &ka, typename Pol::R &G, typename Pol::R &g) {
+  using R = typename Pol::R;
+  const R rp = ((R)c + f) * dr;
+  G = rs.G0[sl] + interp(sm.psi, c, f);
+  if (!(G > (R)0)) flag(status, ST_NUMERIC);
+  const R iG = (R)1 / G;
+  const R up2 = u_r * u_r + u_t * u_t;
+  const R gam = ((R)1 + up2 + G * G) * (R)0.5 * iG;
+  const R uz = gam - G;
+  const R a = u_r * iG;
+  const R dp = interp(sm.dpsi, c, f);
+  const R cent = rp > (R)0 ? u_t * u_t * iG / rp : (R)0;
+  g = gam * iG * dp;
+  const R w = rs.w[sl];
+  v[0] = -w * uz * iG;
+  v[1] = w * iG;
+  v[2] = w * a * a;
+  v[3] = w * (a * a * dp - g - cent) * iG;
+  v[4] = w * a * iG;
+  ka = w * a;
+}
+
+// The current deposit of one ring straight into the node arrays (shared atomics).
+template <class Pol>
+__device__ __forceinline__ void current_direct(MarchSmem<Pol> &sm, int c, typename Pol::R f,
+                                               const typename Pol::R (&v)[5], typename Pol::R ka) {
+  using Acc = typename Pol::Acc;
+  const typename Pol::R g0 = (typename Pol::R)1 - f;
+  Acc *arr[5] = {sm.jz, sm.chi, sm.T, sm.P, sm.U};
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    atomicAdd(&arr[q][c], (Acc)(v[q] * g0));
+    atomicAdd(&arr[q][c + 1], (Acc)(v[q] * f));
+  }
+  atomicAdd(&sm.K[c], (Acc)ka);
+}
+
+// A ring outside the window, at slot sl, through the position functor pos_slot: its values
+// formed again by the same arithmetic and deposited straight into the node arrays.
+template <class Pol, class PosSlot>
+__device__ __forceinline__ void current_miss(MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int sl,
+                                             typename Pol::R dr, int *status, PosSlot &&pos_slot) {
+  using R = typename Pol::R;
+  int c;
+  R f, u_r, u_t, v[5], ka, G, g;
+  pos_slot(sl, c, f, u_r, u_t);
+  current_values<Pol>(sm, rs, sl, c, f, u_r, u_t, dr, status, v, ka, G, g);
+  current_direct<Pol>(sm, c, f, v, ka);
+}
+
 // Pass B: ring quantities at the position given by pos(sl, c, f, u_r, u_theta) and the
 // current-type deposits.  Gam[p] = Gamma, gq[p] = (gamma/Gamma) psi'(r).  All threads call.
-template <class Pol, int NT, int PPT, bool kTrap = false, class Pos>
+// A ring outside the thread's window is only marked in the loop (an atomic there would order
+// every later ring's loads behind it); on_miss(mask) receives the thread's marks after the loop
+// (all lanes call it) and sees to those rings' deposits (current_miss).
+template <class Pol, int NT, int PPT, bool kTrap = false, class Pos, class OnMiss>
 __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int np,
-                                              int nr, typename Pol::R dr, int *status, Pos &&pos,
+                                              int nr, typename Pol::R dr, int *status, Pos &&pos, OnMiss &&on_miss,
                                               typename Pol::R (&Gam)[PPT], typename Pol::R (&gq)[PPT]) {
   using R = typename Pol::R;
   using Acc = typename Pol::Acc;
@@ -794,6 +994,7 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
   WindowAcc<R, 5> acc;
   acc.init(-8);
   R kw[3] = {(R)0, (R)0, (R)0};
+  unsigned miss = 0u;
 #pragma unroll
   for (int p = 0; p < PPT; ++p) {
     Gam[p] = (R)1;
@@ -809,38 +1010,21 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
       if (p == 0) acc.init(c);
       if constexpr (kTrap)
         if (rs.w[sl] == (R)0) continue;  // promoted to a beam particle: no longer in the plasma
-      const R rp = ((R)c + f) * dr;
-      const R G = rs.G0[sl] + interp(sm.psi, c, f);
-      if (!(G > (R)0)) flag(status, ST_NUMERIC);
-      const R iG = (R)1 / G;
-      const R up2 = u_r * u_r + u_t * u_t;
-      const R gam = ((R)1 + up2 + G * G) * (R)0.5 * iG;
-      const R uz = gam - G;
-      const R a = u_r * iG;
-      const R dp = interp(sm.dpsi, c, f);
-      const R cent = rp > (R)0 ? u_t * u_t * iG / rp : (R)0;
-      const R g = gam * iG * dp;
-      const R w = rs.w[sl];
-      const R v[5] = {-w * uz * iG, w * iG, w * a * a, w * (a * a * dp - g - cent) * iG, w * a * iG};
+      R v[5], ka, G, g;
+      current_values<Pol>(sm, rs, sl, c, f, u_r, u_t, dr, status, v, ka, G, g);
       if (acc.add(c, f, v)) {
         const int o = c - acc.c0;
-        kw[0] += o == 0 ? w * a : (R)0;
-        kw[1] += o == 1 ? w * a : (R)0;
-        kw[2] += o == 2 ? w * a : (R)0;
+        kw[0] += o == 0 ? ka : (R)0;
+        kw[1] += o == 1 ? ka : (R)0;
+        kw[2] += o == 2 ? ka : (R)0;
       } else {
-        const R g0 = (R)1 - f;
-        Acc *arr[5] = {sm.jz, sm.chi, sm.T, sm.P, sm.U};
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          atomicAdd(&arr[q][c], (Acc)(v[q] * g0));
-          atomicAdd(&arr[q][c + 1], (Acc)(v[q] * f));
-        }
-        atomicAdd(&sm.K[c], (Acc)(w * a));
+        miss |= 1u << p;
       }
       Gam[p] = G;
       gq[p] = g;
     }
   }
+  on_miss(miss);
   const WarpSeg seg(acc.c0);
   const int c = acc.c0;
   const bool emit = seg.is_tail && c >= 0;
@@ -1010,6 +1194,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
     sm.rho[m] = (typename Pol::Q)0;
     sm.jz[m] = sm.chi[m] = sm.T[m] = sm.P[m] = sm.U[m] = sm.K[m] = (Acc)0;
   }
+  if (tid == 0) *sm.qn = 0;
   // rings: thread t holds rings t*PPT .. t*PPT+PPT-1 (consecutive in radius), slot p*NT + t.
   // A ring's radius is a cell index c and an offset f in [0,1] (r = (c + f) dr), so its
   // position resolution is uniform over the box; moves are exact radial displacements.
@@ -1053,6 +1238,22 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
     R rr;
     move_ring<R>(c0, f0, r, dx, dy, uxh, ut, inv_dr, dR, nr, c, f, rr, u_r, u_t);
     return rr;
+  };
+  auto mid_slot = [&](int sl, int &c, R &f, R &u_r, R &u_t) { midpoint(sl, c, f, u_r, u_t); };
+  // out-of-window rings (queued in the passes, drained by the CTA after them)
+  auto cur_miss1 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, state_pos); };
+  auto cur_miss2 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, mid_slot); };
+  auto chg_miss_mid = [&](int sl) {
+    const R w = rs.w[sl];
+    if (kTrap && w == (R)0) return;  // a promoted ring deposits nothing
+    int c;
+    R f, u_r, u_t;
+    midpoint(sl, c, f, u_r, u_t);
+    ChargeWin<Pol>::direct(sm.rho, c, f, w);
+  };
+  auto chg_miss_full = [&](int sl) {  // the new positions are in the slots
+    const R w = rs.w[sl];
+    if (w != (R)0) ChargeWin<Pol>::direct(sm.rho, rs.c[sl], rs.f[sl], w);
   };
 
   // charge of the initial slice; it is also the ion background (the deposit of the
@@ -1098,7 +1299,9 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
     for (int i = tid; i < n1; i += NT) sm.rho[i] = (typename Pol::Q)0;
     {
       R Gs[PPT], gqs[PPT];
-      pass_currents<Pol, NT, PPT, kTrap>(sm, rs, np, nr, dR, d.status, state_pos, Gs, gqs);
+      pass_currents<Pol, NT, PPT, kTrap>(
+          sm, rs, np, nr, dR, d.status, state_pos,
+          [&](unsigned miss) { queue_misses<NT, PPT>(sm, n1, miss, cur_miss1); }, Gs, gqs);
 #pragma unroll
       for (int p = 0; p < PPT; ++p)
         if (tid * PPT + p < np) {
@@ -1106,9 +1309,10 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
           rs.F1[p * NT + tid] = gqs[p];
         }
       if constexpr (Hooks::kTraj) hk.template ring_state<NT, PPT>(k, rs, np);
-      if constexpr (kTrap) hk.template trap_rings<NT, PPT>(k, rs, np);
     }
     __syncthreads();
+    drain_queue<NT>(sm, n1, cur_miss1);
+    if constexpr (kTrap) hk.template trap_rings<NT, PPT>(k, rs, np);  // after every stage-1 deposit
     solve_fields<Pol, NT>(sm, geo, nbk, nbk, sm.wtot);  // P2
     __syncthreads();
     // P3: fields of slice k, then the move to the midpoint and its charge deposit
@@ -1126,6 +1330,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
     {
       ChargeWin<Pol> acc;
       acc.init(-8);
+      unsigned miss = 0u;
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
         if (tid * PPT + p < np) {
@@ -1145,12 +1350,14 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
           MF[p] = f;
           MUR[p] = u_r;
           MUT[p] = u_t;
-          add_charge<Pol>(sm, acc, p, c, f, rs.w[sl]);
+          add_charge_mark<Pol>(acc, p, c, f, rs.w[sl], miss);
         }
       }
+      queue_misses<NT, PPT>(sm, n1, miss, chg_miss_mid);
       flush_charge<Pol>(sm, acc, nr);
     }
     __syncthreads();
+    drain_queue<NT>(sm, n1, chg_miss_mid);
     // ======== stage 2 at xi_k + dxi/2 ========
     solve_psi<Pol, NT>(sm, geo, sm.wtot);  // P0
     __syncthreads();
@@ -1162,8 +1369,9 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
                                   u_r = MUR[p];
                                   u_t = MUT[p];
                                 },
-                                G2, F2);
+                                [&](unsigned miss) { queue_misses<NT, PPT>(sm, n1, miss, cur_miss2); }, G2, F2);
     __syncthreads();
+    drain_queue<NT>(sm, n1, cur_miss2);
     solve_fields<Pol, NT>(sm, geo, nbk, nbk1, sm.wtot);  // P2
     __syncthreads();
     // P3: full step from the slice-k state with the midpoint derivative, and the charge
@@ -1172,12 +1380,13 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
     {
       ChargeWin<Pol> acc;
       acc.init(-8);
+      unsigned miss = 0u;
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
         if (tid * PPT + p < np) {
           const int sl = p * NT + tid;
           if (kTrap && rs.w[sl] == (R)0) {  // a promoted ring: no move, no charge
-            add_charge<Pol>(sm, acc, p, rs.c[sl], rs.f[sl], (R)0);
+            add_charge_mark<Pol>(acc, p, rs.c[sl], rs.f[sl], (R)0, miss);
             continue;
           }
           const R F2b = F2[p] - interp(sm.bth, MC[p], MF[p]);  // at the midpoint
@@ -1206,12 +1415,14 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
           rs.c[sl] = cn;
           rs.f[sl] = fn;
           rs.ur[sl] = urn;
-          add_charge<Pol>(sm, acc, p, cn, fn, rs.w[sl]);
+          add_charge_mark<Pol>(acc, p, cn, fn, rs.w[sl], miss);
         }
       }
+      queue_misses<NT, PPT>(sm, n1, miss, chg_miss_full);
       flush_charge<Pol>(sm, acc, nr);
     }
     __syncthreads();
+    drain_queue<NT>(sm, n1, chg_miss_full);
   }
   hk.finish(sm);
 }

@@ -226,7 +226,10 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
       base = ch * SLOTS;
       const int npc = chunk_np(ch);
       R Gs[PPT], gqs[PPT];
-      pass_currents<Pol, NT, PPT>(sm, shifted(rs, base), npc, nr, dR, d.status, state_pos, Gs, gqs);
+      const RingSoA<R> rsc = shifted(rs, base);
+      pass_currents<Pol, NT, PPT>(sm, rsc, npc, nr, dR, d.status, state_pos, [&](unsigned miss) {
+        warp_misses<NT, PPT>(miss, [&](int sl) { current_miss<Pol>(sm, rsc, sl, dR, d.status, state_pos); });
+      }, Gs, gqs);
 #pragma unroll
       for (int p = 0; p < PPT; ++p)
         if (tid * PPT + p < npc) {
@@ -244,6 +247,7 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
       const int b0 = ch * SLOTS, npc = chunk_np(ch);
       ChargeWin<Pol> acc;
       acc.init(-8);
+      unsigned miss = 0u;
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
         if (tid * PPT + p < npc) {
@@ -253,9 +257,15 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
           R f, u_r, u_t;
           const R rr = midpoint_abs(sl, c, f, u_r, u_t);
           if (!(rr >= (R)0 && rr <= R_wall)) flag(d.status, ST_ESCAPE);
-          add_charge<Pol>(sm, acc, p, c, f, rs.w[sl]);
+          add_charge_mark<Pol>(acc, p, c, f, rs.w[sl], miss);
         }
       }
+      warp_misses<NT, PPT>(miss, [&](int sl) {
+        int c;
+        R f, u_r, u_t;
+        midpoint_abs(b0 + sl, c, f, u_r, u_t);
+        ChargeWin<Pol>::direct(sm.rho, c, f, rs.w[b0 + sl]);
+      });
       flush_charge<Pol>(sm, acc, nr);
     }
     __syncthreads();
@@ -267,9 +277,11 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
       base = ch * SLOTS;
       const int npc = chunk_np(ch);
       R Gs[PPT], gqs[PPT];
-      pass_currents<Pol, NT, PPT>(sm, shifted(rs, base), npc, nr, dR, d.status,
-                                  [&](int sl, int &c, R &f, R &u_r, R &u_t) { midpoint_abs(sl + base, c, f, u_r, u_t); },
-                                  Gs, gqs);
+      auto mid_chunk = [&](int sl, int &c, R &f, R &u_r, R &u_t) { midpoint_abs(sl + base, c, f, u_r, u_t); };
+      const RingSoA<R> rsc = shifted(rs, base);
+      pass_currents<Pol, NT, PPT>(sm, rsc, npc, nr, dR, d.status, mid_chunk, [&](unsigned miss) {
+        warp_misses<NT, PPT>(miss, [&](int sl) { current_miss<Pol>(sm, rsc, sl, dR, d.status, mid_chunk); });
+      }, Gs, gqs);
 #pragma unroll
       for (int p = 0; p < PPT; ++p)
         if (tid * PPT + p < npc) {
@@ -286,6 +298,7 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
       const int b0 = ch * SLOTS, npc = chunk_np(ch);
       ChargeWin<Pol> acc;
       acc.init(-8);
+      unsigned miss = 0u;
 #pragma unroll
       for (int p = 0; p < PPT; ++p) {
         if (tid * PPT + p < npc) {
@@ -319,9 +332,12 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
           rs.c[sl] = cn;
           rs.f[sl] = fn;
           rs.ur[sl] = urn;
-          add_charge<Pol>(sm, acc, p, cn, fn, rs.w[sl]);
+          add_charge_mark<Pol>(acc, p, cn, fn, rs.w[sl], miss);
         }
       }
+      warp_misses<NT, PPT>(miss, [&](int sl) {  // the new positions are in the slots
+        ChargeWin<Pol>::direct(sm.rho, rs.c[b0 + sl], rs.f[b0 + sl], rs.w[b0 + sl]);
+      });
       flush_charge<Pol>(sm, acc, nr);
     }
     __syncthreads();

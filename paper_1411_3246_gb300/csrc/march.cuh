@@ -386,9 +386,20 @@ __device__ __forceinline__ FF two_prod(float a, float b) {
   const float p = a * b;
   return FF{p, __fmaf_rn(a, b, -p)};
 }
-__device__ __forceinline__ long long ff_to_q(FF x) {
-  return __float2ll_rn(x.h * (float)kQScale) + __float2ll_rn(x.l * (float)kQScale);
+// x rounded to the nearest integer (ties to even), as a 64-bit integer, from 32-bit
+// instructions only (the 64-bit conversions run on the slow FP64 pipe): below 2^31 in
+// magnitude the 32-bit conversion rounds it; above, x has 24 significant bits and is an
+// integer, given exactly by its significand shifted by its exponent.  |x| < 2^63.
+__device__ __forceinline__ long long f2q(float x) {
+  const int b = __float_as_int(x);
+  int e = ((b >> 23) & 0xff) - 150;  // x = m 2^e
+  e = e < 0 ? 0 : (e > 40 ? 40 : e);
+  const long long m = (long long)((b & 0x7fffff) | 0x800000) << e;
+  const bool small = fabsf(x) < 2147483648.f;
+  const long long r = (long long)__float2int_rn(small ? x : 0.f);
+  return small ? r : (b < 0 ? -m : m);
 }
+__device__ __forceinline__ long long ff_to_q(FF x) { return f2q(x.h * (float)kQScale) + f2q(x.l * (float)kQScale); }
 template <class Q, class W>
 __device__ __forceinline__ W q_to_wide(Q d);
 template <>
@@ -399,11 +410,15 @@ __device__ __forceinline__ double q_to_wide<long long, double>(long long d) {
 }
 template <>
 __device__ __forceinline__ FF q_to_wide<long long, FF>(long long d) {
-  // exact split of the integer into two floats, then the exact power-of-two rescale
-  const float hi = (float)d;
-  const float lo = (float)(d - (long long)hi);
+  // the integer (|d| < 2^48) as the float-float sum of three exact floats (32-bit conversions
+  // only), i.e. its correctly rounded float and the exact remainder, then the exact
+  // power-of-two rescale
+  const int dh = (int)(d >> 32);
+  const unsigned dl = (unsigned)d;
+  const FF x = ff_add(ff_add(FF{(float)dh * 4294967296.f, 0.f}, FF{(float)(int)(dl >> 16) * 65536.f, 0.f}),
+                      FF{(float)(int)(dl & 0xffffu), 0.f});
   const float s = (float)(1.0 / kQScale);
-  return FF{hi * s, lo * s};
+  return FF{x.h * s, x.l * s};
 }
 
 // Parallel cyclic reduction (Hockney) on rows a_q x_{q-1} + b_q x_q + c_q x_{q+1} = d_q
@@ -770,7 +785,7 @@ struct ChargeWin<PolMixed> {
   __device__ __forceinline__ static void split(float f, float w, long long &qlo, long long &qhi) {
     const FF hi = two_prod(w, f);
     qhi = ff_to_q(hi);
-    qlo = __float2ll_rn(w * (float)kQScale) - qhi;
+    qlo = f2q(w * (float)kQScale) - qhi;
   }
   __device__ __forceinline__ bool add(int c, float f, float w) {
     const int o = c - c0;

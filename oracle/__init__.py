@@ -37,7 +37,8 @@ class OrcParams(C.Structure):
                 ("n_d", C.c_double), ("n_w", C.c_double), ("sigma_r", C.c_double),
                 ("sigma_zd", C.c_double), ("sigma_zw", C.c_double), ("xi_d", C.c_double),
                 ("xi_w", C.c_double), ("gamma_b", C.c_double), ("eps_n", C.c_double),
-                ("ds", C.c_double), ("n_beam", C.c_int64), ("n_drive", C.c_int64)]
+                ("ds", C.c_double), ("n_beam", C.c_int64), ("n_drive", C.c_int64),
+                ("geometry", C.c_int32), ("pad1", C.c_int32)]
 
 
 def build(force: bool = False) -> str:
@@ -112,7 +113,8 @@ def params(cfg) -> OrcParams:
     """OrcParams from a synth.WakeConfig (or any object with the same attributes)."""
     return OrcParams(cfg.nr, cfg.nxi, cfg.ppc, 0, cfg.rmax, cfg.ximax, cfg.u_th, cfg.n_d,
                      cfg.n_w, cfg.sigma_r, cfg.sigma_zd, cfg.sigma_zw, cfg.xi_d, cfg.xi_w,
-                     cfg.gamma_b, cfg.eps_n, cfg.ds, cfg.n_beam, cfg.n_drive)
+                     cfg.gamma_b, cfg.eps_n, cfg.ds, cfg.n_beam, cfg.n_drive,
+                     int(getattr(cfg, "geometry", 0)), 0)
 
 
 class OracleError(RuntimeError):

@@ -37,6 +37,13 @@
  *     (which carries the u_theta^2/(Gamma r) term of Eq. 4 exactly), l_z re-imposed after
  *     each step, specular reflection at r = R;
  *   - Boris push for the beam (Eqs. 8-11), d xi/dt written without cancellation.
+ * Slab geometry (geometry = 1; Sec. I: WAKE handles slab as well as cylindrical geometry) is
+ * read as the same model with d/dy = 0 in place of d/dtheta = 0: r becomes x >= 0 with the
+ * plane x = 0 a mirror plane (psi even, E_x and B_y odd), volumes per unit area (hats of
+ * width dx, halved at x = 0 and at the wall), lap_perp = d_x^2 and (1/r) d_r(r .) = d_x, the
+ * conserved transverse momentum u_y (in place of l_z) entering gamma only, so Eq. 4 loses its
+ * centrifugal term; a sheet that crosses x = 0 is replaced by its mirror image (x, u_x) ->
+ * (-x, -u_x).  The beam is a sheet beam at y = 0 (u_y = 0), its density folded onto x >= 0.
  */
 #include <math.h>
 #include <stdint.h>
@@ -55,25 +62,36 @@ typedef struct {
   double n_d, n_w, sigma_r, sigma_zd, sigma_zw, xi_d, xi_w;
   double gamma_b, eps_n, ds;
   int64_t n_beam, n_drive;
+  int32_t geometry, pad1; /* 0: cylindrical (r, xi); 1: slab (x, xi) */
 } orc_params;
+
+#define ORC_SLAB(p) ((p)->geometry == 1)
 
 /* ------------------------------------------------------------------------------------ */
 /* Grid helpers                                                                           */
 /* ------------------------------------------------------------------------------------ */
 
-/* Ring volume (per 2 pi) of the linear hat centred on node i: int hat_i(r) r dr. */
-static double node_volume(int i, int nr, double dr) {
+/* Ring volume (per 2 pi) of the linear hat centred on node i: int hat_i(r) r dr.  Slab: the
+ * hat's width on x >= 0, dx (dx/2 at x = 0 and at the wall). */
+static double node_volume(int i, int nr, double dr, int slab) {
+  if (slab) return (i == 0 || i == nr) ? 0.5 * dr : dr;
   if (i == 0) return dr * dr / 6.0;
   if (i == nr) return dr * ((double)nr * dr / 2.0 - dr / 6.0);
   return (double)i * dr * dr;
 }
 
 /* Fraction of hat m's ring volume that lies inside r_m: alpha_m = 1/2 - 1/(6m) for
- * 1 <= m < nr, 1 at the wall node (its hat has no outer half). */
-static double node_alpha(int m, int nr) {
+ * 1 <= m < nr, 1 at the wall node (its hat has no outer half).  Slab: 1/2, 1 at the wall. */
+static double node_alpha(int m, int nr, int slab) {
   if (m == nr) return 1.0;
+  if (slab) return 0.5;
   return 0.5 - 1.0 / (6.0 * (double)m);
 }
+
+/* The metric of Gauss's law at node m (1/r_m; slab 1) and the curvature of (1/r) d_r(r .)
+ * (1/r_m; slab 0). */
+static double node_metric(int m, double dr, int slab) { return slab ? 1.0 : 1.0 / (m * dr); }
+static double node_curv(int m, double dr, int slab) { return slab ? 0.0 : 1.0 / (m * dr); }
 
 /* Cell index c (0..nr-1) and fractional offset f in [0,1] of radius r. */
 static void locate(double r, double dr, int nr, int *c, double *f) {
@@ -109,12 +127,13 @@ void orc_gamma_uz(double uperp2, double Gam, double *gamma, double *uz) {
  * Warm plasma: ppc/2 ring positions per cell, each used by a mirrored pair of draws.
  * Ring weight (per 2 pi) w = r0 dr / ppc times the QS flux factor 1 - v_z0 = Gamma0/gamma0
  * (a QS macroparticle carries the flux of electrons through a xi = const plane).
- * u = u_th * normals; gamma0 = sqrt(1 + u^2); Gamma0 = gamma0 - u_z0; l = r0 u_theta0. */
+ * u = u_th * normals; gamma0 = sqrt(1 + u^2); Gamma0 = gamma0 - u_z0; l = r0 u_theta0.
+ * Slab: sheets with w = dx / ppc times the flux factor and l = u_y0 (conserved). */
 int orc_plasma_init(const orc_params *p, const double *normals, double *r0, double *ur0,
                     double *l, double *G0, double *w) {
   const int nr = p->nr, ppc = p->ppc;
   const double dr = p->rmax / nr;
-  const int warm = (p->u_th != 0.0);
+  const int warm = (p->u_th != 0.0), slab = ORC_SLAB(p);
   if (nr < 2 || ppc < 1 || (warm && (ppc % 2 != 0 || normals == NULL))) return ORC_EINVAL;
   for (int c = 0; c < nr; ++c) {
     for (int m = 0; m < ppc; ++m) {
@@ -133,9 +152,9 @@ int orc_plasma_init(const orc_params *p, const double *normals, double *r0, doub
       const double g0 = sqrt(1.0 + ur * ur + ut * ut + uz * uz);
       r0[j] = r;
       ur0[j] = ur;
-      l[j] = r * ut;
+      l[j] = slab ? ut : r * ut;
       G0[j] = g0 - uz;
-      w[j] = r * dr / (double)ppc * ((g0 - uz) / g0);
+      w[j] = (slab ? dr : r * dr) / (double)ppc * ((g0 - uz) / g0);
     }
   }
   return ORC_OK;
@@ -234,6 +253,9 @@ enum {
  *        (1/r) d_r(r B) = J_z at r = R (there E_z = 0 for all xi).  Central differences on
  *        the nodes, a half cell at the wall; diagonally dominant, solved by Thomas.
  *  E_r = B_theta - d psi/dr (the paper's E_r - B_theta = -d_r psi, Fig. 7).
+ *  Slab (x, xi): psi'_m = Phi_m, d_xi psi'_m = -((1 - alpha_m) K_{m-1} + alpha_m K_m)/dx,
+ *        and (d_x^2 - chi) B_y = d_x J_z + Q + d_x T with F0 = (gamma/Gamma) psi' (no
+ *        centrifugal term), B_y(0) = 0 (odd) and d_x B_y = J_z at the wall.
  *
  * Optional per-particle outputs: Gamma_j and the Cartesian radial force
  * Fc_j = (gamma/Gamma) psi'(r_j) - B(r_j) (Eq. 4 without its centrifugal term).
@@ -242,7 +264,7 @@ enum {
 int orc_solve_slice(const orc_params *p, int np, const double *r, const double *ur,
                     const double *ut, const double *G0, const double *w, const double *rho0,
                     const double *nb, double *out, double *Gam_out, double *Fc_out) {
-  const int nr = p->nr, n1 = nr + 1;
+  const int nr = p->nr, n1 = nr + 1, slab = ORC_SLAB(p);
   const double dr = p->rmax / nr;
   double *psi = out + SL_PSI * n1, *dpsi = out + SL_DPSI * n1, *ez = out + SL_EZ * n1;
   double *bth = out + SL_BTH * n1, *er = out + SL_ER * n1, *rho = out + SL_RHO * n1;
@@ -283,8 +305,8 @@ int orc_solve_slice(const orc_params *p, int np, const double *r, const double *
     dpsi[0] = 0.0;
     for (int m = 1; m <= nr; ++m) {
       C += rho[m - 1] - rho0[m - 1];
-      const double Phi = C + node_alpha(m, nr) * (rho[m] - rho0[m]);
-      dpsi[m] = Phi / (m * dr);
+      const double Phi = C + node_alpha(m, nr, slab) * (rho[m] - rho0[m]);
+      dpsi[m] = Phi * node_metric(m, dr, slab);
     }
     psi[nr] = 0.0;
     for (int m = nr - 1; m >= 0; --m) psi[m] = psi[m + 1] - 0.5 * dr * (dpsi[m] + dpsi[m + 1]);
@@ -307,7 +329,7 @@ int orc_solve_slice(const orc_params *p, int np, const double *r, const double *
     orc_gamma_uz(up2, Gam, &gam, &uz);
     const double a = ur[j] / Gam;
     const double dp = interp(dpsi, r[j], dr, nr);
-    const double cent = (r[j] > 0.0) ? ut[j] * ut[j] / (Gam * r[j]) : 0.0;
+    const double cent = (!slab && r[j] > 0.0) ? ut[j] * ut[j] / (Gam * r[j]) : 0.0;
     const double F0 = (gam / Gam) * dp + cent;
     Gp[j] = Gam;
     ga[j] = gam;
@@ -333,7 +355,7 @@ int orc_solve_slice(const orc_params *p, int np, const double *r, const double *
     K[c] += wj * a;
   }
   for (int i = 0; i <= nr; ++i) {
-    const double V = node_volume(i, nr, dr);
+    const double V = node_volume(i, nr, dr, slab);
     jz[i] = jz[i] / V - nb[i]; /* beam J_z = -n_b (v_b = c) */
     chi[i] /= V;
     T[i] /= V;
@@ -349,9 +371,9 @@ int orc_solve_slice(const orc_params *p, int np, const double *r, const double *
     double *dez = dph; /* d_xi psi' at the nodes */
     dez[0] = 0.0;
     for (int m = 1; m <= nr; ++m) {
-      const double al = node_alpha(m, nr);
+      const double al = node_alpha(m, nr, slab);
       const double Km = (m < nr) ? K[m] : 0.0;
-      dez[m] = -((1.0 - al) * K[m - 1] + al * Km) / dr / (m * dr);
+      dez[m] = -((1.0 - al) * K[m - 1] + al * Km) / dr * node_metric(m, dr, slab);
     }
     ez[nr] = 0.0;
     for (int m = nr - 1; m >= 0; --m) ez[m] = ez[m + 1] - 0.5 * dr * (dez[m] + dez[m + 1]);
@@ -364,19 +386,25 @@ int orc_solve_slice(const orc_params *p, int np, const double *r, const double *
     for (int i = 1; i < nr; ++i) {
       const int q = i - 1;
       const double rm = (i - 0.5), rp = (i + 0.5);
-      ta[q] = (i - 1) / rm * idr2;
-      tc[q] = (i + 1) / rp * idr2;
-      tb[q] = -(double)i * (1.0 / rp + 1.0 / rm) * idr2 - chi[i];
+      if (slab) { /* d_x^2 */
+        ta[q] = idr2;
+        tc[q] = idr2;
+        tb[q] = -2.0 * idr2 - chi[i];
+      } else {    /* d_r (1/r) d_r r */
+        ta[q] = (i - 1) / rm * idr2;
+        tc[q] = (i + 1) / rp * idr2;
+        tb[q] = -(double)i * (1.0 / rp + 1.0 / rm) * idr2 - chi[i];
+      }
       td[q] = (jz[i + 1] - jz[i - 1]) / (2.0 * dr) + Q[i] + (T[i + 1] - T[i - 1]) / (2.0 * dr) +
-              T[i] / (i * dr);
+              T[i] * node_curv(i, dr, slab);
     }
     {
       const int i = nr, q = nr - 1;
       const double rm = (i - 0.5);
-      ta[q] = 2.0 * (i - 1) / rm * idr2;
+      ta[q] = slab ? 2.0 * idr2 : 2.0 * (i - 1) / rm * idr2;
       tc[q] = 0.0;
-      tb[q] = -2.0 * (double)i / rm * idr2 - chi[i];
-      td[q] = Q[i] + (T[i] - T[i - 1]) / dr + T[i] / (i * dr) - (jz[i - 1] + jz[i]) / dr;
+      tb[q] = (slab ? -2.0 * idr2 : -2.0 * (double)i / rm * idr2) - chi[i];
+      td[q] = Q[i] + (T[i] - T[i - 1]) / dr + T[i] * node_curv(i, dr, slab) - (jz[i - 1] + jz[i]) / dr;
     }
     ta[0] = 0.0; /* B_0 = 0 */
     int s = orc_tridiag(nr, ta, tb, tc, td, bth + 1);
@@ -470,10 +498,12 @@ int orc_march_trap(const orc_params *p, const double *r0, const double *ur0, con
                    const double *G0, const double *w_in, const double *nb, double gamma_t, double *psi,
                    double *ez, double *er, double *bth, double *traj, double *trap, int max_trap,
                    int *ntrap) {
-  const int nr = p->nr, nxi = p->nxi, n1 = nr + 1;
+  const int nr = p->nr, nxi = p->nxi, n1 = nr + 1, slab = ORC_SLAB(p);
   const int np = p->nr * p->ppc;
   const double dr = p->rmax / nr, dxi = p->ximax / nxi, R = p->rmax;
   int status = ORC_OK;
+  *ntrap = 0;
+  if (slab && gamma_t > 0.0) return ORC_EINVAL; /* trapping is read for the cylinder only */
   double *r = (double *)malloc(sizeof(double) * np);
   double *ur = (double *)malloc(sizeof(double) * np);
   double *ut = (double *)malloc(sizeof(double) * np);
@@ -492,7 +522,6 @@ int orc_march_trap(const orc_params *p, const double *r0, const double *ur0, con
   double *nbh = (double *)malloc(sizeof(double) * n1);
   double *sl = (double *)malloc(sizeof(double) * SL_COUNT * n1);
   double *w = (double *)malloc(sizeof(double) * np); /* weights; zero once a ring is promoted */
-  *ntrap = 0;
   if (!r || !ur || !ut || !rh || !urh || !uth || !xh || !yh || !uxh || !uyh || !G1 || !F1 ||
       !G2 || !F2 || !rho0 || !nbh || !sl || !w) {
     status = ORC_ENOMEM;
@@ -506,7 +535,8 @@ int orc_march_trap(const orc_params *p, const double *r0, const double *ur0, con
   orc_deposit_charge(p, np, r0, w, rho0);
 
   for (int k = 0; k <= nxi; ++k) {
-    for (int j = 0; j < np; ++j) ut[j] = (r[j] > 0.0) ? l[j] / r[j] : 0.0;
+    /* u_theta = l_z / r (slab: the conserved u_y) */
+    for (int j = 0; j < np; ++j) ut[j] = slab ? l[j] : ((r[j] > 0.0) ? l[j] / r[j] : 0.0);
     /* stage 1 at xi_k */
     status = orc_solve_slice(p, np, r, ur, ut, G0, w, rho0, nb + (size_t)k * n1, sl, G1, F1);
     if (status != ORC_OK) goto done;
@@ -550,10 +580,13 @@ int orc_march_trap(const orc_params *p, const double *r0, const double *ur0, con
         uyh[j] = ut[j];
         continue;
       }
+      /* the frame's y axis: the azimuth (cylinder); in the slab u_y moves nothing that matters
+       * (d/dy = 0), so the frame is the x line and r = |x| mirrors a sheet that crosses x = 0 */
+      const double uyf = slab ? 0.0 : ut[j];
       xh[j] = r[j] + 0.5 * dxi * ur[j] / G1[j];
-      yh[j] = 0.5 * dxi * ut[j] / G1[j];
+      yh[j] = 0.5 * dxi * uyf / G1[j];
       uxh[j] = ur[j] + 0.5 * dxi * F1[j];
-      uyh[j] = ut[j];
+      uyh[j] = uyf;
       double rr = sqrt(xh[j] * xh[j] + yh[j] * yh[j]);
       double urr, utt;
       if (rr > 0.0) {
@@ -573,7 +606,7 @@ int orc_march_trap(const orc_params *p, const double *r0, const double *ur0, con
       }
       rh[j] = rr;
       urh[j] = urr;
-      uth[j] = utt;
+      uth[j] = slab ? l[j] : utt;
     }
     for (int i = 0; i < n1; ++i) nbh[i] = 0.5 * (nb[(size_t)k * n1 + i] + nb[(size_t)(k + 1) * n1 + i]);
     /* stage 2 at xi_k + dxi/2 */
@@ -591,7 +624,7 @@ int orc_march_trap(const orc_params *p, const double *r0, const double *ur0, con
       const double xn = r[j] + dxi * uxh[j] / G2[j];
       const double yn = dxi * uyh[j] / G2[j];
       const double uxn = ur[j] + dxi * F2[j] * ex;
-      const double uyn = ut[j] + dxi * F2[j] * ey;
+      const double uyn = (slab ? 0.0 : ut[j]) + dxi * F2[j] * ey;
       double rn = sqrt(xn * xn + yn * yn);
       double urn = (rn > 0.0) ? (xn * uxn + yn * uyn) / rn : sqrt(uxn * uxn + uyn * uyn);
       if (rn > R) {
@@ -637,12 +670,16 @@ done:
 void orc_beam_weights(const orc_params *p, double *wd, double *ww) {
   const double s2pi = sqrt(2.0 * 3.14159265358979323846);
   const int64_t nw = p->n_beam - p->n_drive;
-  *wd = (p->n_drive > 0) ? p->n_d * s2pi * p->sigma_r * p->sigma_r * p->sigma_zd / (double)p->n_drive : 0.0;
-  *ww = (nw > 0) ? p->n_w * s2pi * p->sigma_r * p->sigma_r * p->sigma_zw / (double)nw : 0.0;
+  /* transverse integral of exp(-r^2/2 sigma^2): r dr gives sigma^2; the slab's x >= 0 half,
+   * on which the folded sheet beam lies, gives sigma sqrt(2 pi) / 2 */
+  const double tr = ORC_SLAB(p) ? 0.5 * s2pi * p->sigma_r : p->sigma_r * p->sigma_r;
+  *wd = (p->n_drive > 0) ? p->n_d * s2pi * tr * p->sigma_zd / (double)p->n_drive : 0.0;
+  *ww = (nw > 0) ? p->n_w * s2pi * tr * p->sigma_zw / (double)nw : 0.0;
 }
 
 /* Beam state from normals (5 x n): x = sigma_r n0, y = sigma_r n1, u_x = (eps_n/sigma_r) n2,
  * u_y = (eps_n/sigma_r) n3, xi = xi_c + sigma_z n4 (drive: first n_drive), u_z = gamma_b.
+ * Slab: a sheet beam, y = u_y = 0 (rows 1 and 3 unused).
  * A particle outside 0 <= xi < L or r >= R is marked lost. */
 void orc_beam_init(const orc_params *p, const double *normals, double *x, double *y,
                    double *xi, double *ux, double *uy, double *uz, uint8_t *lost) {
@@ -650,10 +687,11 @@ void orc_beam_init(const orc_params *p, const double *normals, double *x, double
   const double su = p->eps_n / p->sigma_r;
   for (int64_t j = 0; j < n; ++j) {
     const int drive = j < p->n_drive;
+    const int slab = ORC_SLAB(p);
     x[j] = p->sigma_r * normals[0 * n + j];
-    y[j] = p->sigma_r * normals[1 * n + j];
+    y[j] = slab ? 0.0 : p->sigma_r * normals[1 * n + j];
     ux[j] = su * normals[2 * n + j];
-    uy[j] = su * normals[3 * n + j];
+    uy[j] = slab ? 0.0 : su * normals[3 * n + j];
     xi[j] = drive ? p->xi_d + p->sigma_zd * normals[4 * n + j] : p->xi_w + p->sigma_zw * normals[4 * n + j];
     uz[j] = p->gamma_b;
     const double r = sqrt(x[j] * x[j] + y[j] * y[j]);
@@ -693,7 +731,7 @@ void orc_beam_deposit_w(const orc_params *p, const double *x, const double *y, c
   }
   for (int k = 0; k <= nxi; ++k) {
     const double vx = (k == 0 || k == nxi) ? 0.5 * dxi : dxi;
-    for (int i = 0; i <= nr; ++i) nb[(size_t)k * n1 + i] /= node_volume(i, nr, dr) * vx;
+    for (int i = 0; i <= nr; ++i) nb[(size_t)k * n1 + i] /= node_volume(i, nr, dr, ORC_SLAB(p)) * vx;
   }
 }
 
@@ -864,7 +902,7 @@ void orc_beam_deposit_wt(const orc_params *p, int64_t n, const double *x, const 
   }
   for (int k = 0; k <= nxi; ++k) {
     const double vx = (k == 0 || k == nxi) ? 0.5 * dxi : dxi;
-    for (int i = 0; i <= nr; ++i) nb[(size_t)k * n1 + i] /= node_volume(i, nr, dr) * vx;
+    for (int i = 0; i <= nr; ++i) nb[(size_t)k * n1 + i] /= node_volume(i, nr, dr, ORC_SLAB(p)) * vx;
   }
 }
 

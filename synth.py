@@ -51,6 +51,7 @@ class WakeConfig:
     ds: float = 5.0         # beam time step
     n_steps: int = 0        # beam steps in one run
     seed: int = SEED_BASE
+    geometry: int = 0       # 0: cylindrical (r, xi); 1: slab (x, xi), mirror plane x = 0
 
     @property
     def np_plasma(self) -> int:
@@ -76,6 +77,24 @@ def config_linear(nr=128, nxi=256, n0=0.1) -> WakeConfig:
     (linear regime)."""
     return WakeConfig(nr=nr, nxi=nxi, ppc=4, rmax=6.0, ximax=10.0, u_th=0.0, n_d=n0, n_w=0.0,
                       sigma_r=0.5, sigma_zd=1.0, xi_d=4.0, seed=SEED_BASE + 1)
+
+
+def config_slab_linear(nr=128, nxi=256, n0=0.1) -> WakeConfig:
+    """Slab geometry (x, xi), mirror plane x = 0, conducting wall at x = 6: the linear case's
+    grid and sheet driver n_b = n0 exp(-x^2/2 sigma^2) f(xi), sigma = 0.5, sigma_z = 1."""
+    cfg = config_linear(nr=nr, nxi=nxi, n0=n0)
+    cfg.geometry = 1
+    cfg.seed = SEED_BASE + 21
+    return cfg
+
+
+def config_slab_blowout(n_beam=1 << 20, n_steps=200, nr=512, nxi=2048) -> WakeConfig:
+    """The blowout workload in slab geometry: the same box, warm plasma and two sheet bunches
+    (drive n_b/n_p = 8 peaked on the mirror plane x = 0, witness 4.5 behind)."""
+    cfg = config_blowout(n_beam=n_beam, n_steps=n_steps, nr=nr, nxi=nxi)
+    cfg.geometry = 1
+    cfg.seed = SEED_BASE + 22
+    return cfg
 
 
 def config_blowout(n_beam=1 << 20, n_steps=200, nr=512, nxi=2048) -> WakeConfig:

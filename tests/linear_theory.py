@@ -58,3 +58,34 @@ def linear_fields(cfg):
     n0 = cfg.n_d
     return {"psi": n0 * np.outer(g, H), "ez": n0 * np.outer(gp, H),
             "bth": n0 * np.outer(f, Hp), "er": n0 * np.outer(f - g, Hp)}
+
+
+# ---------------------------------------------------------------------------------------
+# slab geometry (x, xi), mirror plane x = 0, conducting wall at x = L
+# ---------------------------------------------------------------------------------------
+# (d_x^2 - 1) H = -rho on 0 <= x <= L with H'(0) = 0 (even) and H(L) = 0:
+#   H(x) = int_0^L G(x, s) rho(s) ds,  G = cosh(x<) sinh(L - x>) / cosh(L),
+# and the same linear fields psi = n0 g H, E_z = n0 g' H, B_y = n0 f H', E_x = n0 (f - g) H'.
+def slab_profiles(x_nodes, sigma, L):
+    rho = lambda s: np.exp(-s * s / (2 * sigma ** 2))
+    cL = np.cosh(L)
+    H = np.zeros(len(x_nodes))
+    Hp = np.zeros(len(x_nodes))
+    opts = dict(epsabs=1e-14, epsrel=1e-12, limit=400)
+    for n, x in enumerate(x_nodes):
+        inner = integrate.quad(lambda s: np.cosh(s) * rho(s), 0, x, **opts)[0] if x > 0 else 0.0   # s < x
+        outer = integrate.quad(lambda s: np.sinh(L - s) * rho(s), x, L, **opts)[0] if x < L else 0.0  # s > x
+        H[n] = (np.sinh(L - x) * inner + np.cosh(x) * outer) / cL
+        Hp[n] = (-np.cosh(L - x) * inner + np.sinh(x) * outer) / cL
+    return H, Hp
+
+
+def slab_linear_fields(cfg):
+    """psi, ez, bth (B_y), er (E_x) on the (nxi+1) x (nr+1) nodes of a slab cfg."""
+    x = np.arange(cfg.nr + 1) * (cfg.rmax / cfg.nr)
+    xi = np.arange(cfg.nxi + 1) * (cfg.ximax / cfg.nxi)
+    H, Hp = slab_profiles(x, cfg.sigma_r, cfg.rmax)
+    f, g, gp = longitudinal_profiles(xi, cfg.xi_d, cfg.sigma_zd)
+    n0 = cfg.n_d
+    return {"psi": n0 * np.outer(g, H), "ez": n0 * np.outer(gp, H),
+            "bth": n0 * np.outer(f, Hp), "er": n0 * np.outer(f - g, Hp)}

@@ -65,7 +65,25 @@ typedef struct wake_params {
   double n_d, n_w, sigma_r, sigma_zd, sigma_zw, xi_d, xi_w;
   double gamma_b, eps_n, ds;
   int64_t n_beam, n_drive;
+  int32_t geometry; /* WAKE_CYLINDRICAL (0) or WAKE_SLAB (1) */
+  int32_t reserved; /* 0 */
 } wake_params;
+
+/*
+ * Geometry (Sec. I: WAKE handles cylindrical and slab geometry).  WAKE_CYLINDRICAL is the
+ * (r, xi) model of Sec. II.A.  WAKE_SLAB reads it with d/dy = 0 in place of d/dtheta = 0: the
+ * transverse coordinate is x >= 0 with a mirror plane at x = 0 (psi and E_z even, E_x and B_y
+ * odd) and a conducting wall at x = rmax; volumes are per unit area (hat widths dx, halved at
+ * x = 0 and at the wall); lap_perp = d_x^2 and Eq. 6 reads d_x B_y = d_xi^2 psi + J_z; the
+ * plasma particles are sheets whose conserved u_y enters gamma only (Eq. 4 has no centrifugal
+ * term); the beam is a sheet beam at y = u_y = 0, its density folded onto x >= 0 with the
+ * bunch weight n sqrt(2 pi) sigma_z * sigma_r sqrt(2 pi)/2 (the half-slab integral).  The
+ * fields keep their names: er is E_x, bth is B_y.  Slab simulations use the shared-memory
+ * march forms only (nr*ppc and nr within one CTA's shared memory, e.g. nr = 512 with 8192
+ * rings in FP64 or 4096 in the mixed form) and have no trapping and no adjoint.
+ */
+#define WAKE_CYLINDRICAL 0
+#define WAKE_SLAB 1
 
 typedef struct wake_sim wake_sim; /* opaque handle: n_sims independent simulations */
 
@@ -74,7 +92,8 @@ typedef struct wake_sim wake_sim; /* opaque handle: n_sims independent simulatio
  * CUDA stream `stream` (a cudaStream_t; NULL = legacy default stream).  Allocates all
  * scratch: plasma rings, beam state, the beam-density and field grids.  A simulation with
  * n_beam == 0 gets the frozen analytic driver of Eq. 12 on its nodes.
- * Errors: WAKE_EINVAL (sizes out of range: 2 <= nxi, 1 <= ppc; FP64 and mixed 2 <= nr <= 2048
+ * Errors: WAKE_EINVAL (geometry not 0 or 1, or a slab simulation too large for the shared-memory
+ * march; sizes out of range: 2 <= nxi, 1 <= ppc; FP64 and mixed 2 <= nr <= 2048
  * and nr*ppc <= 65536 (beyond 1,024 cells or 8,192 rings the FP64 form marches in its wide
  * form, node arrays in global memory, far slower); WAKE_MIXED64 2 <= nr <= 1024, nr*ppc <= 8192
  * and within one CTA's shared memory (about 4,500 rings at nr = 512); precision mismatch),
@@ -106,7 +125,8 @@ int wake_load_beam(wake_sim *s, int sim, const double *normals);
  * weights per 2 pi (NULL: the Eq. 12 bunch weights, as wake_load_beam gives them); tag a
  * device array of n_beam bytes, nonzero for witness particles (NULL: the particles from
  * n_drive on).  Particles outside 0 <= xi < ximax, r < rmax start lost.  Replaces the beam
- * state; wake_get_beam returns particles in this order.
+ * state; wake_get_beam returns particles in this order.  Slab geometry: y and u_y are taken
+ * as 0 (a sheet beam).
  */
 int wake_set_beam(wake_sim *s, int sim, const double *xyz, const double *w, const uint8_t *tag);
 
@@ -205,8 +225,8 @@ int wake_step_kernel_ms(wake_sim *s, float *ms);
  * dropped.  The same plasma is marched every step, so a ring may be promoted at every step.
  *   gamma_t   threshold (> 0; 0 keeps the arrays but promotes nothing)
  *   capacity  promoted particles the beam can hold (>= 0)
- * Needs a handle of one simulation with a particle beam, FP64 or WAKE_MIXED, that fits one
- * 512-thread march CTA; call it before wake_load_beam / wake_set_beam (the beam's arrays are
+ * Needs a handle of one simulation with a particle beam, FP64 or WAKE_MIXED, cylindrical, that
+ * fits one 512-thread march CTA; call it before wake_load_beam / wake_set_beam (the beam's arrays are
  * reallocated).  With trapping on, wake_step takes the separate calls (deposit, march, push).
  * Errors: WAKE_EINVAL, WAKE_ESTATE (beam already loaded), WAKE_ENOMEM, WAKE_ECUDA.
  */
@@ -258,7 +278,8 @@ int wake_status(wake_sim *s, int sim);
  *           n_beam and n_drive (the bunch macroparticle weights, as wake_beam_deposit takes
  *           them); precision is ignored (FP64 throughout)
  *   xyz     device, 6 x n_beam doubles in wake_get_beam's layout (rows x, y, xi, u_x, u_y,
- *           u_z; only x, y and xi are read); the first n_drive particles are the drive bunch
+ *           u_z; only x, y and xi are read, y not in the slab geometry); the first n_drive
+ *           particles are the drive bunch
  *   lost    device, n_beam bytes, nonzero = lost (NULL: none lost); a particle outside
  *           0 <= xi < ximax, r < rmax also counts as lost
  *   stream  a cudaStream_t of the current device (NULL = legacy default stream); the call is
@@ -304,7 +325,8 @@ int wake_beam_deposit_noalloc(const wake_params *p, const double *xyz, const uin
  * up returns WAKE_ETIMEOUT).
  *
  * wake_adjoint_init: p gives the grid, box, bunches (n_d, sigma_r, sigma_zw, xi_d, gamma_b,
- * eps_n, ds, n_beam, n_drive; the theta entries of p are ignored).  Needs nr <= 256, an even
+ * eps_n, ds, n_beam, n_drive; the theta entries of p are ignored).  Cylindrical geometry
+ * only.  Needs nr <= 256, an even
  * ppc, 0 < n_drive < n_beam, 0 <= nbins <= 1024.  Allocates everything (beam states, densities
  * and fields of every step: about (nsteps + 1) x 49 x n_beam + nsteps x 32 x (Nxi+1)(Nr+1)
  * bytes, plus the tape above and per-CTA scratch).

@@ -609,6 +609,7 @@ int wake_adjoint_init(const wake_params *p, int nsteps, int nbins, void *stream,
   if (!p || !out) return afail(WAKE_EINVAL, "wake_adjoint_init: null argument");
   *out = nullptr;
   if (p->nr < 2 || p->nr > 256) return afail(WAKE_EINVAL, "wake_adjoint_init: need 2 <= nr <= 256");
+  if (p->geometry != WAKE_CYLINDRICAL) return afail(WAKE_EINVAL, "wake_adjoint_init: the adjoint is cylindrical only");
   if (p->nxi < 2 || p->nxi > (1 << 16)) return afail(WAKE_EINVAL, "wake_adjoint_init: need 2 <= nxi <= 65536");
   if (p->ppc < 2 || p->ppc % 2 || (int64_t)p->nr * p->ppc > 8192)
     return afail(WAKE_EINVAL, "wake_adjoint_init: need an even ppc and nr*ppc <= 8192 (warm plasma)");

@@ -28,6 +28,7 @@ struct BeamDesc {
   void *nb;                // beam-density grid (G)
   const void *er, *ez, *bth;  // fields of the last march (G)
   double *diag;            // 5 accumulators
+  int slab;                // slab geometry: a sheet beam at y = u_y = 0, folded onto x >= 0
 };
 
 struct BunchInit {
@@ -48,18 +49,19 @@ __device__ __forceinline__ void clear_tail(const BeamDesc &b) {
   }
 }
 
-// Eq. 12 bunches from standard normals (rows x, y, u_x, u_y, xi of a 5 x n array).
+// Eq. 12 bunches from standard normals (rows x, y, u_x, u_y, xi of a 5 x n array).  Slab: a
+// sheet beam, y = u_y = 0 (rows 1 and 3 unused).
 template <class BT>
 __global__ void beam_init_kernel(BeamDesc b, BunchInit q, const double *__restrict__ nm) {
   const double su = q.eps_n / q.sigma_r;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
     const bool drive = j < b.n_drive;
-    const double x = q.sigma_r * nm[j], y = q.sigma_r * nm[b.n + j];
+    const double x = q.sigma_r * nm[j], y = b.slab ? 0.0 : q.sigma_r * nm[b.n + j];
     const double xi = drive ? q.xi_d + q.sigma_zd * nm[4 * b.n + j] : q.xi_w + q.sigma_zw * nm[4 * b.n + j];
     ((BT *)b.x)[j] = (BT)x;
     ((BT *)b.y)[j] = (BT)y;
     ((BT *)b.ux)[j] = (BT)(su * nm[2 * b.n + j]);
-    ((BT *)b.uy)[j] = (BT)(su * nm[3 * b.n + j]);
+    ((BT *)b.uy)[j] = (BT)(b.slab ? 0.0 : su * nm[3 * b.n + j]);
     b.xi[j] = xi;
     b.uz[j] = q.gamma_b;
     const double r = sqrt(x * x + y * y);
@@ -72,17 +74,17 @@ __global__ void beam_init_kernel(BeamDesc b, BunchInit q, const double *__restri
 
 // A beam given by the caller: xyz rows x, y, xi, u_x, u_y, u_z (6 x n, FP64), weights w (NULL:
 // the Eq. 12 bunch weights), witness tags (NULL: the particles from n_drive on).  Particles
-// outside 0 <= xi < ximax, r < rmax are lost.
+// outside 0 <= xi < ximax, r < rmax are lost.  Slab: y and u_y are taken as 0.
 template <class BT>
 __global__ void beam_set_kernel(BeamDesc b, const double *__restrict__ xyz, const double *__restrict__ w,
                                 const uint8_t *__restrict__ tag) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n; j += (int64_t)gridDim.x * blockDim.x) {
     const bool witness = tag ? tag[j] != 0 : j >= b.n_drive;
-    const double x = xyz[j], y = xyz[b.n + j], xi = xyz[2 * b.n + j];
+    const double x = xyz[j], y = b.slab ? 0.0 : xyz[b.n + j], xi = xyz[2 * b.n + j];
     ((BT *)b.x)[j] = (BT)x;
     ((BT *)b.y)[j] = (BT)y;
     ((BT *)b.ux)[j] = (BT)xyz[3 * b.n + j];
-    ((BT *)b.uy)[j] = (BT)xyz[4 * b.n + j];
+    ((BT *)b.uy)[j] = (BT)(b.slab ? 0.0 : xyz[4 * b.n + j]);
     b.xi[j] = xi;
     b.uz[j] = xyz[5 * b.n + j];
     const double r = sqrt(x * x + y * y);
@@ -127,19 +129,19 @@ __global__ void beam_deposit_kernel(BeamDesc b) {
 
 // Divide the raw deposit by the hats' volumes: V_i in r, dxi in xi (dxi/2 at both ends).
 template <class G>
-__device__ __forceinline__ void normalize_range(G *nb, int nr, int nxi, double dr, double dxi, int64_t t0,
+__device__ __forceinline__ void normalize_range(G *nb, int nr, int nxi, double dr, double dxi, int slab, int64_t t0,
                                                 int64_t stride) {
   const int n1 = nr + 1;
   const int64_t tot = (int64_t)(nxi + 1) * n1;
   for (int64_t t = t0; t < tot; t += stride) {
     const int k = (int)(t / n1), i = (int)(t % n1);
     const double vx = (k == 0 || k == nxi) ? 0.5 * dxi : dxi;
-    nb[t] = (G)((double)nb[t] / (node_volume(i, nr, dr) * vx));
+    nb[t] = (G)((double)nb[t] / (node_volume(i, nr, dr, slab != 0) * vx));
   }
 }
 template <class G>
-__global__ void nb_normalize_kernel(G *nb, int nr, int nxi, double dr, double dxi) {
-  normalize_range<G>(nb, nr, nxi, dr, dxi, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+__global__ void nb_normalize_kernel(G *nb, int nr, int nxi, double dr, double dxi, int slab) {
+  normalize_range<G>(nb, nr, nxi, dr, dxi, slab, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
                      (int64_t)gridDim.x * blockDim.x);
 }
 
@@ -243,7 +245,7 @@ template <class G>
 __global__ void nb_normalize_batch_kernel(const BeamDesc *bs) {
   const BeamDesc &b = bs[blockIdx.y];
   if (b.n == 0) return;
-  normalize_range<G>((G *)b.nb, b.nr, b.nxi, b.dr, b.dxi, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+  normalize_range<G>((G *)b.nb, b.nr, b.nxi, b.dr, b.dxi, b.slab, blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
                      (int64_t)gridDim.x * blockDim.x);
 }
 template <class BT, class G>
@@ -282,9 +284,10 @@ __global__ void beam_diag_kernel(BeamDesc b) {
 // Initial plasma slice (Sec. II.A): cell c, ring m.  Cold: ppc radii (c + (m+1/2)/ppc) dr;
 // warm: ppc/2 radii, each shared by a mirrored pair of draws.  u = u_th * normals,
 // gamma0 = sqrt(1 + u^2), Gamma0 = gamma0 - u_z0, l_z = r u_theta0,
-// w = r dr/ppc * Gamma0/gamma0 (the quasi-static flux factor 1 - v_z0).
+// w = r dr/ppc * Gamma0/gamma0 (the quasi-static flux factor 1 - v_z0).  Slab: sheets,
+// w = dx/ppc * Gamma0/gamma0, and lz holds the conserved u_y0.
 static __global__ void plasma_init_kernel(int nr, int ppc, double dr, double u_th, const double *__restrict__ nm,
-                                   double *r0, double *ur0, double *lz, double *G0, double *w) {
+                                   double *r0, double *ur0, double *lz, double *G0, double *w, int slab) {
   const int np = nr * ppc;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += gridDim.x * blockDim.x) {
     const int c = j / ppc, m = j % ppc;
@@ -300,9 +303,9 @@ static __global__ void plasma_init_kernel(int nr, int ppc, double dr, double u_t
     const double g0 = sqrt(1.0 + ur * ur + ut * ut + uz * uz);
     r0[j] = r;
     ur0[j] = ur;
-    lz[j] = r * ut;
+    lz[j] = slab ? ut : r * ut;
     G0[j] = g0 - uz;
-    w[j] = r * dr / (double)ppc * ((g0 - uz) / g0);
+    w[j] = (slab ? dr : r * dr) / (double)ppc * ((g0 - uz) / g0);
   }
 }
 

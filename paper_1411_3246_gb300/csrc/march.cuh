@@ -309,14 +309,21 @@ struct NodeGeo {
   const R *t_invR, *t_invV, *t_alpha, *t_ga, *t_gb, *t_gc;
   int nr;
   R dr, inv_dr, inv_dr2, dr_6, v_wall_inv;
-  __device__ __forceinline__ R invR(int m) const { return t_invR[m]; }
+  int slab;  // slab geometry (x, xi): lap_perp = d_x^2, hat widths per unit area
+  // the metric of Gauss's law at node m, 1/r_m (slab 1), and the curvature term of
+  // (1/r) d_r(r .), 1/r_m (slab 0)
+  __device__ __forceinline__ R metric(int m) const { return slab ? (R)1 : t_invR[m]; }
+  __device__ __forceinline__ R curv(int m) const { return slab ? (R)0 : t_invR[m]; }
   __device__ __forceinline__ R invV(int m) const {
     if (Pol::kTables) return t_invV[m];
-    // V_m = m dr^2 in the interior; dr^2/6 on the axis; dr^2 (nr/2 - 1/6) at the wall
+    // V_m = m dr^2 in the interior; dr^2/6 on the axis; dr^2 (nr/2 - 1/6) at the wall.  Slab:
+    // dx, dx/2 on the mirror plane and at the wall
+    if (slab) return (m == 0 || m == nr) ? (R)2 * inv_dr : inv_dr;
     return m == 0 ? (R)6 * inv_dr2 : (m == nr ? inv_dr2 * v_wall_inv : t_invR[m] * inv_dr);
   }
   __device__ __forceinline__ R alpha(int m) const {
     if (Pol::kTables) return t_alpha[m];
+    if (slab) return m == 0 ? (R)0 : (m == nr ? (R)1 : (R)0.5);
     return m == 0 ? (R)0 : (m == nr ? (R)1 : (R)0.5 - t_invR[m] * dr_6);
   }
   // row q (node i = q + 1): a_q x_{q-1} + b_q x_q + c_q x_{q+1}, without the -chi shift, and
@@ -332,6 +339,12 @@ struct NodeGeo {
       return;
     }
     const int i = q + 1;
+    if (slab) {  // d_x^2: a row sum of zero in the interior, the margin is chi alone
+      a = q == 0 ? (R)0 : (i < nr ? inv_dr2 : (R)2 * inv_dr2);
+      c = i < nr ? inv_dr2 : (R)0;
+      sum = q == 0 ? (i < nr ? -inv_dr2 : (R)-2 * inv_dr2) : (R)0;
+      return;
+    }
     const R ihm = t_ga[i - 1], ihp = t_ga[i];  // 1/(i - 1/2), 1/(i + 1/2)
     if (i < nr) {
       a = q == 0 ? (R)0 : (R)(i - 1) * ihm * inv_dr2;
@@ -346,18 +359,22 @@ struct NodeGeo {
 };
 
 template <class Pol, int NT>
-__device__ __forceinline__ void fill_tables(MarchSmem<Pol> &sm, int nr, double dr) {
+__device__ __forceinline__ void fill_tables(MarchSmem<Pol> &sm, int nr, double dr, bool slab) {
   using R = typename Pol::N;
   for (int m = threadIdx.x; m <= nr; m += NT) {
     sm.invR[m] = (R)(m > 0 ? 1.0 / ((double)m * dr) : 0.0);
     if constexpr (Pol::kTables) {
-      sm.invV[m] = (R)(1.0 / node_volume(m, nr, dr));
-      sm.alpha[m] = (R)(m > 0 ? node_alpha(m, nr) : 0.0);
+      sm.invV[m] = (R)(1.0 / node_volume(m, nr, dr, slab));
+      sm.alpha[m] = (R)(m > 0 ? node_alpha(m, nr, slab) : 0.0);
       if (m < nr) {
         const int i = m + 1;
         const double idr2 = 1.0 / (dr * dr), rm = i - 0.5, rp = i + 0.5;
         double a, b, c;
-        if (i < nr) {
+        if (slab) {  // d_x^2, a half cell at the wall
+          a = i < nr ? idr2 : 2.0 * idr2;
+          c = i < nr ? idr2 : 0.0;
+          b = -2.0 * idr2;
+        } else if (i < nr) {
           a = (i - 1) / rm * idr2;
           c = (i + 1) / rp * idr2;
           b = -(double)i * (1.0 / rp + 1.0 / rm) * idr2;
@@ -569,7 +586,7 @@ __device__ __forceinline__ void solve_psi(MarchSmem<Pol> &sm, const NodeGeo<Pol>
         R dp = (R)0;
         if (m > 0) {
           const R v = (R)wide_value(q_to_wide<typename Pol::Q, W>(sm.rho[m] - sm.rho0[m]));
-          dp = (R)wide_value(wide_add(incl, wide_of<W, R>(-((R)1 - geo.alpha(m)) * v))) * geo.invR(m);
+          dp = (R)wide_value(wide_add(incl, wide_of<W, R>(-((R)1 - geo.alpha(m)) * v))) * geo.metric(m);
         }
         sm.dpsi[m] = dp;
       });
@@ -594,7 +611,7 @@ __device__ __forceinline__ void solve_fields(MarchSmem<Pol> &sm, const NodeGeo<P
     if (m == 0) return (R)0;
     const R al = geo.alpha(m);
     const R Km = m < nr ? (R)sm.K[m] : (R)0;
-    return -(((R)1 - al) * (R)sm.K[m - 1] + al * Km) * geo.invR(m) * inv_dr;
+    return -(((R)1 - al) * (R)sm.K[m - 1] + al * Km) * geo.metric(m) * inv_dr;
   };
   // E_z: inward trapezoid sum from E_z(R) = 0
   block_scan_fused<NT, Pol::kScanE, true, W>(
@@ -615,9 +632,9 @@ __device__ __forceinline__ void solve_fields(MarchSmem<Pol> &sm, const NodeGeo<P
     R rhs;
     if (i < nr)
       rhs = (jz_node(i + 1) - jz_node(i - 1)) * i2dr + Qi + (dens(sm.T, i + 1) - dens(sm.T, i - 1)) * i2dr +
-            Ti * geo.invR(i);
+            Ti * geo.curv(i);
     else
-      rhs = Qi + (Ti - dens(sm.T, i - 1)) * inv_dr + Ti * geo.invR(i) - (jz_node(i - 1) + jz_node(i)) * inv_dr;
+      rhs = Qi + (Ti - dens(sm.T, i - 1)) * inv_dr + Ti * geo.curv(i) - (jz_node(i - 1) + jz_node(i)) * inv_dr;
     sm.ta[q] = a;
     sm.tb[q] = sgeo - dens(sm.chi, i);  // row sum a + b + c (both terms negative)
     sm.tc[q] = c;
@@ -944,7 +961,8 @@ template <class Pol>
 __device__ __forceinline__ void current_values(const MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int sl,
                                                int c, typename Pol::R f, typename Pol::R u_r, typename Pol::R u_t,
                                                typename Pol::R dr, int *status, typename Pol::R (&v)[5],
-                                               typename Pol::R &ka, typename Pol::R &G, typename Pol::R &g) {
+                                               typename Pol::R &ka, typename Pol::R &G, typename Pol::R &g,
+                                               bool slab = false) {
   using R = typename Pol::R;
   const R rp = ((R)c + f) * dr;
   G = rs.G0[sl] + interp(sm.psi, c, f);
@@ -955,7 +973,7 @@ __device__ __forceinline__ void current_values(const MarchSmem<Pol> &sm, const R
   const R uz = gam - G;
   const R a = u_r * iG;
   const R dp = interp(sm.dpsi, c, f);
-  const R cent = rp > (R)0 ? u_t * u_t * iG / rp : (R)0;
+  const R cent = (!slab && rp > (R)0) ? u_t * u_t * iG / rp : (R)0;  // Eq. 4's centrifugal term (cylinder)
   g = gam * iG * dp;
   const R w = rs.w[sl];
   v[0] = -w * uz * iG;
@@ -985,12 +1003,12 @@ __device__ __forceinline__ void current_direct(MarchSmem<Pol> &sm, int c, typena
 // formed again by the same arithmetic and deposited straight into the node arrays.
 template <class Pol, class PosSlot>
 __device__ __forceinline__ void current_miss(MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int sl,
-                                             typename Pol::R dr, int *status, PosSlot &&pos_slot) {
+                                             typename Pol::R dr, int *status, PosSlot &&pos_slot, bool slab = false) {
   using R = typename Pol::R;
   int c;
   R f, u_r, u_t, v[5], ka, G, g;
   pos_slot(sl, c, f, u_r, u_t);
-  current_values<Pol>(sm, rs, sl, c, f, u_r, u_t, dr, status, v, ka, G, g);
+  current_values<Pol>(sm, rs, sl, c, f, u_r, u_t, dr, status, v, ka, G, g, slab);
   current_direct<Pol>(sm, c, f, v, ka);
 }
 
@@ -1002,7 +1020,8 @@ __device__ __forceinline__ void current_miss(MarchSmem<Pol> &sm, const RingSoA<t
 template <class Pol, int NT, int PPT, bool kTrap = false, class Pos, class OnMiss>
 __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int np,
                                               int nr, typename Pol::R dr, int *status, Pos &&pos, OnMiss &&on_miss,
-                                              typename Pol::R (&Gam)[PPT], typename Pol::R (&gq)[PPT]) {
+                                              typename Pol::R (&Gam)[PPT], typename Pol::R (&gq)[PPT],
+                                              bool slab = false) {
   using R = typename Pol::R;
   using Acc = typename Pol::Acc;
   const int t = threadIdx.x;
@@ -1026,7 +1045,7 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
       if constexpr (kTrap)
         if (rs.w[sl] == (R)0) continue;  // promoted to a beam particle: no longer in the plasma
       R v[5], ka, G, g;
-      current_values<Pol>(sm, rs, sl, c, f, u_r, u_t, dr, status, v, ka, G, g);
+      current_values<Pol>(sm, rs, sl, c, f, u_r, u_t, dr, status, v, ka, G, g, slab);
       if (acc.add(c, f, v)) {
         const int o = c - acc.c0;
         kw[0] += o == 0 ? ka : (R)0;
@@ -1202,9 +1221,10 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
   const double drd = d.dr;
   const R h = (R)d.dxi, R_wall = (R)d.rmax, dR = (R)drd, inv_dr = (R)(1.0 / drd);
   using N = typename Pol::N;
+  const bool slab = d.slab != 0;
   const NodeGeo<Pol> geo{sm.invR, sm.invV, sm.alpha, sm.ga, sm.gb, sm.gc, nr, (N)drd, (N)(1.0 / drd), (N)(1.0 / (drd * drd)),
-                          (N)(drd / 6.0), (N)(1.0 / (0.5 * nr - 1.0 / 6.0))};
-  fill_tables<Pol, NT>(sm, nr, drd);
+                          (N)(drd / 6.0), (N)(1.0 / (0.5 * nr - 1.0 / 6.0)), (int)slab};
+  fill_tables<Pol, NT>(sm, nr, drd, slab);
   for (int m = tid; m < n1; m += NT) {
     sm.rho[m] = (typename Pol::Q)0;
     sm.jz[m] = sm.chi[m] = sm.T[m] = sm.P[m] = sm.U[m] = sm.K[m] = (Acc)0;
@@ -1235,29 +1255,33 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
   // the stage-1 derivative in the local Cartesian frame (x, y) = (r, 0), (u_x, u_y) =
   // (u_r, u_theta) (stage 2), computed once per slice in the midpoint deposit and kept in
   // registers for stage 2 and the full step
+  // u_theta = l_z / r; in the slab, lz holds the conserved u_y, which enters gamma only and
+  // moves nothing (d/dy = 0): the Cartesian frame below is then the x line, and r = |x| puts a
+  // sheet that crosses x = 0 in place of its mirror image
   auto state_pos = [&](int sl, int &c, R &f, R &u_r, R &u_t) {
     c = rs.c[sl];
     f = rs.f[sl];
     u_r = rs.ur[sl];
     const R r = ((R)c + f) * dR;
-    u_t = r > (R)0 ? rs.lz[sl] / r : (R)0;
+    u_t = slab ? rs.lz[sl] : (r > (R)0 ? rs.lz[sl] / r : (R)0);
   };
   auto midpoint = [&](int sl, int &c, R &f, R &u_r, R &u_t) -> R {
     const int c0 = rs.c[sl];
     const R f0 = rs.f[sl], ur0 = rs.ur[sl];
     const R r = ((R)c0 + f0) * dR;
-    const R ut = r > (R)0 ? rs.lz[sl] / r : (R)0;
+    const R ut = slab ? (R)0 : (r > (R)0 ? rs.lz[sl] / r : (R)0);  // the frame's y momentum
     const R iG = (R)1 / rs.G1[sl];
     const R dx = (R)0.5 * h * ur0 * iG, dy = (R)0.5 * h * ut * iG;
     const R uxh = ur0 + (R)0.5 * h * rs.F1[sl];
     R rr;
     move_ring<R>(c0, f0, r, dx, dy, uxh, ut, inv_dr, dR, nr, c, f, rr, u_r, u_t);
+    if (slab) u_t = rs.lz[sl];
     return rr;
   };
   auto mid_slot = [&](int sl, int &c, R &f, R &u_r, R &u_t) { midpoint(sl, c, f, u_r, u_t); };
   // out-of-window rings (queued in the passes, drained by the CTA after them)
-  auto cur_miss1 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, state_pos); };
-  auto cur_miss2 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, mid_slot); };
+  auto cur_miss1 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, state_pos, slab); };
+  auto cur_miss2 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, mid_slot, slab); };
   auto chg_miss_mid = [&](int sl) {
     const R w = rs.w[sl];
     if (kTrap && w == (R)0) return;  // a promoted ring deposits nothing
@@ -1316,7 +1340,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
       R Gs[PPT], gqs[PPT];
       pass_currents<Pol, NT, PPT, kTrap>(
           sm, rs, np, nr, dR, d.status, state_pos,
-          [&](unsigned miss) { queue_misses<NT, PPT>(sm, n1, miss, cur_miss1); }, Gs, gqs);
+          [&](unsigned miss) { queue_misses<NT, PPT>(sm, n1, miss, cur_miss1); }, Gs, gqs, slab);
 #pragma unroll
       for (int p = 0; p < PPT; ++p)
         if (tid * PPT + p < np) {
@@ -1384,7 +1408,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
                                   u_r = MUR[p];
                                   u_t = MUT[p];
                                 },
-                                [&](unsigned miss) { queue_misses<NT, PPT>(sm, n1, miss, cur_miss2); }, G2, F2);
+                                [&](unsigned miss) { queue_misses<NT, PPT>(sm, n1, miss, cur_miss2); }, G2, F2, slab);
     __syncthreads();
     drain_queue<NT>(sm, n1, cur_miss2);
     solve_fields<Pol, NT>(sm, geo, nbk, nbk1, sm.wtot);  // P2
@@ -1408,7 +1432,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
           const int c0 = rs.c[sl];
           const R f0 = rs.f[sl], ur0 = rs.ur[sl], G1v = rs.G1[sl], F1v = rs.F1[sl];
           const R r = ((R)c0 + f0) * dR;
-          const R ut = r > (R)0 ? rs.lz[sl] / r : (R)0;
+          const R ut = slab ? (R)0 : (r > (R)0 ? rs.lz[sl] / r : (R)0);  // the frame's y momentum
           const R iG1 = (R)1 / G1v;
           const R xh = r + (R)0.5 * h * ur0 * iG1;
           const R yh = (R)0.5 * h * ut * iG1;

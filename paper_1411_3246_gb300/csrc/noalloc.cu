@@ -41,12 +41,12 @@ __global__ void na_zero_kernel(double *acc, int64_t n) {
 // handle's deposit does in its FP64 form.
 __global__ void na_deposit_kernel(const double *__restrict__ xyz, const uint8_t *__restrict__ lost, int64_t n,
                                   int64_t n_drive, int nr, int nxi, double rmax, double ximax, double dr,
-                                  double dxi, double wd, double ww, double *acc) {
+                                  double dxi, double wd, double ww, double *acc, bool slab) {
   const int n1 = nr + 1;
   const double inv_dr = 1.0 / dr, inv_dxi = 1.0 / dxi;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
     if (lost && lost[j]) continue;
-    const double x = xyz[j], y = xyz[n + j], xi = xyz[2 * n + j];
+    const double x = xyz[j], y = slab ? 0.0 : xyz[n + j], xi = xyz[2 * n + j];  // slab: a sheet beam at y = 0
     const double r = sqrt(x * x + y * y);
     if (!(xi >= 0.0 && xi < ximax && r < rmax)) continue;  // outside the box: lost
     int c, k;
@@ -64,13 +64,13 @@ __global__ void na_deposit_kernel(const double *__restrict__ xyz, const uint8_t 
 
 // Divide by the hats' volumes: V_i in r, dxi in xi (dxi/2 at both ends).
 __global__ void na_normalize_kernel(const double *__restrict__ acc, double *__restrict__ nb, int nr, int nxi,
-                                    double dr, double dxi) {
+                                    double dr, double dxi, bool slab) {
   const int n1 = nr + 1;
   const int64_t tot = (int64_t)(nxi + 1) * n1;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(t / n1), i = (int)(t % n1);
     const double vx = (k == 0 || k == nxi) ? 0.5 * dxi : dxi;
-    nb[t] = acc[t] / (node_volume(i, nr, dr) * vx);
+    nb[t] = acc[t] / (node_volume(i, nr, dr, slab) * vx);
   }
 }
 
@@ -98,6 +98,8 @@ extern "C" int wake_beam_deposit_noalloc(const wake_params *p, const double *xyz
     return fail_na(WAKE_EINVAL, "wake_beam_deposit_noalloc: rmax and ximax must be positive");
   if (!(p->sigma_r > 0.0) || !(p->sigma_zd > 0.0) || (p->n_w != 0.0 && !(p->sigma_zw > 0.0)))
     return fail_na(WAKE_EINVAL, "wake_beam_deposit_noalloc: bunch sizes must be positive");
+  if (p->geometry != WAKE_CYLINDRICAL && p->geometry != WAKE_SLAB)
+    return fail_na(WAKE_EINVAL, "wake_beam_deposit_noalloc: geometry must be WAKE_CYLINDRICAL or WAKE_SLAB");
 
   // set-up, once per device: the address of the static accumulation grid
   int dev = 0;
@@ -122,13 +124,15 @@ extern "C" int wake_beam_deposit_noalloc(const wake_params *p, const double *xyz
   // macroparticle weights: each bunch's charge (per 2 pi) of Eq. 12 over its macroparticles
   const double s2pi = std::sqrt(2.0 * 3.14159265358979323846);
   const int64_t nw = p->n_beam - p->n_drive;
-  const double wd = p->n_drive > 0 ? p->n_d * s2pi * p->sigma_r * p->sigma_r * p->sigma_zd / (double)p->n_drive : 0.0;
-  const double ww = nw > 0 ? p->n_w * s2pi * p->sigma_r * p->sigma_r * p->sigma_zw / (double)nw : 0.0;
+  const bool slab = p->geometry == WAKE_SLAB;  // half-slab transverse integral sigma_r sqrt(2 pi)/2
+  const double tr = slab ? 0.5 * s2pi * p->sigma_r : p->sigma_r * p->sigma_r;
+  const double wd = p->n_drive > 0 ? p->n_d * s2pi * tr * p->sigma_zd / (double)p->n_drive : 0.0;
+  const double ww = nw > 0 ? p->n_w * s2pi * tr * p->sigma_zw / (double)nw : 0.0;
   na_zero_kernel<<<blocks_for(nodes), 256, 0, s>>>(acc, nodes);
   if (p->n_beam > 0)
     na_deposit_kernel<<<blocks_for(p->n_beam), 256, 0, s>>>(xyz, lost, p->n_beam, p->n_drive, p->nr, p->nxi,
-                                                            p->rmax, p->ximax, dr, dxi, wd, ww, acc);
-  na_normalize_kernel<<<blocks_for(nodes), 256, 0, s>>>(acc, nb, p->nr, p->nxi, dr, dxi);
+                                                            p->rmax, p->ximax, dr, dxi, wd, ww, acc, slab);
+  na_normalize_kernel<<<blocks_for(nodes), 256, 0, s>>>(acc, nb, p->nr, p->nxi, dr, dxi, slab);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     // a stale address (e.g. after cudaDeviceReset) is looked up again by the next call

@@ -189,8 +189,11 @@ struct PipeHooks {
     locate(rn, inv_dr, nr, c2, f2);
     locate(xi, inv_dxi, nxi, k2, g2d);
     const BT g2 = (BT)g2d;
-    const BT wq = p.w * (BT)(1.0 / (dr * dr * dxi));
+    // 1 / V_i = iv(i) / dr^2 (slab: iv(i) / dx, the hat width halved at x = 0 and at the wall)
+    const bool slab = a.d.slab != 0;
+    const BT wq = p.w * (BT)(slab ? 1.0 / (dr * dxi) : 1.0 / (dr * dr * dxi));
     auto iv = [&](int i) -> BT {
+      if (slab) return (i == 0 || i == nr) ? (BT)2 : (BT)1;
       return i == 0 ? (BT)6 : (i == nr ? (BT)1 / ((BT)nr * (BT)0.5 - (BT)(1.0 / 6.0)) : (BT)1 / (BT)i);
     };
     const BT ix0 = k2 == 0 ? (BT)2 : (BT)1, ix1 = k2 + 1 == nxi ? (BT)2 : (BT)1;

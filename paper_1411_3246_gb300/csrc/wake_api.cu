@@ -162,6 +162,8 @@ int check_params(const wake_params &p, int prec0) {
   if (!(p.sigma_r > 0.0) || !(p.sigma_zd > 0.0) || (p.n_w != 0.0 && !(p.sigma_zw > 0.0)))
     return fail(WAKE_EINVAL, "bunch sizes must be positive");
   if (p.n_beam > 0 && (!(p.gamma_b > 1.0) || !(p.ds > 0.0))) return fail(WAKE_EINVAL, "a beam needs gamma_b > 1 and ds > 0");
+  if (p.geometry != WAKE_CYLINDRICAL && p.geometry != WAKE_SLAB)
+    return fail(WAKE_EINVAL, "geometry must be WAKE_CYLINDRICAL or WAKE_SLAB");
   return WAKE_OK;
 }
 
@@ -215,11 +217,14 @@ BeamDesc beam_desc(const Sim &s, double *diag) {
   b.ds = p.ds;
   b.gamma_b = p.gamma_b;
   // macroparticle weight = bunch charge (per 2 pi) of Eq. 12, n sqrt(2 pi) sigma_r^2 sigma_z,
-  // over the bunch's macroparticle count
+  // over the bunch's macroparticle count (slab: per unit area of the half slab, the transverse
+  // integral sigma_r sqrt(2 pi)/2 in place of sigma_r^2)
   const double s2pi = std::sqrt(2.0 * 3.14159265358979323846);
   const int64_t nw = p.n_beam - p.n_drive;
-  b.wd = p.n_drive > 0 ? p.n_d * s2pi * p.sigma_r * p.sigma_r * p.sigma_zd / (double)p.n_drive : 0.0;
-  b.ww = nw > 0 ? p.n_w * s2pi * p.sigma_r * p.sigma_r * p.sigma_zw / (double)nw : 0.0;
+  const double tr = p.geometry == WAKE_SLAB ? 0.5 * s2pi * p.sigma_r : p.sigma_r * p.sigma_r;
+  b.wd = p.n_drive > 0 ? p.n_d * s2pi * tr * p.sigma_zd / (double)p.n_drive : 0.0;
+  b.ww = nw > 0 ? p.n_w * s2pi * tr * p.sigma_zw / (double)nw : 0.0;
+  b.slab = p.geometry == WAKE_SLAB;
   b.x = s.bx;
   b.y = s.by;
   b.ux = s.bux;
@@ -452,6 +457,10 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
       const std::vector<TileFns> cand = tile_candidates(h, s);
       s.wide = !cand.empty() && cand.back().wide;
     }
+    if (s.wide && p[i].geometry == WAKE_SLAB) {
+      rc = fail(WAKE_EINVAL, "wake_init: a slab simulation must fit the shared-memory march (fewer cells or rings)");
+      break;
+    }
     h->max_n1 = std::max(h->max_n1, p[i].nr + 1);
     h->max_np = std::max(h->max_np, s.np);
     const size_t pb = sizeof(double) * s.np;
@@ -522,6 +531,7 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
       d.nxi = s.p.nxi;
       d.np = s.np;
       d.has_beam = s.p.n_beam > 0;
+      d.slab = s.p.geometry == WAKE_SLAB;
       d.rmax = s.p.rmax;
       d.ximax = s.p.ximax;
       d.dr = s.p.rmax / s.p.nr;
@@ -569,7 +579,7 @@ int wake_load_plasma(wake_sim *h, int sim, const double *normals) {
   const double dr = s.p.rmax / s.p.nr;
   plasma_init_kernel<<<grid_blocks(s.np, 256), 256, 0, h->stream>>>(s.p.nr, s.p.ppc, dr, s.p.u_th,
                                                                      s.p.u_th > 0.0 ? normals : nullptr, s.r0, s.ur0,
-                                                                     s.lz, s.G0, s.w);
+                                                                     s.lz, s.G0, s.w, s.p.geometry == WAKE_SLAB);
   CUDA_TRY(cudaGetLastError());
   s.plasma = true;
   return WAKE_OK;
@@ -638,10 +648,10 @@ int wake_beam_deposit(wake_sim *h) {
     const int nb = grid_blocks(s.p.n_beam, 256), ng = grid_blocks((int64_t)s.ng, 256);
     if (h->precision == WAKE_FP64) {
       beam_deposit_kernel<double, double><<<nb, 256, 0, h->stream>>>(b);
-      nb_normalize_kernel<double><<<ng, 256, 0, h->stream>>>((double *)s.nb, s.p.nr, s.p.nxi, b.dr, b.dxi);
+      nb_normalize_kernel<double><<<ng, 256, 0, h->stream>>>((double *)s.nb, s.p.nr, s.p.nxi, b.dr, b.dxi, b.slab);
     } else {
       beam_deposit_kernel<float, float><<<nb, 256, 0, h->stream>>>(b);
-      nb_normalize_kernel<float><<<ng, 256, 0, h->stream>>>((float *)s.nb, s.p.nr, s.p.nxi, b.dr, b.dxi);
+      nb_normalize_kernel<float><<<ng, 256, 0, h->stream>>>((float *)s.nb, s.p.nr, s.p.nxi, b.dr, b.dxi, b.slab);
     }
     CUDA_TRY(cudaGetLastError());
   }
@@ -654,6 +664,7 @@ int wake_set_trapping(wake_sim *h, int sim, double gamma_t, int64_t capacity) {
   Sim &s = h->sims[sim];
   if (h->n != 1) return fail(WAKE_EINVAL, "wake_set_trapping: trapping needs a handle of one simulation");
   if (s.p.n_beam == 0) return fail(WAKE_EINVAL, "wake_set_trapping: trapping needs a particle beam (n_beam > 0)");
+  if (s.p.geometry == WAKE_SLAB) return fail(WAKE_EINVAL, "wake_set_trapping: trapping is cylindrical only");
   if (!(gamma_t >= 0.0) || capacity < 0 || s.p.n_beam + capacity > ((int64_t)1 << 31) - 1)
     return fail(WAKE_EINVAL, "wake_set_trapping: need gamma_t >= 0 and 0 <= capacity < 2^31 - n_beam");
   if (s.beam) return fail(WAKE_ESTATE, "wake_set_trapping: call it before wake_load_beam / wake_set_beam");
@@ -878,6 +889,7 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
   int max_n1 = 0, max_np = 0;
   for (auto &s : h->sims) {
     if (s.p.n_beam == 0 || !s.beam || !s.plasma) return 1;
+    if (s.p.geometry == WAKE_SLAB) return 1;  // the batch pipeline marches the wide (cylindrical) form
     max_n1 = std::max(max_n1, s.p.nr + 1);
     max_np = std::max(max_np, s.np);
   }
@@ -959,7 +971,7 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
       CUDA_TRY(cudaMemsetAsync(s.pgrids, 0, gbytes * (ch + 1), h->stream));
       beam_deposit_kernel<float, float><<<grid_blocks(s.p.n_beam, 256), 256, 0, h->stream>>>(b);
       nb_normalize_kernel<float><<<grid_blocks((int64_t)s.ng, 256), 256, 0, h->stream>>>((float *)s.pgrids, s.p.nr, s.p.nxi,
-                                                                                       b.dr, b.dxi);
+                                                                                       b.dr, b.dxi, b.slab);
       CUDA_TRY(cudaGetLastError());
       CUDA_TRY(cudaMemsetAsync(s.progress, 0, sizeof(int) * ch, h->stream));
       CUDA_TRY(cudaMemsetAsync(s.defer_cnt, 0, sizeof(int) * ch, h->stream));
@@ -971,6 +983,7 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
       d.nxi = s.p.nxi;
       d.np = s.np;
       d.has_beam = 1;
+      d.slab = s.p.geometry == WAKE_SLAB;
       d.rmax = s.p.rmax;
       d.ximax = s.p.ximax;
       d.dr = s.p.rmax / s.p.nr;
@@ -1182,10 +1195,10 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
       const int nbk = grid_blocks(s.p.n_beam, 256), ngk = grid_blocks((int64_t)s.ng, 256);
       if (fp64) {
         beam_deposit_kernel<double, double><<<nbk, 256, 0, h->stream>>>(b);
-        nb_normalize_kernel<double><<<ngk, 256, 0, h->stream>>>((double *)s.pgrids, s.p.nr, s.p.nxi, b.dr, b.dxi);
+        nb_normalize_kernel<double><<<ngk, 256, 0, h->stream>>>((double *)s.pgrids, s.p.nr, s.p.nxi, b.dr, b.dxi, b.slab);
       } else {
         beam_deposit_kernel<float, float><<<nbk, 256, 0, h->stream>>>(b);
-        nb_normalize_kernel<float><<<ngk, 256, 0, h->stream>>>((float *)s.pgrids, s.p.nr, s.p.nxi, b.dr, b.dxi);
+        nb_normalize_kernel<float><<<ngk, 256, 0, h->stream>>>((float *)s.pgrids, s.p.nr, s.p.nxi, b.dr, b.dxi, b.slab);
       }
       CUDA_TRY(cudaGetLastError());
     }
@@ -1199,6 +1212,7 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
     d.nxi = s.p.nxi;
     d.np = s.np;
     d.has_beam = 1;
+    d.slab = s.p.geometry == WAKE_SLAB;
     d.rmax = s.p.rmax;
     d.ximax = s.p.ximax;
     d.dr = s.p.rmax / s.p.nr;

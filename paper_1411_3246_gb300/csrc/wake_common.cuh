@@ -2,7 +2,9 @@
 //
 // Grid conventions (Sec. II.A; readings stated in the library header): node-centred radial
 // nodes r_i = i dr, i = 0..nr; xi nodes xi_k = k dxi, k = 0..nxi; linear hats in r with
-// ring volumes V_0 = dr^2/6, V_i = r_i dr, V_nr = dr (r_nr/2 - dr/6) (per 2 pi).
+// ring volumes V_0 = dr^2/6, V_i = r_i dr, V_nr = dr (r_nr/2 - dr/6) (per 2 pi).  Slab
+// geometry (x, xi), x >= 0 with a mirror plane at x = 0: hat widths V_i = dx, halved at x = 0
+// and at the wall (per unit area).
 #pragma once
 
 #include <cstdint>
@@ -30,6 +32,7 @@ struct SimDesc {
   double *trap;
   int *trap_count;
   int trap_cap;
+  int slab;  // slab geometry: r is x, lz holds the conserved u_y
 };
 
 // Cell index c in [0, nr-1] and offset f = r/dr - c (f in [0,1] for 0 <= r <= rmax).
@@ -49,13 +52,14 @@ __device__ __forceinline__ R interp(const T *v, int c, R f) {
   return ((R)1 - f) * (R)v[c] + f * (R)v[c + 1];
 }
 
-__host__ __device__ __forceinline__ double node_volume(int i, int nr, double dr) {
+__host__ __device__ __forceinline__ double node_volume(int i, int nr, double dr, bool slab = false) {
+  if (slab) return (i == 0 || i == nr) ? 0.5 * dr : dr;
   return i == 0 ? dr * dr / 6.0 : (i == nr ? dr * ((double)nr * dr / 2.0 - dr / 6.0) : (double)i * dr * dr);
 }
 
-// Fraction of hat m's ring volume that lies inside r_m (1/2 - 1/(6m); 1 at the wall).
-__host__ __device__ __forceinline__ double node_alpha(int m, int nr) {
-  return m == nr ? 1.0 : 0.5 - 1.0 / (6.0 * (double)m);
+// Fraction of hat m's ring volume that lies inside r_m (1/2 - 1/(6m); 1 at the wall; slab 1/2).
+__host__ __device__ __forceinline__ double node_alpha(int m, int nr, bool slab = false) {
+  return m == nr ? 1.0 : (slab ? 0.5 : 0.5 - 1.0 / (6.0 * (double)m));
 }
 
 // Eq. 12: the two-bunch driver density.

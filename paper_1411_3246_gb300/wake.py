@@ -30,7 +30,8 @@ class wake_params(C.Structure):
                 ("n_d", C.c_double), ("n_w", C.c_double), ("sigma_r", C.c_double),
                 ("sigma_zd", C.c_double), ("sigma_zw", C.c_double), ("xi_d", C.c_double),
                 ("xi_w", C.c_double), ("gamma_b", C.c_double), ("eps_n", C.c_double),
-                ("ds", C.c_double), ("n_beam", C.c_int64), ("n_drive", C.c_int64)]
+                ("ds", C.c_double), ("n_beam", C.c_int64), ("n_drive", C.c_int64),
+                ("geometry", C.c_int32), ("reserved", C.c_int32)]
 
 
 class WakeError(RuntimeError):
@@ -100,7 +101,7 @@ def params_of(cfg, precision: int) -> wake_params:
     """wake_params from a parameter object with the WakeConfig attribute names."""
     return wake_params(cfg.nr, cfg.nxi, cfg.ppc, precision, cfg.rmax, cfg.ximax, cfg.u_th, cfg.n_d,
                        cfg.n_w, cfg.sigma_r, cfg.sigma_zd, cfg.sigma_zw, cfg.xi_d, cfg.xi_w,
-                       cfg.gamma_b, cfg.eps_n, cfg.ds, cfg.n_beam, cfg.n_drive)
+                       cfg.gamma_b, cfg.eps_n, cfg.ds, cfg.n_beam, cfg.n_drive, int(getattr(cfg, "geometry", 0)), 0)
 
 
 def wake_init(params, stream=None):

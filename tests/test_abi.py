@@ -32,10 +32,11 @@ def test_header_entry_points_are_exported(libwake):
 
 def test_params_struct_layout():
     from paper_1411_3246_gb300 import wake
-    # 4 int32 + 13 doubles + 2 int64, no padding
-    assert C.sizeof(wake.wake_params) == 4 * 4 + 13 * 8 + 2 * 8
+    # 4 int32 + 13 doubles + 2 int64 + 2 int32 (geometry, reserved), no padding
+    assert C.sizeof(wake.wake_params) == 4 * 4 + 13 * 8 + 2 * 8 + 2 * 4
     assert wake.wake_params.rmax.offset == 16
     assert wake.wake_params.n_beam.offset == 16 + 13 * 8
+    assert wake.wake_params.geometry.offset == 16 + 13 * 8 + 16
 
 
 def test_invalid_parameters_rejected_before_any_device_work(libwake):
@@ -62,7 +63,7 @@ def test_corrupt_parameters_rejected(libwake):
     h = C.c_void_p()
     base = synth.config_blowout(n_beam=1024, nr=32, nxi=16)
     for field, value in (("rmax", math.nan), ("ximax", -1.0), ("ds", math.nan), ("gamma_b", 0.5),
-                         ("sigma_r", math.nan), ("u_th", -0.1), ("n_drive", 2048), ("nxi", 1)):
+                         ("sigma_r", math.nan), ("u_th", -0.1), ("n_drive", 2048), ("nxi", 1), ("geometry", 2)):
         p = wake.params_of(base, wake.WAKE_MIXED)
         setattr(p, field, value)
         assert wake.lib().wake_init(C.byref(p), 1, None, C.byref(h)) == wake.WAKE_EINVAL, field

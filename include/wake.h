@@ -78,9 +78,9 @@ typedef struct wake_params {
  * plasma particles are sheets whose conserved u_y enters gamma only (Eq. 4 has no centrifugal
  * term); the beam is a sheet beam at y = u_y = 0, its density folded onto x >= 0 with the
  * bunch weight n sqrt(2 pi) sigma_z * sigma_r sqrt(2 pi)/2 (the half-slab integral).  The
- * fields keep their names: er is E_x, bth is B_y.  Slab simulations use the shared-memory
- * march forms only (nr*ppc and nr within one CTA's shared memory, e.g. nr = 512 with 8192
- * rings in FP64 or 4096 in the mixed form) and have no trapping and no adjoint.
+ * fields keep their names: er is E_x, bth is B_y.  Slab simulations use the 512-thread
+ * shared-memory march forms with up to 8 rings per thread (nr*ppc <= 4096, and within one
+ * CTA's shared memory), and have no trapping and no adjoint.
  */
 #define WAKE_CYLINDRICAL 0
 #define WAKE_SLAB 1

@@ -125,6 +125,7 @@ struct PolFP64 {
   static constexpr bool kSmemRings = false;
   static constexpr bool kTables = true;
   static constexpr bool kWinGlobal = false;
+  static constexpr bool kSlab = false;  // geometry: see SlabOf
   static constexpr int kScanE = 3;  // nodes per thread in the block scans: n1 <= kScanE * NT
 };
 struct PolMixed {
@@ -139,6 +140,7 @@ struct PolMixed {
   static constexpr bool kSmemRings = true;
   static constexpr bool kTables = false;
   static constexpr bool kWinGlobal = false;
+  static constexpr bool kSlab = false;  // geometry: see SlabOf
   static constexpr int kScanE = 3;
 };
 // The precision split in which only the particle arithmetic is FP32: each ring's push and its
@@ -157,6 +159,7 @@ struct PolMixed64 {
   static constexpr bool kSmemRings = true;
   static constexpr bool kTables = false;
   static constexpr bool kWinGlobal = true;
+  static constexpr bool kSlab = false;  // geometry: see SlabOf
   static constexpr int kScanE = 3;
 };
 // The mixed arithmetic for boxes too large for one CTA's shared memory to hold the rings
@@ -174,6 +177,7 @@ struct PolWide {
   static constexpr bool kSmemRings = false;
   static constexpr bool kTables = false;
   static constexpr bool kWinGlobal = false;
+  static constexpr bool kSlab = false;  // geometry: see SlabOf
   static constexpr int kScanE = 5;
 };
 
@@ -192,7 +196,17 @@ struct PolWideFP64 {
   static constexpr bool kSmemRings = false;
   static constexpr bool kTables = false;
   static constexpr bool kWinGlobal = false;
+  static constexpr bool kSlab = false;  // geometry: see SlabOf
   static constexpr int kScanE = 5;
+};
+// The slab geometry (x, xi) of a policy (Sec. I: WAKE handles slab and cylindrical geometry):
+// d/dy = 0 in place of d/dtheta = 0, x >= 0 with a mirror plane at x = 0, volumes per unit
+// area, lap_perp = d_x^2, Eq. 6 as d_x B_y = d_xi^2 psi + J_z, and the conserved u_y (kept in
+// the l_z slot) entering gamma only.  A separate instantiation, so the cylindrical kernels
+// carry no geometry test.
+template <class P>
+struct SlabOf : P {
+  static constexpr bool kSlab = true;
 };
 
 // Ring slot arrays: cell index, offset in the cell, u_r, the constants l_z, Gamma_0, w, and
@@ -309,7 +323,7 @@ struct NodeGeo {
   const R *t_invR, *t_invV, *t_alpha, *t_ga, *t_gb, *t_gc;
   int nr;
   R dr, inv_dr, inv_dr2, dr_6, v_wall_inv;
-  int slab;  // slab geometry (x, xi): lap_perp = d_x^2, hat widths per unit area
+  static constexpr bool slab = Pol::kSlab;  // lap_perp = d_x^2, hat widths per unit area
   // the metric of Gauss's law at node m, 1/r_m (slab 1), and the curvature term of
   // (1/r) d_r(r .), 1/r_m (slab 0)
   __device__ __forceinline__ R metric(int m) const { return slab ? (R)1 : t_invR[m]; }
@@ -359,8 +373,9 @@ struct NodeGeo {
 };
 
 template <class Pol, int NT>
-__device__ __forceinline__ void fill_tables(MarchSmem<Pol> &sm, int nr, double dr, bool slab) {
+__device__ __forceinline__ void fill_tables(MarchSmem<Pol> &sm, int nr, double dr) {
   using R = typename Pol::N;
+  constexpr bool slab = Pol::kSlab;
   for (int m = threadIdx.x; m <= nr; m += NT) {
     sm.invR[m] = (R)(m > 0 ? 1.0 / ((double)m * dr) : 0.0);
     if constexpr (Pol::kTables) {
@@ -830,6 +845,8 @@ template <>
 struct ChargeWin<PolMixed64> : ChargeWin<PolMixed> {};
 template <>
 struct ChargeWin<PolWideFP64> : ChargeWin<PolFP64> {};
+template <class P>
+struct ChargeWin<SlabOf<P>> : ChargeWin<P> {};
 
 
 __device__ __forceinline__ void q_atomic_add(double *p, double v) { atomicAdd(p, v); }
@@ -961,9 +978,9 @@ template <class Pol>
 __device__ __forceinline__ void current_values(const MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int sl,
                                                int c, typename Pol::R f, typename Pol::R u_r, typename Pol::R u_t,
                                                typename Pol::R dr, int *status, typename Pol::R (&v)[5],
-                                               typename Pol::R &ka, typename Pol::R &G, typename Pol::R &g,
-                                               bool slab = false) {
+                                               typename Pol::R &ka, typename Pol::R &G, typename Pol::R &g) {
   using R = typename Pol::R;
+  constexpr bool slab = Pol::kSlab;
   const R rp = ((R)c + f) * dr;
   G = rs.G0[sl] + interp(sm.psi, c, f);
   if (!(G > (R)0)) flag(status, ST_NUMERIC);
@@ -1003,12 +1020,12 @@ __device__ __forceinline__ void current_direct(MarchSmem<Pol> &sm, int c, typena
 // formed again by the same arithmetic and deposited straight into the node arrays.
 template <class Pol, class PosSlot>
 __device__ __forceinline__ void current_miss(MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int sl,
-                                             typename Pol::R dr, int *status, PosSlot &&pos_slot, bool slab = false) {
+                                             typename Pol::R dr, int *status, PosSlot &&pos_slot) {
   using R = typename Pol::R;
   int c;
   R f, u_r, u_t, v[5], ka, G, g;
   pos_slot(sl, c, f, u_r, u_t);
-  current_values<Pol>(sm, rs, sl, c, f, u_r, u_t, dr, status, v, ka, G, g, slab);
+  current_values<Pol>(sm, rs, sl, c, f, u_r, u_t, dr, status, v, ka, G, g);
   current_direct<Pol>(sm, c, f, v, ka);
 }
 
@@ -1020,8 +1037,7 @@ __device__ __forceinline__ void current_miss(MarchSmem<Pol> &sm, const RingSoA<t
 template <class Pol, int NT, int PPT, bool kTrap = false, class Pos, class OnMiss>
 __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<typename Pol::R> &rs, int np,
                                               int nr, typename Pol::R dr, int *status, Pos &&pos, OnMiss &&on_miss,
-                                              typename Pol::R (&Gam)[PPT], typename Pol::R (&gq)[PPT],
-                                              bool slab = false) {
+                                              typename Pol::R (&Gam)[PPT], typename Pol::R (&gq)[PPT]) {
   using R = typename Pol::R;
   using Acc = typename Pol::Acc;
   const int t = threadIdx.x;
@@ -1045,7 +1061,7 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
       if constexpr (kTrap)
         if (rs.w[sl] == (R)0) continue;  // promoted to a beam particle: no longer in the plasma
       R v[5], ka, G, g;
-      current_values<Pol>(sm, rs, sl, c, f, u_r, u_t, dr, status, v, ka, G, g, slab);
+      current_values<Pol>(sm, rs, sl, c, f, u_r, u_t, dr, status, v, ka, G, g);
       if (acc.add(c, f, v)) {
         const int o = c - acc.c0;
         kw[0] += o == 0 ? ka : (R)0;
@@ -1221,10 +1237,14 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
   const double drd = d.dr;
   const R h = (R)d.dxi, R_wall = (R)d.rmax, dR = (R)drd, inv_dr = (R)(1.0 / drd);
   using N = typename Pol::N;
-  const bool slab = d.slab != 0;
+  constexpr bool slab = Pol::kSlab;
+  if ((d.slab != 0) != slab) {  // a descriptor of the other geometry: refuse, touch nothing
+    if (tid == 0) flag(d.status, ST_NUMERIC);
+    return;
+  }
   const NodeGeo<Pol> geo{sm.invR, sm.invV, sm.alpha, sm.ga, sm.gb, sm.gc, nr, (N)drd, (N)(1.0 / drd), (N)(1.0 / (drd * drd)),
-                          (N)(drd / 6.0), (N)(1.0 / (0.5 * nr - 1.0 / 6.0)), (int)slab};
-  fill_tables<Pol, NT>(sm, nr, drd, slab);
+                          (N)(drd / 6.0), (N)(1.0 / (0.5 * nr - 1.0 / 6.0))};
+  fill_tables<Pol, NT>(sm, nr, drd);
   for (int m = tid; m < n1; m += NT) {
     sm.rho[m] = (typename Pol::Q)0;
     sm.jz[m] = sm.chi[m] = sm.T[m] = sm.P[m] = sm.U[m] = sm.K[m] = (Acc)0;
@@ -1280,8 +1300,8 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
   };
   auto mid_slot = [&](int sl, int &c, R &f, R &u_r, R &u_t) { midpoint(sl, c, f, u_r, u_t); };
   // out-of-window rings (queued in the passes, drained by the CTA after them)
-  auto cur_miss1 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, state_pos, slab); };
-  auto cur_miss2 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, mid_slot, slab); };
+  auto cur_miss1 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, state_pos); };
+  auto cur_miss2 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, mid_slot); };
   auto chg_miss_mid = [&](int sl) {
     const R w = rs.w[sl];
     if (kTrap && w == (R)0) return;  // a promoted ring deposits nothing
@@ -1340,7 +1360,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
       R Gs[PPT], gqs[PPT];
       pass_currents<Pol, NT, PPT, kTrap>(
           sm, rs, np, nr, dR, d.status, state_pos,
-          [&](unsigned miss) { queue_misses<NT, PPT>(sm, n1, miss, cur_miss1); }, Gs, gqs, slab);
+          [&](unsigned miss) { queue_misses<NT, PPT>(sm, n1, miss, cur_miss1); }, Gs, gqs);
 #pragma unroll
       for (int p = 0; p < PPT; ++p)
         if (tid * PPT + p < np) {
@@ -1408,7 +1428,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
                                   u_r = MUR[p];
                                   u_t = MUT[p];
                                 },
-                                [&](unsigned miss) { queue_misses<NT, PPT>(sm, n1, miss, cur_miss2); }, G2, F2, slab);
+                                [&](unsigned miss) { queue_misses<NT, PPT>(sm, n1, miss, cur_miss2); }, G2, F2);
     __syncthreads();
     drain_queue<NT>(sm, n1, cur_miss2);
     solve_fields<Pol, NT>(sm, geo, nbk, nbk1, sm.wtot);  // P2

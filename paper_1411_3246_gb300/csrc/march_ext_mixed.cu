@@ -7,9 +7,9 @@
 namespace wake {
 
 namespace {
-template <int PPT>
+template <class P, int PPT>
 cudaError_t go_traj(const SimDesc *d, int n1, double *traj, int every, cudaStream_t s) {
-  auto kern = march_traj_kernel<PolMixed, 512, PPT>;
+  auto kern = march_traj_kernel<P, 512, PPT>;
   const size_t smem = MarchSmem<PolMixed>::bytes(n1, 512 * PPT, true);
   if (smem > kMaxSmemPerCta) return cudaErrorInvalidValue;
   const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -51,13 +51,23 @@ cudaError_t launch_march_trap_mixed(const SimDesc *d, int n1, int np, cudaStream
   }
 }
 
-cudaError_t launch_march_traj_mixed(const SimDesc *d, int n1, int np, double *traj, int every, cudaStream_t s) {
+cudaError_t launch_march_traj_mixed(const SimDesc *d, int n1, int np, double *traj, int every, bool slab,
+                                     cudaStream_t s) {
+  if (slab) {  // the slab geometry's kernels (up to 8 rings per thread)
+    switch (traj_ppt(np)) {
+      case 1: return go_traj<SlabOf<PolMixed>, 1>(d, n1, traj, every, s);
+      case 2: return go_traj<SlabOf<PolMixed>, 2>(d, n1, traj, every, s);
+      case 4: return go_traj<SlabOf<PolMixed>, 4>(d, n1, traj, every, s);
+      case 8: return go_traj<SlabOf<PolMixed>, 8>(d, n1, traj, every, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (traj_ppt(np)) {
-    case 1: return go_traj<1>(d, n1, traj, every, s);
-    case 2: return go_traj<2>(d, n1, traj, every, s);
-    case 4: return go_traj<4>(d, n1, traj, every, s);
-    case 8: return go_traj<8>(d, n1, traj, every, s);
-    case 16: return go_traj<16>(d, n1, traj, every, s);
+    case 1: return go_traj<PolMixed, 1>(d, n1, traj, every, s);
+    case 2: return go_traj<PolMixed, 2>(d, n1, traj, every, s);
+    case 4: return go_traj<PolMixed, 4>(d, n1, traj, every, s);
+    case 8: return go_traj<PolMixed, 8>(d, n1, traj, every, s);
+    case 16: return go_traj<PolMixed, 16>(d, n1, traj, every, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -4,8 +4,17 @@
 
 namespace wake {
 
-bool march_tile_fp64(int nt, int ppt, TileFns *out) {
+bool march_tile_fp64(int nt, int ppt, TileFns *out, bool slab) {
   if (nt != PolFP64::NT) return false;
+  if (slab) {
+    switch (ppt) {
+      case 1: *out = tile_fns<SlabOf<PolFP64>, 512, 1>(); return true;
+      case 2: *out = tile_fns<SlabOf<PolFP64>, 512, 2>(); return true;
+      case 4: *out = tile_fns<SlabOf<PolFP64>, 512, 4>(); return true;
+      case 8: *out = tile_fns<SlabOf<PolFP64>, 512, 8>(); return true;
+      default: return false;
+    }
+  }
   switch (ppt) {
     case 1: *out = tile_fns<PolFP64, 512, 1>(); return true;
     case 2: *out = tile_fns<PolFP64, 512, 2>(); return true;
@@ -16,10 +25,11 @@ bool march_tile_fp64(int nt, int ppt, TileFns *out) {
   }
 }
 
-bool march_tile(int form, int nt, int ppt, TileFns *out) {
-  if (form == kFormFP64) return march_tile_fp64(nt, ppt, out);
-  if (form == kFormMixed64) return march_tile_mixed64(nt, ppt, out);
-  return nt == 512 ? march_tile_mixed512(nt, ppt, out) : march_tile_mixed_small(nt, ppt, out);
+bool march_tile(int form, bool slab, int nt, int ppt, TileFns *out) {
+  if (form == kFormFP64) return march_tile_fp64(nt, ppt, out, slab);
+  if (form == kFormMixed64) return march_tile_mixed64(nt, ppt, out, slab);
+  if (nt == 512) return march_tile_mixed512(nt, ppt, out, slab);
+  return !slab && march_tile_mixed_small(nt, ppt, out);  // the small tiles are cylindrical only
 }
 
 size_t ring_buf_bytes(int form) {
@@ -28,9 +38,9 @@ size_t ring_buf_bytes(int form) {
 }
 
 
-template <int PPT>
+template <class P, int PPT>
 static cudaError_t go_step(const PipeArgs &a, int ctas, cudaStream_t stream) {
-  auto kern = step_kernel<PolFP64, PolFP64::NT, PPT>;
+  auto kern = step_kernel<P, PolFP64::NT, PPT>;
   const size_t smem = step_smem_bytes<PolFP64, PolFP64::NT, PPT>(a.d.nr + 1);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -65,12 +75,21 @@ static size_t step_bytes_for(int n1, int np) {
   }
 }
 cudaError_t launch_step_fp64(const PipeArgs &a, int np, int ctas, cudaStream_t stream) {
+  if (a.d.slab) {  // the slab geometry's kernels (up to 8 rings per thread)
+    switch (ppt_for(np)) {
+      case 1: return go_step<SlabOf<PolFP64>, 1>(a, ctas, stream);
+      case 2: return go_step<SlabOf<PolFP64>, 2>(a, ctas, stream);
+      case 4: return go_step<SlabOf<PolFP64>, 4>(a, ctas, stream);
+      case 8: return go_step<SlabOf<PolFP64>, 8>(a, ctas, stream);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (ppt_for(np)) {
-    case 1: return go_step<1>(a, ctas, stream);
-    case 2: return go_step<2>(a, ctas, stream);
-    case 4: return go_step<4>(a, ctas, stream);
-    case 8: return go_step<8>(a, ctas, stream);
-    case 16: return go_step<16>(a, ctas, stream);
+    case 1: return go_step<PolFP64, 1>(a, ctas, stream);
+    case 2: return go_step<PolFP64, 2>(a, ctas, stream);
+    case 4: return go_step<PolFP64, 4>(a, ctas, stream);
+    case 8: return go_step<PolFP64, 8>(a, ctas, stream);
+    case 16: return go_step<PolFP64, 16>(a, ctas, stream);
     default: return cudaErrorInvalidValue;
   }
 }

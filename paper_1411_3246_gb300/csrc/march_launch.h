@@ -25,12 +25,13 @@ struct TileFns {
   size_t (*smem)(int n1);
   int (*occupancy)(int n1);  // CTAs per SM for n1 nodes, 0 if it does not fit
 };
-// The tile (nt, ppt) of a precision form, if it is compiled.
-bool march_tile(int form, int nt, int ppt, TileFns *out);
-bool march_tile_fp64(int nt, int ppt, TileFns *out);
-bool march_tile_mixed512(int nt, int ppt, TileFns *out);
+// The tile (nt, ppt) of a precision form and geometry (slab: nt = 512, ppt <= 8), if it is
+// compiled.
+bool march_tile(int form, bool slab, int nt, int ppt, TileFns *out);
+bool march_tile_fp64(int nt, int ppt, TileFns *out, bool slab);
+bool march_tile_mixed512(int nt, int ppt, TileFns *out, bool slab);
 bool march_tile_mixed_small(int nt, int ppt, TileFns *out);
-bool march_tile_mixed64(int nt, int ppt, TileFns *out);
+bool march_tile_mixed64(int nt, int ppt, TileFns *out, bool slab);
 // The wide mixed march (march_wide.cuh) and its ring buffer for np rings.
 TileFns march_tile_wide();
 size_t wide_ring_bytes(int np);
@@ -72,8 +73,8 @@ int step_ctas_mixed64(int n1, int np);
 // and its launch on the descriptor d (device).
 size_t march_traj_smem_fp64(int n1, int np);
 size_t march_traj_smem_mixed(int n1, int np);
-cudaError_t launch_march_traj_fp64(const SimDesc *d, int n1, int np, double *traj, int every, cudaStream_t s);
-cudaError_t launch_march_traj_mixed(const SimDesc *d, int n1, int np, double *traj, int every, cudaStream_t s);
+cudaError_t launch_march_traj_fp64(const SimDesc *d, int n1, int np, double *traj, int every, bool slab, cudaStream_t s);
+cudaError_t launch_march_traj_mixed(const SimDesc *d, int n1, int np, double *traj, int every, bool slab, cudaStream_t s);
 // The plain march with trapping (march_trap_kernel) on descriptor d (device); same shared memory.
 cudaError_t launch_march_trap_fp64(const SimDesc *d, int n1, int np, cudaStream_t s);
 cudaError_t launch_march_trap_mixed(const SimDesc *d, int n1, int np, cudaStream_t s);

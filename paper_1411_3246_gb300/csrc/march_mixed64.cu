@@ -6,8 +6,17 @@
 
 namespace wake {
 
-bool march_tile_mixed64(int nt, int ppt, TileFns *out) {
+bool march_tile_mixed64(int nt, int ppt, TileFns *out, bool slab) {
   if (nt != 512) return false;
+  if (slab) {
+    switch (ppt) {
+      case 1: *out = tile_fns<SlabOf<PolMixed64>, 512, 1>(); return true;
+      case 2: *out = tile_fns<SlabOf<PolMixed64>, 512, 2>(); return true;
+      case 4: *out = tile_fns<SlabOf<PolMixed64>, 512, 4>(); return true;
+      case 8: *out = tile_fns<SlabOf<PolMixed64>, 512, 8>(); return true;
+      default: return false;
+    }
+  }
   switch (ppt) {
     case 1: *out = tile_fns<PolMixed64, 512, 1>(); return true;
     case 2: *out = tile_fns<PolMixed64, 512, 2>(); return true;
@@ -18,9 +27,9 @@ bool march_tile_mixed64(int nt, int ppt, TileFns *out) {
   }
 }
 
-template <int PPT>
+template <class P, int PPT>
 static cudaError_t go_step(const PipeArgs &a, int ctas, cudaStream_t stream) {
-  auto kern = step_kernel<PolMixed64, PolMixed64::NT, PPT>;
+  auto kern = step_kernel<P, PolMixed64::NT, PPT>;
   const size_t smem = step_smem_bytes<PolMixed64, PolMixed64::NT, PPT>(a.d.nr + 1);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -55,12 +64,21 @@ static size_t step_bytes_for(int n1, int np) {
   }
 }
 cudaError_t launch_step_mixed64(const PipeArgs &a, int np, int ctas, cudaStream_t stream) {
+  if (a.d.slab) {
+    switch (ppt_for(np)) {
+      case 1: return go_step<SlabOf<PolMixed64>, 1>(a, ctas, stream);
+      case 2: return go_step<SlabOf<PolMixed64>, 2>(a, ctas, stream);
+      case 4: return go_step<SlabOf<PolMixed64>, 4>(a, ctas, stream);
+      case 8: return go_step<SlabOf<PolMixed64>, 8>(a, ctas, stream);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (ppt_for(np)) {
-    case 1: return go_step<1>(a, ctas, stream);
-    case 2: return go_step<2>(a, ctas, stream);
-    case 4: return go_step<4>(a, ctas, stream);
-    case 8: return go_step<8>(a, ctas, stream);
-    case 16: return go_step<16>(a, ctas, stream);
+    case 1: return go_step<PolMixed64, 1>(a, ctas, stream);
+    case 2: return go_step<PolMixed64, 2>(a, ctas, stream);
+    case 4: return go_step<PolMixed64, 4>(a, ctas, stream);
+    case 8: return go_step<PolMixed64, 8>(a, ctas, stream);
+    case 16: return go_step<PolMixed64, 16>(a, ctas, stream);
     default: return cudaErrorInvalidValue;
   }
 }

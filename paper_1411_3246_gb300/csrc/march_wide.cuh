@@ -132,7 +132,7 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
   const R h = (R)d.dxi, R_wall = (R)d.rmax, dR = (R)drd, inv_dr = (R)(1.0 / drd);
   const NodeGeo<Pol> geo{sm.invR, sm.invV, sm.alpha, sm.ga, sm.gb, sm.gc, nr, dR, inv_dr, (R)(1.0 / (drd * drd)),
                           (R)(drd / 6.0), (R)(1.0 / (0.5 * nr - 1.0 / 6.0))};
-  fill_tables<Pol, NT>(sm, nr, drd, false);  // the wide form is cylindrical only
+  fill_tables<Pol, NT>(sm, nr, drd);  // the wide form is cylindrical only
   for (int m = tid; m < n1; m += NT) {
     sm.rho[m] = (typename Pol::Q)0;
     sm.jz[m] = sm.chi[m] = sm.T[m] = sm.P[m] = sm.U[m] = sm.K[m] = (Acc)0;

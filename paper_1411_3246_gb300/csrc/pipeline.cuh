@@ -190,7 +190,7 @@ struct PipeHooks {
     locate(xi, inv_dxi, nxi, k2, g2d);
     const BT g2 = (BT)g2d;
     // 1 / V_i = iv(i) / dr^2 (slab: iv(i) / dx, the hat width halved at x = 0 and at the wall)
-    const bool slab = a.d.slab != 0;
+    constexpr bool slab = Pol::kSlab;
     const BT wq = p.w * (BT)(slab ? 1.0 / (dr * dxi) : 1.0 / (dr * dr * dxi));
     auto iv = [&](int i) -> BT {
       if (slab) return (i == 0 || i == nr) ? (BT)2 : (BT)1;

@@ -262,10 +262,11 @@ std::vector<TileFns> tile_candidates(const wake_sim *h, const Sim &s) {
     if (n1 > 3 * nt) continue;
     const int ppt = pow2_at_least((s.np + nt - 1) / nt);
     TileFns f;
-    if (!march_tile(h->precision, nt, ppt, &f)) continue;
+    if (!march_tile(h->precision, s.p.geometry == WAKE_SLAB, nt, ppt, &f)) continue;
     if (f.smem(n1) > kMaxSmemPerCta) continue;
     out.push_back(f);
   }
+  if (s.p.geometry == WAKE_SLAB) return out;  // the wide forms are cylindrical only
   if (out.empty() && h->precision == WAKE_MIXED && (!h->tile_nt_forced || h->tile_nt_forced == -1)) {
     const TileFns f = march_tile_wide();
     if (n1 <= 5 * f.nt && f.smem(n1) <= kMaxSmemPerCta) out.push_back(f);
@@ -456,10 +457,10 @@ int wake_init(const wake_params *p, int n_sims, void *stream, wake_sim **out) {
     {
       const std::vector<TileFns> cand = tile_candidates(h, s);
       s.wide = !cand.empty() && cand.back().wide;
-    }
-    if (s.wide && p[i].geometry == WAKE_SLAB) {
-      rc = fail(WAKE_EINVAL, "wake_init: a slab simulation must fit the shared-memory march (fewer cells or rings)");
-      break;
+      if (cand.empty() && p[i].geometry == WAKE_SLAB) {
+        rc = fail(WAKE_EINVAL, "wake_init: a slab simulation needs the shared-memory march (nr*ppc <= 4096 within one CTA)");
+        break;
+      }
     }
     h->max_n1 = std::max(h->max_n1, p[i].nr + 1);
     h->max_np = std::max(h->max_np, s.np);
@@ -748,8 +749,9 @@ int wake_plasma_march_traj(wake_sim *h, int sim, int every, double *traj) {
   if (s.wide || smem > kMaxSmemPerCta)
     return fail(WAKE_EINVAL, "wake_plasma_march_traj: the simulation does not fit one 512-thread march CTA "
                              "(nr + 1 <= 1536 nodes and its rings in shared memory)");
-  const cudaError_t e = fp64 ? launch_march_traj_fp64(h->d_desc + sim, n1, s.np, traj, every, h->stream)
-                             : launch_march_traj_mixed(h->d_desc + sim, n1, s.np, traj, every, h->stream);
+  const bool slab = s.p.geometry == WAKE_SLAB;
+  const cudaError_t e = fp64 ? launch_march_traj_fp64(h->d_desc + sim, n1, s.np, traj, every, slab, h->stream)
+                             : launch_march_traj_mixed(h->d_desc + sim, n1, s.np, traj, every, slab, h->stream);
   if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("trajectory march launch: ") + cudaGetErrorString(e));
   s.marched = true;
   return WAKE_OK;

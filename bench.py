@@ -51,8 +51,8 @@ BEAM_STEPS = 200
 # DRAM traffic of one launch of the step kernel on this workload (200 steps), from one ncu
 # capture with one pass (dram__bytes_read.sum + dram__bytes_write.sum: 953.89 + 120.62 MB),
 # valid while the kernel's sources hash to STEP_TRAFFIC_SOURCES
-STEP_TRAFFIC_BYTES = 1074.51e6
-STEP_TRAFFIC_SOURCES = "bfad194e28efbd3b"
+STEP_TRAFFIC_BYTES = 1078.48e6
+STEP_TRAFFIC_SOURCES = "e98dda56a2273d07"
 STEP_SOURCES = ("beam.cuh", "march.cuh", "march_mixed.cu", "march_wide.cuh", "pipeline.cuh", "wake_common.cuh")
 
 
@@ -514,6 +514,42 @@ def osiris_leg(wake, torch, length_m, rank, flush, world):
                         f"{cfg.ppc} rings/cell", "dtype": "f32"}
 
 
+def slab_leg(wake, torch, nsteps, rank, flush, world):
+    """The blowout workload in slab geometry (Sec. I: WAKE handles slab as well as cylindrical
+    geometry): Nr=512 x Nxi=2048, 8 sheets/cell, two sheet bunches of 2^20 particles, mixed
+    form, one pipelined wake_step of nsteps, timed, after an untimed step."""
+    cfg = synth.config_slab_blowout(n_steps=nsteps)
+    cfg.seed = replica_seed(cfg.seed, rank)
+    stream = torch.cuda.Stream()
+    nm_p = torch.from_numpy(synth.plasma_normals(cfg)).pin_memory()
+    nm_b = torch.from_numpy(synth.beam_normals(cfg)).pin_memory()
+    sim = wake.Simulations([cfg], wake.WAKE_MIXED, stream)
+    with torch.cuda.stream(stream):
+        dp, db = nm_p.cuda(non_blocking=True), nm_b.cuda(non_blocking=True)
+        wake.wake_load_plasma(sim.h, 0, dp)
+        wake.wake_load_beam(sim.h, 0, db)
+        wake.wake_step(sim.h, 1)
+        wake.wake_load_beam(sim.h, 0, db)
+        flush.fill_(1)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        wake.wake_step(sim.h, nsteps)
+        ev[1].record(stream)
+    stream.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    d = sim.diagnostics()[0]
+    st = sim.status(0)
+    sim.close()
+    if st != wake.WAKE_OK:
+        raise RuntimeError(f"slab leg: simulation status {st}: {wake.wake_last_error()}")
+    t = barrier_max(ms / 1e3, world)
+    return {"value": world * plasma_pushes_per_step(cfg) * nsteps / t, "unit": "pushes/s", "ms_per_run": 1e3 * t,
+            "beam_steps": nsteps, "beam_pushes_per_s": world * cfg.n_beam * nsteps / t,
+            "witness_mean_gamma": d[1], "workload": f"slab blowout: two sheet bunches, {cfg.n_beam} particles, "
+            f"Nr={cfg.nr} x Nxi={cfg.nxi}, {cfg.ppc} sheets/cell, warm (u_th={cfg.u_th}), {nsteps} steps",
+            "dtype": "f32"}
+
+
 def adjoint_case(nsteps, rank):
     """The differentiation workload (synth.config_adjoint): the linear-driver grid (Nr=128 over
     6, 4 rings/cell) at Nxi=1024 over 10, two bunches, 262,144 beam particles, u_th = 0.005;
@@ -591,6 +627,7 @@ def main():
     ap.add_argument("--osiris-m", type=float, default=1.4,
                     help="metres the single bunch of the OSIRIS parameter set is carried (0: skip)")
     ap.add_argument("--latency", type=int, default=1, help="time the one-march latency case (0: skip)")
+    ap.add_argument("--slab-steps", type=int, default=200, help="beam steps of the slab-geometry leg (0: skip)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -724,6 +761,9 @@ def main():
     if args.osiris_m > 0:
         osiris = osiris_leg(wake, torch, args.osiris_m, rank, flush, world)
 
+    # --- slab geometry: the blowout workload with sheet plasma and sheet bunches ---
+    slab = slab_leg(wake, torch, args.slab_steps, rank, flush, world) if args.slab_steps > 0 else None
+
     # --- the latency-bound case: one march of the linear workload, microseconds ---
     latency = latency_leg(wake, torch, stream) if args.latency else None
 
@@ -772,7 +812,7 @@ def main():
                 "e2e": {"value": world * pushes * e2e_steps / e2e_s, "unit": "pushes/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 5 * 8},
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "batched": batched, "adjoint": adjoint,
-                "large": large, "large_fp64": large_fp64, "facet": facet, "osiris": osiris, "latency": latency, "alu_peaks": fma,
+                "large": large, "large_fp64": large_fp64, "facet": facet, "osiris": osiris, "slab": slab, "latency": latency, "alu_peaks": fma,
                 "host_cores": {"nproc": os.cpu_count(), "affinity": len(os.sched_getaffinity(0))},
                 "gpu_launches": KERNELS_PER_RUN * args.steps,
                 "witness": {"mean_gamma": diag[1], "rms_gamma": diag[2], "alive": diag[0]}}

@@ -164,6 +164,22 @@ int wake_plasma_march_traj(wake_sim *s, int sim, int every, double *traj);
  * for every simulation with a beam.  Needs a march. */
 int wake_beam_push(wake_sim *s);
 
+/* nsteps beam time steps through the same fields (the wake of the last march held frozen:
+ * the beam pushed as test particles, with no deposit or march in between); nsteps >= 0.
+ * Errors as wake_beam_push. */
+int wake_beam_push_steps(wake_sim *s, int nsteps);
+
+/*
+ * Caller-owned field grids for simulation `sim` (Eqs. 6-7 output): from now on every march
+ * and step writes psi, E_z, E_r and B_theta (slab: E_x, B_y) of the simulation straight into
+ * these device arrays, and the beam push reads them there; the library frees its own grids and
+ * never frees these.  Each is (nxi + 1) x (nr + 1), slice-major, double (WAKE_FP64) or float
+ * (mixed forms), and must stay valid until wake_destroy.  wake_get_fields still copies from
+ * them.  Call before the first march or step of the handle.  Synchronises the stream.
+ * Errors: WAKE_EINVAL (bad sim, a null pointer), WAKE_ESTATE (after a march or step), WAKE_ECUDA.
+ */
+int wake_bind_fields(wake_sim *s, int sim, void *psi, void *ez, void *er, void *bth);
+
 /*
  * nsteps x (wake_beam_deposit, wake_plasma_march, wake_beam_push).  With several
  * simulations of the mixed form that all have beams, every simulation's steps run pipelined

@@ -68,6 +68,7 @@ struct Sim {
   int64_t *trap_used = nullptr;  // [0] promoted particles in the beam, [1] promotions dropped
   bool trap_pending = false;     // a march's promotions not yet appended to the beam
   bool plasma = false, beam = false, marched = false;
+  bool fields_bound = false;  // psi, ez, er, bth are the caller's (wake_bind_fields): never freed
   bool wide = false;  // marched by the wide form (rings in a global buffer)
 };
 
@@ -137,6 +138,7 @@ struct wake_sim {
 namespace {
 
 void free_sim(Sim &s) {
+  if (s.fields_bound) s.psi = s.ez = s.er = s.bth = nullptr;  // the caller's memory
   void *ptrs[] = {s.r0, s.ur0, s.lz, s.G0, s.w, s.ring_buf, s.nb, s.psi, s.ez, s.er, s.bth, s.bx, s.by, s.bux, s.buy,
                   s.bxi, s.buz, s.blost, s.status, s.orig, s.bx2, s.by2, s.bux2, s.buy2, s.bxi2, s.buz2, s.blost2,
                   s.orig2, s.bin_count, s.bin_start, s.bin_cursor, s.slip, s.pgrids, s.progress, s.pring,
@@ -754,6 +756,47 @@ int wake_plasma_march_traj(wake_sim *h, int sim, int every, double *traj) {
                              : launch_march_traj_mixed(h->d_desc + sim, n1, s.np, traj, every, slab, h->stream);
   if (e != cudaSuccess) return fail(WAKE_ECUDA, std::string("trajectory march launch: ") + cudaGetErrorString(e));
   s.marched = true;
+  return WAKE_OK;
+}
+
+int wake_bind_fields(wake_sim *h, int sim, void *psi, void *ez, void *er, void *bth) {
+  int rc = check_handle(h, sim);
+  if (rc) return rc;
+  if (!psi || !ez || !er || !bth) return fail(WAKE_EINVAL, "wake_bind_fields: null field pointer");
+  Sim &s = h->sims[sim];
+  if (s.marched || h->step_graph) return fail(WAKE_ESTATE, "wake_bind_fields after a march or step");
+  if (!s.fields_bound) {  // the library's own grids are no longer needed
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    void *own[] = {s.psi, s.ez, s.er, s.bth};
+    for (void *q : own)
+      if (q) cudaFree(q);
+  }
+  s.psi = psi;
+  s.ez = ez;
+  s.er = er;
+  s.bth = bth;
+  s.fields_bound = true;
+  // every descriptor that carries the field pointers: the march's, and the batched beam's
+  SimDesc &d = h->h_desc[sim];
+  d.psi = psi;
+  d.ez = ez;
+  d.er = er;
+  d.bth = bth;
+  CUDA_TRY(cudaMemcpyAsync(h->d_desc + sim, &d, sizeof(SimDesc), cudaMemcpyHostToDevice, h->stream));
+  if (h->d_bdesc) {
+    const BeamDesc b = beam_desc(s, nullptr);
+    CUDA_TRY(cudaMemcpyAsync(h->d_bdesc + sim, &b, sizeof(BeamDesc), cudaMemcpyHostToDevice, h->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(h->stream));  // the host copies above may be reused
+  return WAKE_OK;
+}
+
+int wake_beam_push_steps(wake_sim *h, int nsteps) {
+  if (!h || nsteps < 0) return fail(WAKE_EINVAL, "wake_beam_push_steps: null handle or nsteps < 0");
+  for (int t = 0; t < nsteps; ++t) {
+    const int rc = wake_beam_push(h);
+    if (rc) return rc;
+  }
   return WAKE_OK;
 }
 

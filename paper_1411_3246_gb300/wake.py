@@ -15,10 +15,11 @@ LIB_PATH = os.path.join(HERE, "_build", "libwake.so")
 
 WAKE_OK, WAKE_EINVAL, WAKE_ENOMEM, WAKE_ECUDA, WAKE_ENUMERIC, WAKE_ETIMEOUT, WAKE_EESCAPE, WAKE_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 WAKE_FP64, WAKE_MIXED, WAKE_MIXED64 = 0, 1, 2
+WAKE_CYLINDRICAL, WAKE_SLAB = 0, 1
 
 # every entry point the header declares
 EXPORTS = ["wake_init", "wake_load_plasma", "wake_load_beam", "wake_set_beam", "wake_beam_deposit", "wake_plasma_march",
-           "wake_plasma_march_traj", "wake_beam_push", "wake_step", "wake_tile", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
+           "wake_plasma_march_traj", "wake_beam_push", "wake_beam_push_steps", "wake_bind_fields", "wake_step", "wake_tile", "wake_step_kernel_ms", "wake_get_fields", "wake_get_nb", "wake_get_beam",
            "wake_diagnostics", "wake_status", "wake_set_trapping", "wake_trapped", "wake_beam_deposit_noalloc", "wake_adjoint_init",
            "wake_adjoint_forward", "wake_adjoint_backward", "wake_adjoint_destroy", "wake_last_error", "wake_destroy"]
 WAKE_NOALLOC_MAX_NODES = 524288
@@ -58,6 +59,8 @@ def lib():
         for n in ("wake_beam_deposit", "wake_plasma_march", "wake_beam_push"):
             getattr(L, n).argtypes = [vp]
         L.wake_plasma_march_traj.argtypes = [vp, i32, i32, vp]
+        L.wake_beam_push_steps.argtypes = [vp, i32]
+        L.wake_bind_fields.argtypes = [vp, i32, vp, vp, vp, vp]
         L.wake_step.argtypes = [vp, i32]
         L.wake_step_kernel_ms.argtypes = [vp, C.POINTER(C.c_float)]
         L.wake_tile.argtypes = [vp, i32, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -144,6 +147,16 @@ def wake_plasma_march_traj(h, sim, every, traj):
 
 def wake_beam_push(h):
     _check(lib().wake_beam_push(h))
+
+
+def wake_beam_push_steps(h, nsteps):
+    _check(lib().wake_beam_push_steps(h, int(nsteps)))
+
+
+def wake_bind_fields(h, sim, psi, ez, er, bth):
+    """psi, ez, er, bth: caller-owned (nxi+1) x (nr+1) CUDA tensors of the handle's field type
+    (float64 for WAKE_FP64, float32 otherwise), kept alive by the caller until wake_destroy."""
+    _check(lib().wake_bind_fields(h, sim, _ptr(psi), _ptr(ez), _ptr(er), _ptr(bth)))
 
 
 def wake_step(h, nsteps):

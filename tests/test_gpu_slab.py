@@ -201,3 +201,49 @@ def test_slab_refuses_trapping_and_the_adjoint(wk):
     a = C.c_void_p()
     assert wk.lib().wake_adjoint_init(C.byref(p), 2, 0, None, C.byref(a)) == wk.WAKE_EINVAL
     assert not a.value
+
+
+def test_bound_fields_and_frozen_wake_pushes(wk):
+    """wake_bind_fields: the march writes straight into caller-owned grids (the library's own
+    march to rounding) and the push reads them there; wake_beam_push_steps(n) equals n pushes."""
+    import torch
+    for geometry in (0, 1):
+        cfg = (synth.config_slab_blowout if geometry else synth.config_blowout)(n_beam=1 << 12, nr=64, nxi=128)
+        nm_p = torch.from_numpy(synth.plasma_normals(cfg)).cuda()
+        nm_b = torch.from_numpy(synth.beam_normals(cfg)).cuda()
+        got = []
+        for bind in (False, True):
+            with wk.Simulations([cfg], wk.WAKE_FP64) as s:
+                own = [torch.full((cfg.nxi + 1, cfg.nr + 1), float("nan"), dtype=torch.float64, device="cuda")
+                       for _ in range(4)]
+                if bind:
+                    wk.wake_bind_fields(s.h, 0, *own)
+                wk.wake_load_plasma(s.h, 0, nm_p)
+                wk.wake_load_beam(s.h, 0, nm_b)
+                wk.wake_beam_deposit(s.h)
+                wk.wake_plasma_march(s.h)
+                if bind:
+                    f = {k: v.cpu().numpy() for k, v in zip(("psi", "ez", "er", "bth"), own)}
+                    with pytest.raises(wk.WakeError):  # after a march: refused
+                        wk.wake_bind_fields(s.h, 0, *own)
+                else:
+                    f = {k: v.cpu().numpy() for k, v in s.fields(0).items()}
+                wk.wake_beam_push_steps(s.h, 3)
+                xyz = s.beam(0)[0].cpu().numpy()
+                assert s.status(0) == wk.WAKE_OK, wk.wake_last_error()
+            got.append((f, xyz))
+        # the same march (the FP64 deposit sums differ only in the order of their atomics)
+        for k in ("psi", "ez", "er", "bth"):
+            a, b = got[0][0][k], got[1][0][k]
+            assert np.isfinite(b).all() and np.abs(a - b).max() <= 1e-12 * np.abs(a).max(), k
+        assert np.abs(got[0][1] - got[1][1]).max() <= 1e-10 * np.abs(got[0][1]).max()
+        # three frozen-wake pushes = three separate pushes
+        with wk.Simulations([cfg], wk.WAKE_FP64) as s:
+            wk.wake_load_plasma(s.h, 0, nm_p)
+            wk.wake_load_beam(s.h, 0, nm_b)
+            wk.wake_beam_deposit(s.h)
+            wk.wake_plasma_march(s.h)
+            for _ in range(3):
+                wk.wake_beam_push(s.h)
+            xyz3 = s.beam(0)[0].cpu().numpy()
+        assert np.abs(xyz3 - got[0][1]).max() <= 1e-10 * np.abs(got[0][1]).max()

@@ -126,6 +126,8 @@ struct PolFP64 {
   static constexpr bool kTables = true;
   static constexpr bool kWinGlobal = false;
   static constexpr bool kSlab = false;  // geometry: see SlabOf
+  static constexpr bool kDeferMisses = false;  // out-of-window rings deposited after the ring loops
+  static constexpr bool kWarpPCR = false;      // the tridiagonal solve finished per warp
   static constexpr int kScanE = 3;  // nodes per thread in the block scans: n1 <= kScanE * NT
 };
 struct PolMixed {
@@ -141,6 +143,8 @@ struct PolMixed {
   static constexpr bool kTables = false;
   static constexpr bool kWinGlobal = false;
   static constexpr bool kSlab = false;  // geometry: see SlabOf
+  static constexpr bool kDeferMisses = true;  // out-of-window rings deposited after the ring loops
+  static constexpr bool kWarpPCR = true;      // the tridiagonal solve finished per warp
   static constexpr int kScanE = 3;
 };
 // The precision split in which only the particle arithmetic is FP32: each ring's push and its
@@ -160,6 +164,8 @@ struct PolMixed64 {
   static constexpr bool kTables = false;
   static constexpr bool kWinGlobal = true;
   static constexpr bool kSlab = false;  // geometry: see SlabOf
+  static constexpr bool kDeferMisses = true;  // out-of-window rings deposited after the ring loops
+  static constexpr bool kWarpPCR = true;      // the tridiagonal solve finished per warp
   static constexpr int kScanE = 3;
 };
 // The mixed arithmetic for boxes too large for one CTA's shared memory to hold the rings
@@ -178,6 +184,8 @@ struct PolWide {
   static constexpr bool kTables = false;
   static constexpr bool kWinGlobal = false;
   static constexpr bool kSlab = false;  // geometry: see SlabOf
+  static constexpr bool kDeferMisses = false;  // out-of-window rings deposited after the ring loops
+  static constexpr bool kWarpPCR = false;      // the tridiagonal solve finished per warp
   static constexpr int kScanE = 5;
 };
 
@@ -197,6 +205,8 @@ struct PolWideFP64 {
   static constexpr bool kTables = false;
   static constexpr bool kWinGlobal = false;
   static constexpr bool kSlab = false;  // geometry: see SlabOf
+  static constexpr bool kDeferMisses = false;  // out-of-window rings deposited after the ring loops
+  static constexpr bool kWarpPCR = false;      // the tridiagonal solve finished per warp
   static constexpr int kScanE = 5;
 };
 // The slab geometry (x, xi) of a policy (Sec. I: WAKE handles slab and cylindrical geometry):
@@ -453,6 +463,43 @@ __device__ __forceinline__ FF q_to_wide<long long, FF>(long long d) {
   return FF{x.h * s, x.l * s};
 }
 
+// Block-wide parallel cyclic reduction on the row-sum form (see pcr_rowsum_solve below), every
+// doubling over the block with a barrier.  Double-buffered; returns the buffer holding the
+// result (x_q = d_q / s_q there).  Ends with a barrier.
+template <int NT, class S>
+__device__ __forceinline__ int pcr_rowsum(S *a0, S *s0, S *c0, S *d0, S *a1, S *s1, S *c1, S *d1, int n) {
+  int cur = 0;
+  for (int k = 1; k < n; k <<= 1) {
+    const S *a = cur ? a1 : a0, *sm_ = cur ? s1 : s0, *c = cur ? c1 : c0, *d = cur ? d1 : d0;
+    S *an = cur ? a0 : a1, *sn = cur ? s0 : s1, *cn = cur ? c0 : c1, *dn = cur ? d0 : d1;
+    for (int q = threadIdx.x; q < n; q += NT) {
+      const S aq = a[q], cq = c[q];
+      S sq = sm_[q], dq = d[q], na = (S)0, nc = (S)0;
+      if (q - k >= 0) {
+        const S bm = sm_[q - k] - a[q - k] - c[q - k];
+        const S k1 = aq / bm;
+        sq -= k1 * sm_[q - k];
+        dq -= k1 * d[q - k];
+        na = -a[q - k] * k1;
+      }
+      if (q + k < n) {
+        const S bp = sm_[q + k] - a[q + k] - c[q + k];
+        const S k2 = cq / bp;
+        sq -= k2 * sm_[q + k];
+        dq -= k2 * d[q + k];
+        nc = -c[q + k] * k2;
+      }
+      an[q] = na;
+      sn[q] = sq;
+      cn[q] = nc;
+      dn[q] = dq;
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  return cur;
+}
+
 // Parallel cyclic reduction (Hockney) on rows a_q x_{q-1} + b_q x_q + c_q x_{q+1} = d_q
 // stored as (a, s = a + b + c, c, d).  For this M-matrix (a, c >= 0, s < 0) the eliminated
 // row sum s' = s - k1 s_{q-k} - k2 s_{q+k} (k1 = a_q/b_{q-k}, k2 = c_q/b_{q+k}, both <= 0)
@@ -659,9 +706,15 @@ __device__ __forceinline__ void solve_fields(MarchSmem<Pol> &sm, const NodeGeo<P
   // parallel cyclic reduction (on row sums); the second buffer reuses the deposit arrays J_z, chi, T, P,
   // which are dead once the rows are set up (they are zeroed before the next pass B)
   static_assert(sizeof(Acc) == sizeof(R), "PCR buffer reuses deposit arrays");
-  pcr_rowsum_solve<NT, R>(sm.ta, sm.tb, sm.tc, sm.td, (R *)sm.jz, (R *)sm.chi, (R *)sm.T, (R *)sm.P, nr,
-                          [&](int q, R x) { sm.bth[q + 1] = x; });  // row q is node q + 1
-  if (tid == 0) sm.bth[0] = (R)0;
+  if constexpr (Pol::kWarpPCR) {
+    pcr_rowsum_solve<NT, R>(sm.ta, sm.tb, sm.tc, sm.td, (R *)sm.jz, (R *)sm.chi, (R *)sm.T, (R *)sm.P, nr,
+                            [&](int q, R x) { sm.bth[q + 1] = x; });  // row q is node q + 1
+    if (tid == 0) sm.bth[0] = (R)0;
+  } else {
+    const int cur = pcr_rowsum<NT, R>(sm.ta, sm.tb, sm.tc, sm.td, (R *)sm.jz, (R *)sm.chi, (R *)sm.T, (R *)sm.P, nr);
+    const R *bb = cur ? (const R *)sm.chi : sm.tb, *dd = cur ? (const R *)sm.P : sm.td;  // row sum = diagonal now
+    for (int m = tid; m < n1; m += NT) sm.bth[m] = m > 0 ? dd[m - 1] / bb[m - 1] : (R)0;
+  }
   __syncthreads();
 }
 
@@ -878,10 +931,15 @@ __device__ __forceinline__ void add_charge(MarchSmem<Pol> &sm, ChargeWin<Pol> &a
 // Charge deposit of ring p through the window; a ring outside it is marked in miss (bit p) and
 // left to warp_misses.
 template <class Pol>
-__device__ __forceinline__ void add_charge_mark(ChargeWin<Pol> &acc, int p, int c, typename Pol::R f,
-                                                typename Pol::R w, unsigned &miss) {
+__device__ __forceinline__ void add_charge_mark(MarchSmem<Pol> &sm, ChargeWin<Pol> &acc, int p, int c,
+                                                typename Pol::R f, typename Pol::R w, unsigned &miss) {
   if (p == 0) acc.init(c);
-  if (!acc.add(c, f, w)) miss |= 1u << p;
+  if (!acc.add(c, f, w)) {
+    if constexpr (Pol::kDeferMisses)
+      miss |= 1u << p;
+    else
+      ChargeWin<Pol>::direct(sm.rho, c, f, w);  // the policy deposits in the loop
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1067,14 +1125,16 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
         kw[0] += o == 0 ? ka : (R)0;
         kw[1] += o == 1 ? ka : (R)0;
         kw[2] += o == 2 ? ka : (R)0;
-      } else {
+      } else if constexpr (Pol::kDeferMisses) {
         miss |= 1u << p;
+      } else {
+        current_direct<Pol>(sm, c, f, v, ka);
       }
       Gam[p] = G;
       gq[p] = g;
     }
   }
-  on_miss(miss);
+  if constexpr (Pol::kDeferMisses) on_miss(miss);
   const WarpSeg seg(acc.c0);
   const int c = acc.c0;
   const bool emit = seg.is_tail && c >= 0;
@@ -1299,7 +1359,8 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
     return rr;
   };
   auto mid_slot = [&](int sl, int &c, R &f, R &u_r, R &u_t) { midpoint(sl, c, f, u_r, u_t); };
-  // out-of-window rings (queued in the passes, drained by the CTA after them)
+  // out-of-window rings: those of the current passes queued and drained by the CTA after the
+  // pass, those of the charge passes (two atomics each) deposited by their own warp
   auto cur_miss1 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, state_pos); };
   auto cur_miss2 = [&](int sl) { current_miss<Pol>(sm, rs, sl, dR, d.status, mid_slot); };
   auto chg_miss_mid = [&](int sl) {
@@ -1409,14 +1470,13 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
           MF[p] = f;
           MUR[p] = u_r;
           MUT[p] = u_t;
-          add_charge_mark<Pol>(acc, p, c, f, rs.w[sl], miss);
+          add_charge_mark<Pol>(sm, acc, p, c, f, rs.w[sl], miss);
         }
       }
-      queue_misses<NT, PPT>(sm, n1, miss, chg_miss_mid);
+      warp_misses<NT, PPT>(miss, chg_miss_mid);
       flush_charge<Pol>(sm, acc, nr);
     }
     __syncthreads();
-    drain_queue<NT>(sm, n1, chg_miss_mid);
     // ======== stage 2 at xi_k + dxi/2 ========
     solve_psi<Pol, NT>(sm, geo, sm.wtot);  // P0
     __syncthreads();
@@ -1445,7 +1505,7 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
         if (tid * PPT + p < np) {
           const int sl = p * NT + tid;
           if (kTrap && rs.w[sl] == (R)0) {  // a promoted ring: no move, no charge
-            add_charge_mark<Pol>(acc, p, rs.c[sl], rs.f[sl], (R)0, miss);
+            add_charge_mark<Pol>(sm, acc, p, rs.c[sl], rs.f[sl], (R)0, miss);
             continue;
           }
           const R F2b = F2[p] - interp(sm.bth, MC[p], MF[p]);  // at the midpoint
@@ -1474,14 +1534,13 @@ __device__ __forceinline__ void march_body(const SimDesc &d, unsigned char *smem
           rs.c[sl] = cn;
           rs.f[sl] = fn;
           rs.ur[sl] = urn;
-          add_charge_mark<Pol>(acc, p, cn, fn, rs.w[sl], miss);
+          add_charge_mark<Pol>(sm, acc, p, cn, fn, rs.w[sl], miss);
         }
       }
-      queue_misses<NT, PPT>(sm, n1, miss, chg_miss_full);
+      warp_misses<NT, PPT>(miss, chg_miss_full);
       flush_charge<Pol>(sm, acc, nr);
     }
     __syncthreads();
-    drain_queue<NT>(sm, n1, chg_miss_full);
   }
   hk.finish(sm);
 }

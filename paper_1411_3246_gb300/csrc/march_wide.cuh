@@ -257,7 +257,7 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
           R f, u_r, u_t;
           const R rr = midpoint_abs(sl, c, f, u_r, u_t);
           if (!(rr >= (R)0 && rr <= R_wall)) flag(d.status, ST_ESCAPE);
-          add_charge_mark<Pol>(acc, p, c, f, rs.w[sl], miss);
+          add_charge_mark<Pol>(sm, acc, p, c, f, rs.w[sl], miss);
         }
       }
       warp_misses<NT, PPT>(miss, [&](int sl) {
@@ -332,7 +332,7 @@ __device__ __forceinline__ void march_body_wide(const SimDesc &d, unsigned char 
           rs.c[sl] = cn;
           rs.f[sl] = fn;
           rs.ur[sl] = urn;
-          add_charge_mark<Pol>(acc, p, cn, fn, rs.w[sl], miss);
+          add_charge_mark<Pol>(sm, acc, p, cn, fn, rs.w[sl], miss);
         }
       }
       warp_misses<NT, PPT>(miss, [&](int sl) {  // the new positions are in the slots

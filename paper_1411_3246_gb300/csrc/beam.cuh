@@ -1,9 +1,11 @@
 // Beam-driver and set-up kernels: the Eq. 12 bunches, their (r, xi) deposit, the Boris push
 // of Eqs. 8-11, witness diagnostics, and the initial plasma slice of Sec. II.A.
 //
-// Beam state is SoA: x, y, u_x, u_y in the policy's type BT (float in the mixed form),
-// xi and u_z always in FP64 (u_z ~ gamma_b = 4e4 changes by O(1) per step and xi slips by
-// ~1e-9 per step: both are accumulated in FP64, the kicks themselves computed in BT).  A
+// Beam state is SoA: x, y, u_x, u_y in the policy's type BT (float in the mixed form).  xi
+// and u_z need more than FP32: u_z ~ gamma_b = 4e4 changes by O(1) per step and xi slips by
+// ~1e-9 per step.  The FP64 form keeps them in FP64; the mixed form keeps each as a
+// float-float pair (BeamWide below) in the same 8-byte slot, so that its push runs without
+// FP64 instructions.  The kicks themselves are computed in BT either way.  A
 // flag byte per particle holds bit 0 = lost, bit 1 = witness and bit 2 = a plasma particle
 // promoted by trapping; orig holds the particle's index in the caller's order (the beam is
 // kept sorted by xi cell for the pipelined step).  With trapping the arrays have room for
@@ -21,7 +23,7 @@ struct BeamDesc {
   double rmax, ximax, dr, dxi, ds, gamma_b;
   double wd, ww;           // macroparticle weights of the drive and witness bunches
   void *x, *y, *ux, *uy;   // BT
-  double *xi, *uz;
+  double *xi, *uz;         // 8-byte slots: FP64, or (BT float) float-float pairs
   uint8_t *lost;           // flags: bit 0 lost, bit 1 witness, bit 2 promoted (trapping)
   int *orig;               // index in the caller's order
   void *w;                 // per-particle weight (BT): charge per 2 pi
@@ -29,6 +31,83 @@ struct BeamDesc {
   const void *er, *ez, *bth;  // fields of the last march (G)
   double *diag;            // 5 accumulators
   int slab;                // slab geometry: a sheet beam at y = u_y = 0, folded onto x >= 0
+  float2 ffi, ffx;         // 1/dxi and ximax as float-float pairs (the mixed form's xi tests)
+};
+
+// A double as a float-float pair (hi, lo): hi = v rounded to FP32, lo = the rest rounded.
+__host__ __device__ inline float2 ff_pair(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
+// The beam's xi and u_z in the form's wide type T.  FP64 form: double.  Mixed form: a
+// float-float pair (hi, lo) with |lo| <= ulp(hi)/2, about 48 significant bits.  A sum adds
+// an FP32 increment by Knuth's two-sum of the high parts and renormalises; the cell of xi
+// comes from the float-float product xi (1/dxi), floored and corrected by the product's low
+// part.  The sort by cell and the push both call cell(), so they agree on every particle.
+template <class BT>
+struct BeamWide;
+
+template <>
+struct BeamWide<double> {
+  using T = double;
+  struct Box {
+    double inv_dxi, ximax;
+  };
+  __device__ static Box box(double dxi, double ximax, float2, float2) { return {1.0 / dxi, ximax}; }
+  __device__ static T ld(const double *p, int64_t j) { return p[j]; }
+  __device__ static T ldcg(const double *p, int64_t j) { return __ldcg(p + j); }
+  __device__ static void st(double *p, int64_t j, T v) { p[j] = v; }
+  __device__ static T from(double v) { return v; }
+  __device__ static double to(T v) { return v; }
+  __device__ static double lead(T v) { return v; }
+  __device__ static void add(T &v, double d) { v += d; }
+  __device__ static bool inside(T xi, const Box &bx) { return xi >= 0.0 && xi < bx.ximax; }
+  __device__ static void cell(T xi, const Box &bx, int nxi, int &k, double &g) { locate(xi, bx.inv_dxi, nxi, k, g); }
+};
+
+template <>
+struct BeamWide<float> {
+  using T = float2;
+  struct Box {
+    float2 inv_dxi, ximax;
+  };
+  __device__ static Box box(double, double, float2 ffi, float2 ffx) { return {ffi, ffx}; }
+  __device__ static T ld(const double *p, int64_t j) { return reinterpret_cast<const float2 *>(p)[j]; }
+  __device__ static T ldcg(const double *p, int64_t j) { return __ldcg(reinterpret_cast<const float2 *>(p) + j); }
+  __device__ static void st(double *p, int64_t j, T v) { reinterpret_cast<float2 *>(p)[j] = v; }
+  __device__ static T from(double v) { return ff_pair(v); }
+  __device__ static double to(T v) { return (double)v.x + (double)v.y; }
+  __device__ static float lead(T v) { return v.x; }
+  __device__ static void add(T &v, float d) {
+    const float s = v.x + d, bv = s - v.x;
+    const float e = ((v.x - (s - bv)) + (d - bv)) + v.y;  // the rounding error of s, plus lo
+    const float h = s + e;
+    v = make_float2(h, e - (h - s));
+  }
+  // 0 <= xi < ximax, the pairs compared high part first
+  __device__ static bool inside(T xi, const Box &bx) {
+    const bool ge0 = xi.x > 0.0f || (xi.x == 0.0f && xi.y >= 0.0f);
+    const bool lt = xi.x < bx.ximax.x || (xi.x == bx.ximax.x && xi.y < bx.ximax.y);
+    return ge0 && lt;
+  }
+  __device__ static void cell(T xi, const Box &bx, int nxi, int &k, float &g) {
+    const float p = xi.x * bx.inv_dxi.x;
+    const float e = fmaf(xi.x, bx.inv_dxi.y, fmaf(xi.y, bx.inv_dxi.x, fmaf(xi.x, bx.inv_dxi.x, -p)));
+    float kf = floorf(p);
+    float f = (p - kf) + e;  // p - kf is exact
+    if (f < 0.0f) {
+      kf -= 1.0f;
+      f += 1.0f;
+    } else if (f >= 1.0f) {
+      kf += 1.0f;
+      f -= 1.0f;
+    }
+    int i = (int)kf;
+    i = i < 0 ? 0 : (i > nxi - 1 ? nxi - 1 : i);
+    k = i;
+    g = f + (kf - (float)i);
+  }
 };
 
 struct BunchInit {
@@ -41,8 +120,8 @@ __device__ __forceinline__ void clear_tail(const BeamDesc &b) {
   for (int64_t j = b.n + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap;
        j += (int64_t)gridDim.x * blockDim.x) {
     ((BT *)b.x)[j] = ((BT *)b.y)[j] = ((BT *)b.ux)[j] = ((BT *)b.uy)[j] = (BT)0;
-    b.xi[j] = 0.0;
-    b.uz[j] = 0.0;
+    BeamWide<BT>::st(b.xi, j, BeamWide<BT>::from(0.0));
+    BeamWide<BT>::st(b.uz, j, BeamWide<BT>::from(0.0));
     b.lost[j] = 1;
     b.orig[j] = (int)j;
     ((BT *)b.w)[j] = (BT)0;
@@ -62,8 +141,8 @@ __global__ void beam_init_kernel(BeamDesc b, BunchInit q, const double *__restri
     ((BT *)b.y)[j] = (BT)y;
     ((BT *)b.ux)[j] = (BT)(su * nm[2 * b.n + j]);
     ((BT *)b.uy)[j] = (BT)(b.slab ? 0.0 : su * nm[3 * b.n + j]);
-    b.xi[j] = xi;
-    b.uz[j] = q.gamma_b;
+    BeamWide<BT>::st(b.xi, j, BeamWide<BT>::from(xi));
+    BeamWide<BT>::st(b.uz, j, BeamWide<BT>::from(q.gamma_b));
     const double r = sqrt(x * x + y * y);
     b.lost[j] = (uint8_t)((xi >= 0.0 && xi < b.ximax && r < b.rmax) ? 0 : 1) | (uint8_t)(drive ? 0 : 2);
     b.orig[j] = (int)j;
@@ -85,8 +164,8 @@ __global__ void beam_set_kernel(BeamDesc b, const double *__restrict__ xyz, cons
     ((BT *)b.y)[j] = (BT)y;
     ((BT *)b.ux)[j] = (BT)xyz[3 * b.n + j];
     ((BT *)b.uy)[j] = (BT)(b.slab ? 0.0 : xyz[4 * b.n + j]);
-    b.xi[j] = xi;
-    b.uz[j] = xyz[5 * b.n + j];
+    BeamWide<BT>::st(b.xi, j, BeamWide<BT>::from(xi));
+    BeamWide<BT>::st(b.uz, j, BeamWide<BT>::from(xyz[5 * b.n + j]));
     const double r = sqrt(x * x + y * y);
     b.lost[j] = (uint8_t)((xi >= 0.0 && xi < b.ximax && r < b.rmax) ? 0 : 1) | (uint8_t)(witness ? 2 : 0);
     b.orig[j] = (int)j;
@@ -101,19 +180,18 @@ template <class BT, class G>
 __device__ __forceinline__ void deposit_range(const BeamDesc &b, int64_t j0, int64_t stride) {
   G *nb = (G *)b.nb;
   const int n1 = b.nr + 1;
+  using W = BeamWide<BT>;
   const BT inv_dr = (BT)(1.0 / b.dr);
-  const double inv_dxi = 1.0 / b.dxi;
+  const typename W::Box bx = W::box(b.dxi, b.ximax, b.ffi, b.ffx);
   for (int64_t j = j0; j < b.n_cap; j += stride) {
     const uint8_t fl = b.lost[j];
     if (fl & 1) continue;
     const BT x = ((const BT *)b.x)[j], y = ((const BT *)b.y)[j];
     const BT r = sqrt(x * x + y * y);
     int c, k;
-    BT f;
+    BT f, gg;
     locate(r, inv_dr, b.nr, c, f);
-    double g;
-    locate(b.xi[j], inv_dxi, b.nxi, k, g);
-    const BT gg = (BT)g;
+    W::cell(W::ld(b.xi, j), bx, b.nxi, k, gg);
     const BT w = ((const BT *)b.w)[j];
     G *row = nb + (size_t)k * n1 + c;
     atomicAdd(row, (G)(w * ((BT)1 - f) * ((BT)1 - gg)));
@@ -160,14 +238,16 @@ __global__ void nb_analytic_kernel(G *nb, int nr, int nxi, double dr, double dxi
 // One Boris step (Eqs. 8-11 are the Lorentz force of E = (E_r rhat, E_z), B = B_theta
 // thetahat on a charge -1) with the fields (Er, Ez, Bt) gathered at the particle: momentum at
 // half steps; x_perp += dt u_perp/gamma; xi += dt (1 + u_perp^2)/(gamma (gamma + u_z)).  The
-// u_z kick 2 h E_z + (p x s)_z is formed in BT and added to the FP64 u_z.
+// u_z kick 2 h E_z + (p x s)_z and the xi increment are formed in BT and added to the wide
+// u_z and xi.
 template <class BT>
-__device__ __forceinline__ void boris_step(BT &x, BT &y, BT &ux, BT &uy, double &xi, double &uzd, BT r, BT Er,
-                                           BT Ez, BT Bt, BT dt) {
+__device__ __forceinline__ void boris_step(BT &x, BT &y, BT &ux, BT &uy, typename BeamWide<BT>::T &xi,
+                                           typename BeamWide<BT>::T &uzd, BT r, BT Er, BT Ez, BT Bt, BT dt) {
+  using W = BeamWide<BT>;
   const BT h = (BT)-0.5 * dt;  // q dt / 2 with q = -1
   const BT cs = r > (BT)0 ? x / r : (BT)0, sn = r > (BT)0 ? y / r : (BT)0;
   const BT Ex = Er * cs, Ey = Er * sn, Bx = -Bt * sn, By = Bt * cs;
-  const BT uz = (BT)uzd;
+  const BT uz = (BT)W::lead(uzd);
   const BT mx = ux + h * Ex, my = uy + h * Ey, mz = uz + h * Ez;
   const BT gm = sqrt((BT)1 + mx * mx + my * my + mz * mz);
   const BT tx = h * Bx / gm, ty = h * By / gm;
@@ -176,13 +256,13 @@ __device__ __forceinline__ void boris_step(BT &x, BT &y, BT &ux, BT &uy, double 
   const BT sx = s * tx, sy = s * ty;
   ux = mx - pz * sy + h * Ex;
   uy = my + pz * sx + h * Ey;
-  uzd += (double)((BT)2 * h * Ez + (px * sy - py * sx));
-  const BT uzn = (BT)uzd;
+  W::add(uzd, (BT)2 * h * Ez + (px * sy - py * sx));
+  const BT uzn = (BT)W::lead(uzd);
   const BT up2 = ux * ux + uy * uy;
   const BT gam = sqrt((BT)1 + up2 + uzn * uzn);
   x += dt * ux / gam;
   y += dt * uy / gam;
-  xi += (double)(dt * ((BT)1 + up2) / (gam * (gam + uzn)));
+  W::add(xi, dt * ((BT)1 + up2) / (gam * (gam + uzn)));
 }
 
 // One beam step through the grid fields of the last march, bilinear gather in (r, xi):
@@ -192,19 +272,18 @@ __device__ __forceinline__ void push_range(const BeamDesc &b, int64_t j0, int64_
   const G *er = (const G *)b.er, *ez = (const G *)b.ez, *bt = (const G *)b.bth;
   BT *X = (BT *)b.x, *Y = (BT *)b.y, *UX = (BT *)b.ux, *UY = (BT *)b.uy;
   const int n1 = b.nr + 1;
+  using W = BeamWide<BT>;
   const BT inv_dr = (BT)(1.0 / b.dr), dt = (BT)b.ds, Rw = (BT)b.rmax;
-  const double inv_dxi = 1.0 / b.dxi;
+  const typename W::Box bx = W::box(b.dxi, b.ximax, b.ffi, b.ffx);
   for (int64_t j = j0; j < b.n_cap; j += stride) {
     if (b.lost[j] & 1) continue;
     BT x = X[j], y = Y[j], ux = UX[j], uy = UY[j];
-    double xi = b.xi[j], uzd = b.uz[j];
+    typename W::T xi = W::ld(b.xi, j), uzd = W::ld(b.uz, j);
     const BT r = sqrt(x * x + y * y);
     int c, k;
-    BT f;
-    double gd;
+    BT f, g;
     locate(r, inv_dr, b.nr, c, f);
-    locate(xi, inv_dxi, b.nxi, k, gd);
-    const BT g = (BT)gd;
+    W::cell(xi, bx, b.nxi, k, g);
     const size_t i00 = (size_t)k * n1 + c;
     const BT w00 = ((BT)1 - f) * ((BT)1 - g), w01 = f * ((BT)1 - g), w10 = ((BT)1 - f) * g, w11 = f * g;
     const BT Er = w00 * (BT)er[i00] + w01 * (BT)er[i00 + 1] + w10 * (BT)er[i00 + n1] + w11 * (BT)er[i00 + n1 + 1];
@@ -215,10 +294,10 @@ __device__ __forceinline__ void push_range(const BeamDesc &b, int64_t j0, int64_
     Y[j] = y;
     UX[j] = ux;
     UY[j] = uy;
-    b.xi[j] = xi;
-    b.uz[j] = uzd;
+    W::st(b.xi, j, xi);
+    W::st(b.uz, j, uzd);
     const BT rn = sqrt(x * x + y * y);
-    if (!(xi >= 0.0 && xi < b.ximax && rn < Rw)) b.lost[j] |= 1;
+    if (!(W::inside(xi, bx) && rn < Rw)) b.lost[j] |= 1;
   }
 }
 template <class BT, class G>
@@ -261,7 +340,7 @@ __global__ void beam_diag_kernel(BeamDesc b) {
   double nw = 0, sw = 0, sw2 = 0, nd = 0, sd = 0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap; j += (int64_t)gridDim.x * blockDim.x) {
     if (b.lost[j] & 5) continue;  // lost, or a promoted plasma particle (neither bunch)
-    const double ux = UX[j], uy = UY[j], uz = b.uz[j];
+    const double ux = UX[j], uy = UY[j], uz = BeamWide<BT>::to(BeamWide<BT>::ld(b.uz, j));
     const double g = sqrt(1.0 + ux * ux + uy * uy + uz * uz) - b.gamma_b;
     if (b.lost[j] & 2) {
       nw += 1;
@@ -310,12 +389,13 @@ static __global__ void plasma_init_kernel(int nr, int ppc, double dr, double u_t
 }
 
 // Counting sort of the beam by xi cell (lost particles go to the extra bin nxi).
-// The cell is found exactly as the push finds it (locate with 1/dxi).
-__device__ __forceinline__ int beam_bin(const BeamDesc &b, int64_t j) {
+// The cell is found exactly as the push finds it (BeamWide<BT>::cell).
+template <class BT>
+__device__ __forceinline__ int beam_bin(const BeamDesc &b, const typename BeamWide<BT>::Box &bx, int64_t j) {
   if (b.lost[j] & 1) return b.nxi;
   int k;
-  double g;
-  locate(b.xi[j], 1.0 / b.dxi, b.nxi, k, g);
+  BT g;
+  BeamWide<BT>::cell(BeamWide<BT>::ld(b.xi, j), bx, b.nxi, k, g);
   return k;
 }
 // Slip rates dxi/dt = (1 + u_perp^2) / (gamma (gamma + u_z)) of the live beam: the largest, as
@@ -330,7 +410,8 @@ __global__ void beam_slip_kernel(BeamDesc b, double span, unsigned long long *ou
   double m = 0.0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap; j += (int64_t)gridDim.x * blockDim.x) {
     if (b.lost[j] & 1) continue;
-    const double ux = ((const BT *)b.ux)[j], uy = ((const BT *)b.uy)[j], uz = b.uz[j];
+    const double ux = ((const BT *)b.ux)[j], uy = ((const BT *)b.uy)[j];
+    const double uz = BeamWide<BT>::to(BeamWide<BT>::ld(b.uz, j));
     const double up2 = ux * ux + uy * uy, g = sqrt(1.0 + up2 + uz * uz);
     const double rate = (1.0 + up2) / (g * (g + uz));
     m = fmax(m, rate);
@@ -344,9 +425,11 @@ __global__ void beam_slip_kernel(BeamDesc b, double span, unsigned long long *ou
   for (int q = threadIdx.x; q < 64; q += blockDim.x)
     if (sh[q]) atomicAdd(&hist[q], sh[q]);
 }
-static __global__ void bin_count_kernel(BeamDesc b, int *count) {
+template <class BT>
+__global__ void bin_count_kernel(BeamDesc b, int *count) {
+  const typename BeamWide<BT>::Box bx = BeamWide<BT>::box(b.dxi, b.ximax, b.ffi, b.ffx);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap; j += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&count[beam_bin(b, j)], 1);
+    atomicAdd(&count[beam_bin<BT>(b, bx, j)], 1);
 }
 // exclusive scan of nbins counts into start[0..nbins] (one block of 1024 threads)
 static __global__ void bin_scan_kernel(const int *count, int *start, int *cursor, int nbins) {
@@ -372,14 +455,15 @@ static __global__ void bin_scan_kernel(const int *count, int *start, int *cursor
 }
 template <class BT>
 __global__ void bin_scatter_kernel(BeamDesc b, BeamDesc dst, int *cursor) {
+  const typename BeamWide<BT>::Box bx = BeamWide<BT>::box(b.dxi, b.ximax, b.ffi, b.ffx);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap; j += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t q = atomicAdd(&cursor[beam_bin(b, j)], 1);
+    const int64_t q = atomicAdd(&cursor[beam_bin<BT>(b, bx, j)], 1);
     ((BT *)dst.x)[q] = ((const BT *)b.x)[j];
     ((BT *)dst.y)[q] = ((const BT *)b.y)[j];
     ((BT *)dst.ux)[q] = ((const BT *)b.ux)[j];
     ((BT *)dst.uy)[q] = ((const BT *)b.uy)[j];
-    dst.xi[q] = b.xi[j];
-    dst.uz[q] = b.uz[j];
+    BeamWide<BT>::st(dst.xi, q, BeamWide<BT>::ld(b.xi, j));
+    BeamWide<BT>::st(dst.uz, q, BeamWide<BT>::ld(b.uz, j));
     dst.lost[q] = b.lost[j];
     dst.orig[q] = b.orig[j];
     ((BT *)dst.w)[q] = ((const BT *)b.w)[j];
@@ -394,10 +478,10 @@ __global__ void beam_unpermute_kernel(BeamDesc b, double *xyz, uint8_t *lost) {
     if (xyz) {
       xyz[0 * b.n + o] = (double)((const BT *)b.x)[j];
       xyz[1 * b.n + o] = (double)((const BT *)b.y)[j];
-      xyz[2 * b.n + o] = b.xi[j];
+      xyz[2 * b.n + o] = BeamWide<BT>::to(BeamWide<BT>::ld(b.xi, j));
       xyz[3 * b.n + o] = (double)((const BT *)b.ux)[j];
       xyz[4 * b.n + o] = (double)((const BT *)b.uy)[j];
-      xyz[5 * b.n + o] = b.uz[j];
+      xyz[5 * b.n + o] = BeamWide<BT>::to(BeamWide<BT>::ld(b.uz, j));
     }
     if (lost) lost[o] = b.lost[j] & 1;
   }
@@ -431,8 +515,8 @@ __global__ void trap_append_kernel(BeamDesc b, const double *__restrict__ list, 
     ((BT *)b.y)[j] = (BT)0;
     ((BT *)b.ux)[j] = (BT)ur;
     ((BT *)b.uy)[j] = (BT)ut;
-    b.uz[j] = (1.0 + up2 - G * G) / (2.0 * G);
-    b.xi[j] = xi;
+    BeamWide<BT>::st(b.uz, j, BeamWide<BT>::from((1.0 + up2 - G * G) / (2.0 * G)));
+    BeamWide<BT>::st(b.xi, j, BeamWide<BT>::from(xi));
     b.lost[j] = (uint8_t)4 | (uint8_t)((xi >= 0.0 && xi < b.ximax && r < b.rmax) ? 0 : 1);
     b.orig[j] = (int)j;
     ((BT *)b.w)[j] = (BT)(e[6] * b.ds);
@@ -454,10 +538,10 @@ __global__ void trapped_out_kernel(BeamDesc b, int64_t used, int64_t cap_out, do
     if (xyz) {
       xyz[0 * cap_out + q] = (double)((const BT *)b.x)[j];
       xyz[1 * cap_out + q] = (double)((const BT *)b.y)[j];
-      xyz[2 * cap_out + q] = b.xi[j];
+      xyz[2 * cap_out + q] = BeamWide<BT>::to(BeamWide<BT>::ld(b.xi, j));
       xyz[3 * cap_out + q] = (double)((const BT *)b.ux)[j];
       xyz[4 * cap_out + q] = (double)((const BT *)b.uy)[j];
-      xyz[5 * cap_out + q] = b.uz[j];
+      xyz[5 * cap_out + q] = BeamWide<BT>::to(BeamWide<BT>::ld(b.uz, j));
     }
     if (w) w[q] = (double)((const BT *)b.w)[j];
     if (lost) lost[q] = b.lost[j] & 1;

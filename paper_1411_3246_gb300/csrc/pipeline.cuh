@@ -32,11 +32,12 @@ struct PipeArgs {
   int write_last;         // write the last step's fields to the output grids
   // beam (sorted by xi cell; cell b holds particles bin_start[b] .. bin_start[b+1]-1)
   void *x, *y, *ux, *uy;
-  double *xi, *uz;
+  double *xi, *uz;        // FP64, or (BT float) float-float pairs
   uint8_t *flags;
   const int *bin_start;
   void *w;               // per-particle weights (BT)
   double ds;
+  float2 ffi, ffx;        // 1/dxi and ximax as float-float pairs
   long long spin_limit;   // polls before a wait gives up
   void *ring_bufs;        // per-CTA ring slot storage (FP64 and wide forms)
   size_t ring_stride;
@@ -65,6 +66,8 @@ struct PipeHooks {
   using R = typename Pol::R;
   using G = typename Pol::G;
   using BT = R;
+  using W = BeamWide<BT>;
+  using Box = typename W::Box;
   static constexpr bool kTraj = false;
   static constexpr bool kTrap = false;
   const PipeArgs &a;
@@ -132,37 +135,35 @@ struct PipeHooks {
   // particles per thread ahead of their stores spilled registers of the march and was slower.)
   struct Part {
     BT x, y, ux, uy, w;
-    double xi, uz;
+    typename W::T xi, uz;
     int tgt;
     uint8_t fl;
   };
   __device__ __forceinline__ void load_part(int j, Part &p) const {
     p.fl = __ldcg(a.flags + j);
-    p.xi = __ldcg(a.xi + j);
+    p.xi = W::ldcg(a.xi, j);
     p.tgt = __ldcg(a.target + j);
     p.x = __ldcg((const BT *)a.x + j);
     p.y = __ldcg((const BT *)a.y + j);
     p.ux = __ldcg((const BT *)a.ux + j);
     p.uy = __ldcg((const BT *)a.uy + j);
-    p.uz = __ldcg(a.uz + j);
+    p.uz = W::ldcg(a.uz, j);
     p.w = __ldcg((const BT *)a.w + j);
   }
 
   // Push particle j (state p), found in cell kk (kk == b or b + 1, fields of slices b .. b+2 in
   // the window), and deposit it into the grid of step t+1.
-  __device__ __forceinline__ void push_one(int j, const Part &p, int kk, double gd) {
+  __device__ __forceinline__ void push_one(int j, const Part &p, int kk, BT g, const Box &bx) {
     BT *X = (BT *)a.x, *Y = (BT *)a.y, *UX = (BT *)a.ux, *UY = (BT *)a.uy;
     G *nbn = (G *)a.grids + (size_t)(t + 1) * a.ng;
     const BT inv_dr = (BT)(1.0 / dr), dt = (BT)a.ds, Rw = (BT)rmax;
-    const double inv_dxi = 1.0 / dxi;
     const uint8_t fl = p.fl;
     BT x = p.x, y = p.y, ux = p.ux, uy = p.uy;
-    double xi = p.xi, uzd = p.uz;
+    typename W::T xi = p.xi, uzd = p.uz;
     const BT r = sqrt(x * x + y * y);
     int c;
     BT f;
     locate(r, inv_dr, nr, c, f);
-    const BT g = (BT)gd;
     const R *w0 = win + (size_t)(kk & 3) * 3 * n1, *w1 = win + (size_t)((kk + 1) & 3) * 3 * n1;
     const BT a00 = ((BT)1 - f) * ((BT)1 - g), a01 = f * ((BT)1 - g), a10 = ((BT)1 - f) * g, a11 = f * g;
     const BT Er = a00 * w0[c] + a01 * w0[c + 1] + a10 * w1[c] + a11 * w1[c + 1];
@@ -173,10 +174,10 @@ struct PipeHooks {
     Y[j] = y;
     UX[j] = ux;
     UY[j] = uy;
-    a.xi[j] = xi;
-    a.uz[j] = uzd;
+    W::st(a.xi, j, xi);
+    W::st(a.uz, j, uzd);
     const BT rn = sqrt(x * x + y * y);
-    if (!(xi >= 0.0 && xi < ximax && rn < Rw)) {
+    if (!(W::inside(xi, bx) && rn < Rw)) {
       a.flags[j] = fl | 1;
       return;
     }
@@ -184,11 +185,9 @@ struct PipeHooks {
     // (dr^2/6 on the axis, dr^2 (nr/2 - 1/6) at the wall) in r, dxi (dxi/2 at the two end
     // slices) in xi
     int c2, k2;
-    BT f2;
-    double g2d;
+    BT f2, g2;
     locate(rn, inv_dr, nr, c2, f2);
-    locate(xi, inv_dxi, nxi, k2, g2d);
-    const BT g2 = (BT)g2d;
+    W::cell(xi, bx, nxi, k2, g2);
     // 1 / V_i = iv(i) / dr^2 (slab: iv(i) / dx, the hat width halved at x = 0 and at the wall)
     constexpr bool slab = Pol::kSlab;
     const BT wq = p.w * (BT)(slab ? 1.0 / (dr * dxi) : 1.0 / (dr * dr * dxi));
@@ -212,7 +211,7 @@ struct PipeHooks {
   // is b + 2 or beyond is deferred to that cell: an earlier step may still have to push it
   // there, and the progress chain makes that happen first.
   __device__ void push_cell(int b) {
-    const double inv_dxi = 1.0 / dxi;
+    const Box bx = W::box(dxi, ximax, a.ffi, a.ffx);
     const int beg = a.bin_start[b], end = a.bin_start[b + 1];
     int *cnt = a.defer_cnt + t;
     int2 *list = a.defer_list + (size_t)t * a.defer_cap;
@@ -221,8 +220,8 @@ struct PipeHooks {
       load_part(j, p);  // every load of the particle at once, before any branch on them
       if (p.fl & 1) continue;
       int kk;
-      double gd;
-      locate(p.xi, inv_dxi, nxi, kk, gd);
+      BT g;
+      W::cell(p.xi, bx, nxi, kk, g);
       const int tgt = max(kk, p.tgt);
       if (tgt >= b + 2) {
         const int q = atomicAdd(cnt, 1);
@@ -238,7 +237,7 @@ struct PipeHooks {
         flag(a.d.status, ST_DRIFT);
         continue;
       }
-      push_one(j, p, kk, gd);
+      push_one(j, p, kk, g, bx);
     }
     __syncthreads();  // every entry counted so far is written
     // this step's deferred particles whose target is b (all listed by earlier cells)
@@ -251,13 +250,13 @@ struct PipeHooks {
       load_part(j, p);
       if (p.fl & 1) continue;
       int kk;
-      double gd;
-      locate(p.xi, inv_dxi, nxi, kk, gd);
+      BT g;
+      W::cell(p.xi, bx, nxi, kk, g);
       if (kk != b && kk != b + 1) {
         flag(a.d.status, ST_DRIFT);
         continue;
       }
-      push_one(j, p, kk, gd);
+      push_one(j, p, kk, g, bx);
     }
     __threadfence();
     __syncthreads();

@@ -227,6 +227,8 @@ BeamDesc beam_desc(const Sim &s, double *diag) {
   b.wd = p.n_drive > 0 ? p.n_d * s2pi * tr * p.sigma_zd / (double)p.n_drive : 0.0;
   b.ww = nw > 0 ? p.n_w * s2pi * tr * p.sigma_zw / (double)nw : 0.0;
   b.slab = p.geometry == WAKE_SLAB;
+  b.ffi = ff_pair(1.0 / b.dxi);
+  b.ffx = ff_pair(b.ximax);
   b.x = s.bx;
   b.y = s.by;
   b.ux = s.bux;
@@ -859,12 +861,15 @@ int sort_beam(wake_sim *h, Sim &s) {
   const int nbins = s.p.nxi + 1;
   CUDA_TRY(cudaMemsetAsync(s.bin_count, 0, sizeof(int) * (nbins + 1), h->stream));
   const int blocks = grid_blocks(s.p.n_beam, 256);
-  bin_count_kernel<<<blocks, 256, 0, h->stream>>>(b, s.bin_count);
-  bin_scan_kernel<<<1, 1024, 0, h->stream>>>(s.bin_count, s.bin_start, s.bin_cursor, nbins);
-  if (h->precision == WAKE_FP64)
+  if (h->precision == WAKE_FP64) {
+    bin_count_kernel<double><<<blocks, 256, 0, h->stream>>>(b, s.bin_count);
+    bin_scan_kernel<<<1, 1024, 0, h->stream>>>(s.bin_count, s.bin_start, s.bin_cursor, nbins);
     bin_scatter_kernel<double><<<blocks, 256, 0, h->stream>>>(b, d, s.bin_cursor);
-  else
+  } else {
+    bin_count_kernel<float><<<blocks, 256, 0, h->stream>>>(b, s.bin_count);
+    bin_scan_kernel<<<1, 1024, 0, h->stream>>>(s.bin_count, s.bin_start, s.bin_cursor, nbins);
     bin_scatter_kernel<float><<<blocks, 256, 0, h->stream>>>(b, d, s.bin_cursor);
+  }
   CUDA_TRY(cudaGetLastError());
   std::swap(s.bx, s.bx2);
   std::swap(s.by, s.by2);
@@ -1058,6 +1063,8 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
       a.bin_start = s.bin_start;
       a.w = b.w;
       a.ds = s.p.ds;
+      a.ffi = b.ffi;
+      a.ffx = b.ffx;
       a.spin_limit = h->spin_limit;
       a.defer_cnt = s.defer_cnt;
       a.defer_list = s.defer_list;
@@ -1289,6 +1296,8 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
     a.bin_start = s.bin_start;
     a.w = bd.w;
     a.ds = s.p.ds;
+    a.ffi = bd.ffi;
+    a.ffx = bd.ffx;
     a.spin_limit = h->spin_limit;  // polls of >= 128 ns: by default a wait gives up after seconds
     a.ring_bufs = s.pring;
     a.ring_stride = rb;

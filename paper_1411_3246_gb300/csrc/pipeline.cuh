@@ -38,6 +38,9 @@ struct PipeArgs {
   void *w;               // per-particle weights (BT)
   double ds;
   float2 ffi, ffx;        // 1/dxi and ximax as float-float pairs
+  // the push's constants in FP32 for the mixed form: 1/dr, ds, rmax, and the deposit's
+  // 1/(dr^2 dxi) (slab: 1/(dr dxi))
+  float f_inv_dr, f_ds, f_rmax, f_wq;
   long long spin_limit;   // polls before a wait gives up
   void *ring_bufs;        // per-CTA ring slot storage (FP64 and wide forms)
   size_t ring_stride;
@@ -156,7 +159,10 @@ struct PipeHooks {
   __device__ __forceinline__ void push_one(int j, const Part &p, int kk, BT g, const Box &bx) {
     BT *X = (BT *)a.x, *Y = (BT *)a.y, *UX = (BT *)a.ux, *UY = (BT *)a.uy;
     G *nbn = (G *)a.grids + (size_t)(t + 1) * a.ng;
-    const BT inv_dr = (BT)(1.0 / dr), dt = (BT)a.ds, Rw = (BT)rmax;
+    constexpr bool slab = Pol::kSlab;
+    constexpr bool f32 = std::is_same_v<BT, float>;  // constants from the arguments: no FP64
+    const BT inv_dr = f32 ? (BT)a.f_inv_dr : (BT)(1.0 / dr), dt = f32 ? (BT)a.f_ds : (BT)a.ds,
+             Rw = f32 ? (BT)a.f_rmax : (BT)rmax;
     const uint8_t fl = p.fl;
     BT x = p.x, y = p.y, ux = p.ux, uy = p.uy;
     typename W::T xi = p.xi, uzd = p.uz;
@@ -189,8 +195,7 @@ struct PipeHooks {
     locate(rn, inv_dr, nr, c2, f2);
     W::cell(xi, bx, nxi, k2, g2);
     // 1 / V_i = iv(i) / dr^2 (slab: iv(i) / dx, the hat width halved at x = 0 and at the wall)
-    constexpr bool slab = Pol::kSlab;
-    const BT wq = p.w * (BT)(slab ? 1.0 / (dr * dxi) : 1.0 / (dr * dr * dxi));
+    const BT wq = p.w * (f32 ? (BT)a.f_wq : (BT)(slab ? 1.0 / (dr * dxi) : 1.0 / (dr * dr * dxi)));
     auto iv = [&](int i) -> BT {
       if (slab) return (i == 0 || i == nr) ? (BT)2 : (BT)1;
       return i == 0 ? (BT)6 : (i == nr ? (BT)1 / ((BT)nr * (BT)0.5 - (BT)(1.0 / 6.0)) : (BT)1 / (BT)i);

@@ -204,6 +204,16 @@ int alloc_beam(wake_sim *h, Sim &s) {
   return WAKE_OK;
 }
 
+// The pipelined push's FP32 constants (the mixed form reads them instead of forming them in
+// FP64 per particle).
+void push_consts(PipeArgs &a, const wake_params &p) {
+  const double dr = p.rmax / p.nr, dxi = p.ximax / p.nxi;
+  a.f_inv_dr = (float)(1.0 / dr);
+  a.f_ds = (float)p.ds;
+  a.f_rmax = (float)p.rmax;
+  a.f_wq = (float)(p.geometry == WAKE_SLAB ? 1.0 / (dr * dxi) : 1.0 / (dr * dr * dxi));
+}
+
 BeamDesc beam_desc(const Sim &s, double *diag) {
   BeamDesc b{};
   const wake_params &p = s.p;
@@ -1065,6 +1075,7 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
       a.ds = s.p.ds;
       a.ffi = b.ffi;
       a.ffx = b.ffx;
+      push_consts(a, s.p);
       a.spin_limit = h->spin_limit;
       a.defer_cnt = s.defer_cnt;
       a.defer_list = s.defer_list;
@@ -1298,6 +1309,7 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
     a.ds = s.p.ds;
     a.ffi = bd.ffi;
     a.ffx = bd.ffx;
+    push_consts(a, s.p);
     a.spin_limit = h->spin_limit;  // polls of >= 128 ns: by default a wait gives up after seconds
     a.ring_bufs = s.pring;
     a.ring_stride = rb;

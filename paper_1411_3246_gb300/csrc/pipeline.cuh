@@ -5,14 +5,16 @@
 // a particle stays in its cell or moves to the next one.  One persistent cooperative launch
 // therefore runs many steps at once, one CTA per SM, each CTA marching its own step a few
 // slices behind the previous step's CTA:
-//   - step t's CTA keeps the fields of its last four slices in shared memory; once slice k is
-//     solved it pushes the beam particles sorted into cell b = k - 2 (their fields lie in
-//     slices b .. b+2) and deposits them straight into the beam-density grid of step t+1;
+//   - step t's CTA keeps the fields of its last slices in shared memory; once slice k is
+//     solved it pushes the beam particles in cell b = k - 1 (their fields lie in slices b and
+//     b+1) and deposits them straight into the beam-density grid of step t+1;
 //   - it then publishes progress[t] = b + 1 (release); step t+1's CTA waits (acquire, bounded)
 //     for progress[t] >= k + 2 before it reads rows <= k + 1 of its grid.
-// Every step has its own density grid (zeroed before the launch), so no grid is reused within
-// a launch.  A wait that exceeds its bound sets ST_TIMEOUT and the CTA leaves cleanly; a
-// particle found more than one cell from its sorted cell sets ST_DRIFT.
+// Step t+1 thus trails step t by two slices, which sets the pace of a launch whose steps
+// outnumber the SMs.  A particle sorted into cell b that has slipped into a later cell is
+// listed and pushed with that cell.  Every step has its own density grid (zeroed before the
+// launch), so no grid is reused within a launch.  A wait that exceeds its bound sets
+// ST_TIMEOUT and the CTA leaves cleanly; a particle found behind its sorted cell sets ST_DRIFT.
 #pragma once
 
 #include "beam.cuh"
@@ -46,9 +48,12 @@ struct PipeArgs {
   size_t ring_stride;
   void *win_bufs;         // per-CTA field windows in global memory (wide form)
   size_t win_stride;
-  // particles that slipped two or more cells past their sorted cell within the launch: step t
-  // lists them (index, target cell) in defer_list[t * defer_cap ...] and pushes them at their
-  // target; target[j] is the latest target any step gave particle j (-1: none)
+  // particles found past their sorted cell within the launch: step t lists them (index,
+  // target cell) and pushes them with their target.  Two lists of defer_cap entries per step:
+  // the next cell's (entries made while cell b is pushed, all for cell b + 1, so cell b + 1
+  // reads only those) at defer_list[2t * defer_cap ...] counted in defer_cnt[2t], and the
+  // rest at defer_list[(2t + 1) * defer_cap ...] counted in defer_cnt[2t + 1], read in full by
+  // every cell.  target[j] is the latest target any step gave particle j (-1: none).
   int *defer_cnt;
   int2 *defer_list;
   int defer_cap;
@@ -127,11 +132,9 @@ struct PipeHooks {
       }
     }
     __syncthreads();
-    if (k >= 2) push_cell(k - 2);
+    if (k >= 1) push_cell(k - 1);
   }
-  __device__ __forceinline__ void finish(MarchSmem<Pol> &) {
-    if (ctl[0] == 0 && nxi >= 1) push_cell(nxi - 1);
-  }
+  __device__ __forceinline__ void finish(MarchSmem<Pol> &) {}  // slice nxi pushed cell nxi - 1
 
   // A particle's state as the push reads it, loaded in one go: the flag, xi and target
   // checks then wait for one round trip to L2 instead of a chain of them.  (Loading several
@@ -154,8 +157,8 @@ struct PipeHooks {
     p.w = __ldcg((const BT *)a.w + j);
   }
 
-  // Push particle j (state p), found in cell kk (kk == b or b + 1, fields of slices b .. b+2 in
-  // the window), and deposit it into the grid of step t+1.
+  // Push particle j (state p), found in cell kk (fields of slices kk, kk+1 in the window), and
+  // deposit it into the grid of step t+1.
   __device__ __forceinline__ void push_one(int j, const Part &p, int kk, BT g, const Box &bx) {
     BT *X = (BT *)a.x, *Y = (BT *)a.y, *UX = (BT *)a.ux, *UY = (BT *)a.uy;
     G *nbn = (G *)a.grids + (size_t)(t + 1) * a.ng;
@@ -210,16 +213,45 @@ struct PipeHooks {
     atomicAdd(row + n1 + 1, (G)(s11 * f2 * g2));
   }
 
-  // Push the beam particles sorted into cell b (fields of slices b .. b+2 are in the window)
-  // and those this step deferred to cell b, deposit them into the grid of step t+1; then
+  // List particle j (state p), met while cell b is pushed, for the push of cell tgt > b.
+  __device__ __forceinline__ void defer(int b, int j, const Part &p, int tgt) {
+    const int l = 2 * t + (tgt == b + 1 ? 0 : 1);
+    const int q = atomicAdd(a.defer_cnt + l, 1);
+    if (q < a.defer_cap) {
+      a.defer_list[(size_t)l * a.defer_cap + q] = make_int2(j, tgt);
+      if (tgt > p.tgt) a.target[j] = tgt;
+    } else {
+      flag(a.d.status, ST_DRIFT);
+    }
+  }
+
+  // A listed particle j for cell b: pushed, listed again if it has slipped on.
+  __device__ __forceinline__ void push_listed(int b, int j, const Box &bx) {
+    Part p;
+    load_part(j, p);
+    if (p.fl & 1) return;
+    int kk;
+    BT g;
+    W::cell(p.xi, bx, nxi, kk, g);
+    if (kk > b) {
+      defer(b, j, p, kk);
+      return;
+    }
+    if (kk != b) {
+      flag(a.d.status, ST_DRIFT);
+      return;
+    }
+    push_one(j, p, kk, g, bx);
+  }
+
+  // Push the beam particles sorted into cell b (fields of slices b, b+1 are in the window)
+  // and those this step listed for cell b, deposit them into the grid of step t+1; then
   // publish progress[t] = b + 1.  A particle whose cell (or an earlier step's target for it)
-  // is b + 2 or beyond is deferred to that cell: an earlier step may still have to push it
-  // there, and the progress chain makes that happen first.
+  // is past b is listed for that cell: its fields are not all solved yet, or an earlier step
+  // may still have to push it there, and the progress chain makes that happen first.
   __device__ void push_cell(int b) {
     const Box bx = W::box(dxi, ximax, a.ffi, a.ffx);
     const int beg = a.bin_start[b], end = a.bin_start[b + 1];
-    int *cnt = a.defer_cnt + t;
-    int2 *list = a.defer_list + (size_t)t * a.defer_cap;
     for (int j = beg + threadIdx.x; j < end; j += NT) {
       Part p;
       load_part(j, p);  // every load of the particle at once, before any branch on them
@@ -228,44 +260,34 @@ struct PipeHooks {
       BT g;
       W::cell(p.xi, bx, nxi, kk, g);
       const int tgt = max(kk, p.tgt);
-      if (tgt >= b + 2) {
-        const int q = atomicAdd(cnt, 1);
-        if (q < a.defer_cap) {
-          list[q] = make_int2(j, tgt);
-          if (tgt > p.tgt) a.target[j] = tgt;
-        } else {
-          flag(a.d.status, ST_DRIFT);
-        }
+      if (tgt > b) {
+        defer(b, j, p, tgt);
         continue;
       }
-      if (kk != b && kk != b + 1) {  // behind its sorted cell: cannot happen (xi only grows)
+      if (kk != b) {  // behind its sorted cell: cannot happen (xi only grows)
         flag(a.d.status, ST_DRIFT);
         continue;
       }
       push_one(j, p, kk, g, bx);
     }
     __syncthreads();  // every entry counted so far is written
-    // this step's deferred particles whose target is b (all listed by earlier cells)
-    const int nd = min(__ldcg(cnt), a.defer_cap);
-    for (int q = threadIdx.x; q < nd; q += NT) {
-      const int2 e = __ldcg(list + q);
-      if (e.y != b) continue;
-      const int j = e.x;
-      Part p;
-      load_part(j, p);
-      if (p.fl & 1) continue;
-      int kk;
-      BT g;
-      W::cell(p.xi, bx, nxi, kk, g);
-      if (kk != b && kk != b + 1) {
-        flag(a.d.status, ST_DRIFT);
-        continue;
-      }
-      push_one(j, p, kk, g, bx);
+    // this step's listed particles for cell b: the next-cell entries made while cell b - 1 was
+    // pushed (ctl[2] .. ctl[3]), and the others whose target is b
+    const int2 *near = a.defer_list + (size_t)(2 * t) * a.defer_cap;
+    const int2 *far = a.defer_list + (size_t)(2 * t + 1) * a.defer_cap;
+    for (int q = ctl[2] + threadIdx.x; q < ctl[3]; q += NT) push_listed(b, __ldcg(near + q).x, bx);
+    const int nf = min(__ldcg(a.defer_cnt + 2 * t + 1), a.defer_cap);
+    for (int q = threadIdx.x; q < nf; q += NT) {
+      const int2 e = __ldcg(far + q);
+      if (e.y == b) push_listed(b, e.x, bx);
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) st_release(&a.progress[t], b + 1);
+    if (threadIdx.x == 0) {
+      st_release(&a.progress[t], b + 1);
+      ctl[2] = ctl[3];  // the entries made while cell b was pushed are cell b + 1's
+      ctl[3] = min(__ldcg(a.defer_cnt + 2 * t), a.defer_cap);
+    }
   }
 };
 
@@ -288,6 +310,8 @@ __global__ void __launch_bounds__(NT, 1) step_kernel(PipeArgs a) {
     if (threadIdx.x == 0) {
       ctl[0] = 0;
       ctl[1] = 0;
+      ctl[2] = 0;  // the next-cell list entries of the cell pushed last
+      ctl[3] = 0;
     }
     __syncthreads();
     PipeHooks<Pol, NT> hk{a, t, win, ctl, n1, a.d.nr, a.d.nxi, a.d.dr, a.d.dxi, a.d.rmax, a.d.ximax};
@@ -312,6 +336,8 @@ __global__ void __launch_bounds__(NT, (NT < 512 ? 512 / NT : 1)) step_wide_kerne
     if (threadIdx.x == 0) {
       ctl[0] = 0;
       ctl[1] = 0;
+      ctl[2] = 0;  // the next-cell list entries of the cell pushed last
+      ctl[3] = 0;
     }
     __syncthreads();
     PipeHooks<Pol, NT> hk{a, t, win, ctl, n1, a.d.nr, a.d.nxi, a.d.dr, a.d.dxi, a.d.rmax, a.d.ximax};
@@ -353,6 +379,8 @@ __global__ void __launch_bounds__(NT, (NT < 512 ? 512 / NT : 1)) batch_step_kern
     if (threadIdx.x == 0) {
       ctl[0] = 0;
       ctl[1] = 0;
+      ctl[2] = 0;  // the next-cell list entries of the cell pushed last
+      ctl[3] = 0;
     }
     __syncthreads();
     PipeHooks<Pol, NT> hk{a, it.y, win, ctl, n1, a.d.nr, a.d.nxi, a.d.dr, a.d.dxi, a.d.rmax, a.d.ximax};

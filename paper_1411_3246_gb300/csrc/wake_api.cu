@@ -57,6 +57,7 @@ struct Sim {
   void *pring = nullptr;
   size_t pring_bytes = 0;
   int *defer_cnt = nullptr, *target = nullptr;  // pipelined steps: slipped-particle lists
+  size_t target_n = 0;                           // entries of target
   int2 *defer_list = nullptr;
   size_t defer_bytes = 0;
   int *status = nullptr;
@@ -174,6 +175,18 @@ int dalloc(T **p, size_t bytes) {
   cudaError_t e = cudaMalloc((void **)p, bytes);
   if (e != cudaSuccess) return fail(WAKE_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
   return WAKE_OK;
+}
+
+// The pipelined steps' per-particle targets, one per beam slot (promoted particles included).
+int alloc_target(Sim &s) {
+  const size_t n = (size_t)(s.n_cap > s.p.n_beam ? s.n_cap : s.p.n_beam);
+  if (s.target && s.target_n >= n) return WAKE_OK;
+  if (s.target) cudaFree(s.target);
+  s.target = nullptr;
+  s.target_n = 0;
+  const int rc = dalloc(&s.target, sizeof(int) * n);
+  if (rc == WAKE_OK) s.target_n = n;
+  return rc;
 }
 
 // The beam arrays of simulation s for s.n_cap particles (any earlier ones freed).
@@ -964,16 +977,26 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
     beam_slip_kernel<float><<<grid_blocks(s.p.n_beam, 256), 256, 0, h->stream>>>(b, span, s.slip, (int *)(s.slip + 1));
   }
   CUDA_TRY(cudaGetLastError());
-  std::vector<unsigned long long> rates(h->n);
+  // the largest slip rate and the histogram of steps per cell of each simulation
+  std::vector<unsigned long long> slip((size_t)h->n * 33);
   for (int i = 0; i < h->n; ++i)
-    CUDA_TRY(cudaMemcpyAsync(&rates[i], h->sims[i].slip, sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(&slip[(size_t)i * 33], h->sims[i].slip, sizeof(unsigned long long) + 64 * sizeof(int),
+                             cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(cudaStreamSynchronize(h->stream));
   for (int i = 0; i < h->n; ++i) {
     double rate;
-    std::memcpy(&rate, &rates[i], sizeof(rate));
+    std::memcpy(&rate, &slip[(size_t)i * 33], sizeof(rate));
     const Sim &s = h->sims[i];
     if (4.0 * s.p.ds * rate > 0.5 * (s.p.ximax / s.p.nxi)) return 1;
   }
+  // list entries a simulation's particles make in L steps (each crossing into the next cell
+  // one; a particle that slips a cell in about 2^q steps crosses L / 2^q times)
+  auto crossings = [&](int i, int L) {
+    const int *hc = (const int *)&slip[(size_t)i * 33 + 1];
+    double p = 0.0;
+    for (int q = 0; q < 63; ++q) p += (double)hc[q] * (double)L / (double)(1LL << q);
+    return (int64_t)std::ceil(p);
+  };
   // steps per launch: the per-step density grids of all simulations within half the free memory
   size_t free_b = 0, total_b = 0;
   CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
@@ -1003,7 +1026,7 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
     for (int i = 0; i < h->n; ++i) {
       Sim &s = h->sims[i];
       const size_t gbytes = sizeof(float) * s.ng;
-      const int dcap = (int)std::min<int64_t>(s.p.n_beam, 4096);
+      const int dcap = (int)std::min<int64_t>(s.p.n_beam, std::max<int64_t>(4096, 2 * crossings(i, ch) + 64));
       if (s.pgrid_cap < ch + 1) {
         void *old[] = {s.pgrids, s.progress, s.defer_cnt};
         for (void *q : old)
@@ -1013,18 +1036,18 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
         s.defer_cnt = nullptr;
         s.pgrid_cap = 0;
         if ((rc = dalloc(&s.pgrids, gbytes * (ch + 1))) || (rc = dalloc(&s.progress, sizeof(int) * ch)) ||
-            (rc = dalloc(&s.defer_cnt, sizeof(int) * ch)))
+            (rc = dalloc(&s.defer_cnt, 2 * sizeof(int) * ch)))
           return rc;
         s.pgrid_cap = ch + 1;
       }
-      if (s.defer_bytes < sizeof(int2) * (size_t)dcap * ch) {
+      if (s.defer_bytes < 2 * sizeof(int2) * (size_t)dcap * ch) {  // two lists per step
         if (s.defer_list) cudaFree(s.defer_list);
         s.defer_list = nullptr;
         s.defer_bytes = 0;
-        if ((rc = dalloc(&s.defer_list, sizeof(int2) * (size_t)dcap * ch))) return rc;
-        s.defer_bytes = sizeof(int2) * (size_t)dcap * ch;
+        if ((rc = dalloc(&s.defer_list, 2 * sizeof(int2) * (size_t)dcap * ch))) return rc;
+        s.defer_bytes = 2 * sizeof(int2) * (size_t)dcap * ch;
       }
-      if (!s.target && (rc = dalloc(&s.target, sizeof(int) * s.p.n_beam))) return rc;
+      if ((rc = alloc_target(s))) return rc;
       if ((rc = sort_beam(h, s))) return rc;
       BeamDesc b = beam_desc(s, nullptr);
       b.nb = s.pgrids;
@@ -1034,8 +1057,8 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
                                                                                        b.dr, b.dxi, b.slab);
       CUDA_TRY(cudaGetLastError());
       CUDA_TRY(cudaMemsetAsync(s.progress, 0, sizeof(int) * ch, h->stream));
-      CUDA_TRY(cudaMemsetAsync(s.defer_cnt, 0, sizeof(int) * ch, h->stream));
-      CUDA_TRY(cudaMemsetAsync(s.target, 0xff, sizeof(int) * s.p.n_beam, h->stream));
+      CUDA_TRY(cudaMemsetAsync(s.defer_cnt, 0, 2 * sizeof(int) * ch, h->stream));
+      CUDA_TRY(cudaMemsetAsync(s.target, 0xff, sizeof(int) * s.target_n, h->stream));
       PipeArgs &a = bs[i].p;
       a = PipeArgs{};
       SimDesc &d = a.d;
@@ -1206,9 +1229,12 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
     // count
     long long L = std::min<long long>(nsteps - done, chmax), dcap_l = 0;
     for (;;) {
-      long long pred = 0;
-      for (int q = 0; q < 64 && (1LL << q) < L; ++q) pred += hist[q];
-      dcap_l = std::min<long long>(s.p.n_beam, (long long)(list_budget / (sizeof(int2) * (size_t)L)));
+      // a particle that slips a cell in about 2^q steps crosses into the next cell L / 2^q
+      // times in L steps (a fraction: the chance that it does at all), each crossing one entry
+      double predf = 0.0;
+      for (int q = 0; q < 63; ++q) predf += (double)hist[q] * (double)L / (double)(1LL << q);
+      const long long pred = (long long)std::ceil(predf);
+      dcap_l = std::min<long long>(s.p.n_beam, (long long)(list_budget / (2 * sizeof(int2) * (size_t)L)));
       if (2 * pred <= dcap_l || L == 1) break;
       L = L > ctas_max ? (L - 1) / ctas_max * ctas_max : L / 2;
     }
@@ -1229,18 +1255,18 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
       s.pgrid_cap = 0;
       const int cap = std::min(nsteps, chmax);
       if ((rc = dalloc(&s.pgrids, gbytes * (cap + 1))) || (rc = dalloc(&s.progress, sizeof(int) * cap)) ||
-          (rc = dalloc(&s.defer_cnt, sizeof(int) * cap)))
+          (rc = dalloc(&s.defer_cnt, 2 * sizeof(int) * cap)))
         return rc;
       s.pgrid_cap = cap + 1;
     }
-    if (s.defer_bytes < sizeof(int2) * (size_t)dcap * ch) {
+    if (s.defer_bytes < 2 * sizeof(int2) * (size_t)dcap * ch) {  // two lists per step
       if (s.defer_list) cudaFree(s.defer_list);
       s.defer_list = nullptr;
       s.defer_bytes = 0;
-      if ((rc = dalloc(&s.defer_list, sizeof(int2) * (size_t)dcap * ch))) return rc;
-      s.defer_bytes = sizeof(int2) * (size_t)dcap * ch;
+      if ((rc = dalloc(&s.defer_list, 2 * sizeof(int2) * (size_t)dcap * ch))) return rc;
+      s.defer_bytes = 2 * sizeof(int2) * (size_t)dcap * ch;
     }
-    if (!s.target && (rc = dalloc(&s.target, sizeof(int) * s.p.n_beam))) return rc;
+    if ((rc = alloc_target(s))) return rc;
     const int ctas = std::min(ch, ctas_max);
     if (rb + wb > 0 && s.pring_bytes < (rb + wb) * ctas) {
       if (s.pring) cudaFree(s.pring);
@@ -1267,8 +1293,8 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
     }
     CUDA_TRY(cudaMemsetAsync((char *)s.pgrids + gbytes, 0, gbytes * ch, h->stream));
     CUDA_TRY(cudaMemsetAsync(s.progress, 0, sizeof(int) * ch, h->stream));
-    CUDA_TRY(cudaMemsetAsync(s.defer_cnt, 0, sizeof(int) * ch, h->stream));
-    CUDA_TRY(cudaMemsetAsync(s.target, 0xff, sizeof(int) * s.p.n_beam, h->stream));  // -1: no target
+    CUDA_TRY(cudaMemsetAsync(s.defer_cnt, 0, 2 * sizeof(int) * ch, h->stream));
+    CUDA_TRY(cudaMemsetAsync(s.target, 0xff, sizeof(int) * s.target_n, h->stream));  // -1: no target
     PipeArgs a{};
     SimDesc &d = a.d;
     d.nr = s.p.nr;

@@ -191,18 +191,17 @@ int wake_bind_fields(wake_sim *s, int sim, void *psi, void *ez, void *er, void *
  * legacy default stream, or while the caller's stream is capturing, the launches are issued
  * directly).  With one simulation
  * that has a beam, the steps run pipelined: the beam is sorted by xi cell and one
- * cooperative launch marches up to one step per SM, each step a few slices behind the one
+ * cooperative launch marches up to one step per SM, each step two slices behind the one
  * before, pushing each cell of the beam as soon as its fields are solved (same arithmetic as
  * the separate calls; only the order of the deposit sums differs).  A step whose wait for the
  * step before it gives up (after WAKE_SPIN_LIMIT polls of >= 128 ns, the environment variable
  * read by wake_init; default 2^24) leaves cleanly and raises WAKE_ETIMEOUT through wake_status.
- * A particle that slips
- * two or more cells past the cell it was sorted into during a launch is pushed when that
- * cell's fields are solved.  The beam must slip less than a cell per step: a beam whose
- * fastest particle, measured at the start of each launch, slips more than 1/8 of a cell
- * per step takes the separate calls (the check synchronises the stream once per launch), and
- * a particle found to have slipped a cell or more in one step anyway raises WAKE_ESTATE
- * through wake_status.
+ * A particle that slips past the cell it was sorted into during a launch is pushed with the
+ * cell it has reached.  The beam must slip less than a cell per step: a beam whose fastest
+ * particle, measured at the start of each launch, slips more than 1/8 of a cell per step
+ * takes the separate calls (the check synchronises the stream once per launch).  A particle
+ * found behind the cell it was sorted into, or more slipped particles than the launch's
+ * lists hold, raise WAKE_ESTATE through wake_status.
  */
 int wake_step(wake_sim *s, int nsteps);
 

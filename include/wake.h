@@ -38,10 +38,11 @@ extern "C" {
 
 #define WAKE_FP64 0    /* FP64 throughout                                            */
 #define WAKE_MIXED 1   /* FP32 particle arithmetic and fields; charge sums in exact    */
-                       /* fixed point, scans in float-float, FP32 tridiagonal solve    */
+                       /* fixed point, scans in float-float, FP32 tridiagonal solve;   */
+                       /* the beam's xi and u_z held as float-float pairs              */
 #define WAKE_MIXED64 2 /* FP32 particle arithmetic and fields; the sums across rings,  */
                        /* the scans and the tridiagonal solve in FP64 (charge sums in  */
-                       /* exact fixed point)                                           */
+                       /* exact fixed point); beam as in WAKE_MIXED                    */
 
 /*
  * Parameters of one simulation (Sec. II, Eq. 12, Table I notation):

@@ -917,8 +917,8 @@ __device__ __forceinline__ void flush_charge(MarchSmem<Pol> &sm, const ChargeWin
   for (int a = 0; a < 4; ++a) t[a] = acc.node(a);
   seg.sum_n(t);
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
-    if (seg.is_tail && acc.c0 >= 0 && acc.c0 + a <= nr) q_atomic_add(&sm.rho[acc.c0 + a], t[a]);
+  for (int a = 0; a < 4; ++a)  // a node no ring of the segment touched is not added to
+    if (seg.is_tail && acc.c0 >= 0 && acc.c0 + a <= nr && t[a] != (Q)0) q_atomic_add(&sm.rho[acc.c0 + a], t[a]);
 }
 
 // Charge deposit of one ring through a window (direct atomics outside it).
@@ -1146,15 +1146,18 @@ __device__ __forceinline__ void pass_currents(MarchSmem<Pol> &sm, const RingSoA<
 #pragma unroll
   for (int a = 0; a < 3; ++a) tot[20 + a] = (Acc)kw[a];
   seg.sum_n(tot);
+  // The window's last nodes are often untouched (a thread's rings span one or two cells where
+  // the plasma is dense), and the shared-memory adds are the pass's costliest part: zero sums
+  // are not added.
   Acc *arr[5] = {sm.jz, sm.chi, sm.T, sm.P, sm.U};
 #pragma unroll
   for (int q = 0; q < 5; ++q)
 #pragma unroll
     for (int a = 0; a < 4; ++a)
-      if (emit && c + a <= nr) atomicAdd(&arr[q][c + a], (Acc)tot[q * 4 + a]);
+      if (emit && c + a <= nr && tot[q * 4 + a] != (Acc)0) atomicAdd(&arr[q][c + a], (Acc)tot[q * 4 + a]);
 #pragma unroll
   for (int a = 0; a < 3; ++a)
-    if (emit && c + a < nr) atomicAdd(&sm.K[c + a], (Acc)tot[20 + a]);
+    if (emit && c + a < nr && tot[20 + a] != (Acc)0) atomicAdd(&sm.K[c + a], (Acc)tot[20 + a]);
 }
 
 // Re-sort the rings of the CTA by cell (counting sort) so that each thread's rings are

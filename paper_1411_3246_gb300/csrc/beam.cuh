@@ -42,9 +42,10 @@ __host__ __device__ inline float2 ff_pair(double v) {
 
 // The beam's xi and u_z in the form's wide type T.  FP64 form: double.  Mixed form: a
 // float-float pair (hi, lo) with |lo| <= ulp(hi)/2, about 48 significant bits.  A sum adds
-// an FP32 increment by Knuth's two-sum of the high parts and renormalises; the cell of xi
-// comes from the float-float product xi (1/dxi), floored and corrected by the product's low
-// part.  The sort by cell and the push both call cell(), so they agree on every particle.
+// an FP32 increment by Knuth's two-sum of the high parts and renormalises.  The cell of xi is
+// the floor of the float-float product xi (1/dxi), decided by exact comparisons: it does not
+// decrease as xi grows (a particle cannot be found behind a cell it has reached), and the
+// sort by cell and the push both call cell(), so they agree on every particle.
 template <class BT>
 struct BeamWide;
 
@@ -91,18 +92,19 @@ struct BeamWide<float> {
     const bool lt = xi.x < bx.ximax.x || (xi.x == bx.ximax.x && xi.y < bx.ximax.y);
     return ge0 && lt;
   }
+  // The cell is floor(p + e) for the float-float product p + e of xi and 1/dxi: decided by
+  // exact comparisons of p - floor(p) (exact) with -e, not by a rounded sum, so that a
+  // particle is not put back a cell by rounding as xi grows.
   __device__ static void cell(T xi, const Box &bx, int nxi, int &k, float &g) {
     const float p = xi.x * bx.inv_dxi.x;
     const float e = fmaf(xi.x, bx.inv_dxi.y, fmaf(xi.y, bx.inv_dxi.x, fmaf(xi.x, bx.inv_dxi.x, -p)));
     float kf = floorf(p);
-    float f = (p - kf) + e;  // p - kf is exact
-    if (f < 0.0f) {
+    const float r = p - kf;  // exact, in [0, 1)
+    if (r < -e)
       kf -= 1.0f;
-      f += 1.0f;
-    } else if (f >= 1.0f) {
+    else if (r - 1.0f >= -e)  // exact where it can hold (r >= 1/2)
       kf += 1.0f;
-      f -= 1.0f;
-    }
+    const float f = (p - kf) + e;
     int i = (int)kf;
     i = i < 0 ? 0 : (i > nxi - 1 ? nxi - 1 : i);
     k = i;
@@ -430,6 +432,13 @@ __global__ void bin_count_kernel(BeamDesc b, int *count) {
   const typename BeamWide<BT>::Box bx = BeamWide<BT>::box(b.dxi, b.ximax, b.ffi, b.ffx);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < b.n_cap; j += (int64_t)gridDim.x * blockDim.x)
     atomicAdd(&count[beam_bin<BT>(b, bx, j)], 1);
+}
+// The largest of the counts of bins 0 .. n-1, into *out (zeroed before).
+static __global__ void bin_max_kernel(const int *count, int n, int *out) {
+  int m = 0;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) m = max(m, count[q]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_down_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(out, m);
 }
 // exclusive scan of nbins counts into start[0..nbins] (one block of 1024 threads)
 static __global__ void bin_scan_kernel(const int *count, int *start, int *cursor, int nbins) {

@@ -24,6 +24,7 @@
 namespace wake {
 
 constexpr int ST_DRIFT = 8;
+constexpr int ST_LISTFULL = 16;  // more slipped particles than a step's lists hold
 
 struct PipeArgs {
   SimDesc d;              // the simulation (plasma, output grids, status)
@@ -49,14 +50,18 @@ struct PipeArgs {
   void *win_bufs;         // per-CTA field windows in global memory (wide form)
   size_t win_stride;
   // particles found past their sorted cell within the launch: step t lists them (index,
-  // target cell) and pushes them with their target.  Two lists of defer_cap entries per step:
-  // the next cell's (entries made while cell b is pushed, all for cell b + 1, so cell b + 1
-  // reads only those) at defer_list[2t * defer_cap ...] counted in defer_cnt[2t], and the
-  // rest at defer_list[(2t + 1) * defer_cap ...] counted in defer_cnt[2t + 1], read in full by
-  // every cell.  target[j] is the latest target any step gave particle j (-1: none).
+  // target cell) and pushes them with their target.  Two lists per step.  Those found in the
+  // next cell (entries made while cell b is pushed, all for cell b + 1, which reads only
+  // them) go to a ring of near_cap entries at near_list[t * near_cap ...], defer_cnt[2t]
+  // counting every entry made; only two cells' entries are alive at once, so the ring holds
+  // a few cells' worth.  The rest (two or more cells on) go to defer_list[t * defer_cap ...],
+  // counted in defer_cnt[2t + 1] and read in full by every cell.  target[j] is the latest
+  // target any step gave particle j (-1: none).
   int *defer_cnt;
   int2 *defer_list;
   int defer_cap;
+  int2 *near_list;
+  int near_cap;
   int *target;
 };
 
@@ -213,20 +218,32 @@ struct PipeHooks {
     atomicAdd(row + n1 + 1, (G)(s11 * f2 * g2));
   }
 
-  // List particle j (state p), met while cell b is pushed, for the push of cell tgt > b.
+  // List particle j (state p), met while cell b is pushed, for the push of cell tgt > b.  A
+  // next-cell entry may not overwrite the entries of cell b - 1 that cell b is still reading
+  // (from ctl[2] on).
   __device__ __forceinline__ void defer(int b, int j, const Part &p, int tgt) {
-    const int l = 2 * t + (tgt == b + 1 ? 0 : 1);
-    const int q = atomicAdd(a.defer_cnt + l, 1);
-    if (q < a.defer_cap) {
-      a.defer_list[(size_t)l * a.defer_cap + q] = make_int2(j, tgt);
-      if (tgt > p.tgt) a.target[j] = tgt;
+    bool ok;
+    if (tgt == b + 1) {
+      const int q = atomicAdd(a.defer_cnt + 2 * t, 1);
+      ok = q - ctl[2] < a.near_cap;
+      if (ok) a.near_list[(size_t)t * a.near_cap + q % a.near_cap] = make_int2(j, tgt);
     } else {
-      flag(a.d.status, ST_DRIFT);
+      const int q = atomicAdd(a.defer_cnt + 2 * t + 1, 1);
+      ok = q < a.defer_cap;
+      if (ok) a.defer_list[(size_t)t * a.defer_cap + q] = make_int2(j, tgt);
     }
+    if (!ok) {
+      flag(a.d.status, ST_LISTFULL);
+      return;
+    }
+    if (tgt > p.tgt) a.target[j] = tgt;
   }
 
-  // A listed particle j for cell b: pushed, listed again if it has slipped on.
+  // A listed particle j for cell b: pushed, listed again if it has slipped on.  (An index
+  // outside the sorted beam can only come from a ring slot overwritten after an overflow,
+  // which has raised ST_LISTFULL: it is skipped.)
   __device__ __forceinline__ void push_listed(int b, int j, const Box &bx) {
+    if (j < 0 || j >= a.bin_start[nxi + 1]) return;
     Part p;
     load_part(j, p);
     if (p.fl & 1) return;
@@ -273,9 +290,9 @@ struct PipeHooks {
     __syncthreads();  // every entry counted so far is written
     // this step's listed particles for cell b: the next-cell entries made while cell b - 1 was
     // pushed (ctl[2] .. ctl[3]), and the others whose target is b
-    const int2 *near = a.defer_list + (size_t)(2 * t) * a.defer_cap;
-    const int2 *far = a.defer_list + (size_t)(2 * t + 1) * a.defer_cap;
-    for (int q = ctl[2] + threadIdx.x; q < ctl[3]; q += NT) push_listed(b, __ldcg(near + q).x, bx);
+    const int2 *near = a.near_list + (size_t)t * a.near_cap;
+    const int2 *far = a.defer_list + (size_t)t * a.defer_cap;
+    for (int q = ctl[2] + threadIdx.x; q < ctl[3]; q += NT) push_listed(b, __ldcg(near + q % a.near_cap).x, bx);
     const int nf = min(__ldcg(a.defer_cnt + 2 * t + 1), a.defer_cap);
     for (int q = threadIdx.x; q < nf; q += NT) {
       const int2 e = __ldcg(far + q);
@@ -286,7 +303,7 @@ struct PipeHooks {
     if (threadIdx.x == 0) {
       st_release(&a.progress[t], b + 1);
       ctl[2] = ctl[3];  // the entries made while cell b was pushed are cell b + 1's
-      ctl[3] = min(__ldcg(a.defer_cnt + 2 * t), a.defer_cap);
+      ctl[3] = __ldcg(a.defer_cnt + 2 * t);
     }
   }
 };

@@ -60,6 +60,8 @@ struct Sim {
   size_t target_n = 0;                           // entries of target
   int2 *defer_list = nullptr;
   size_t defer_bytes = 0;
+  int2 *near_list = nullptr;  // pipelined steps: the next-cell rings
+  size_t near_bytes = 0;
   int *status = nullptr;
   // trapping (wake_set_trapping): beam slots for promoted particles, the march's promotions
   int64_t n_cap = 0;            // beam slots: n_beam, plus room for promoted particles
@@ -143,7 +145,8 @@ void free_sim(Sim &s) {
   void *ptrs[] = {s.r0, s.ur0, s.lz, s.G0, s.w, s.ring_buf, s.nb, s.psi, s.ez, s.er, s.bth, s.bx, s.by, s.bux, s.buy,
                   s.bxi, s.buz, s.blost, s.status, s.orig, s.bx2, s.by2, s.bux2, s.buy2, s.bxi2, s.buz2, s.blost2,
                   s.orig2, s.bin_count, s.bin_start, s.bin_cursor, s.slip, s.pgrids, s.progress, s.pring,
-                  s.defer_cnt, s.target, s.defer_list, s.bwt, s.bwt2, s.trap_list, s.trap_count, s.trap_used};
+                  s.defer_cnt, s.target, s.defer_list, s.near_list, s.bwt, s.bwt2, s.trap_list, s.trap_count,
+                  s.trap_used};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   s = Sim();
@@ -186,6 +189,23 @@ int alloc_target(Sim &s) {
   s.target_n = 0;
   const int rc = dalloc(&s.target, sizeof(int) * n);
   if (rc == WAKE_OK) s.target_n = n;
+  return rc;
+}
+
+// Entries of a step's next-cell ring: the entries of two consecutive cells are alive at
+// once, each cell's at most the particles sorted into it (and a few listed again), so four
+// times the densest cell suffices.
+int near_ring(const Sim &s, int occ) {
+  return (int)std::min<int64_t>((int64_t)4 * occ + 1024, (int64_t)s.n_cap + 1024);
+}
+int alloc_near(Sim &s, int cap, int ch) {
+  const size_t need = sizeof(int2) * (size_t)cap * ch;
+  if (s.near_bytes >= need) return WAKE_OK;
+  if (s.near_list) cudaFree(s.near_list);
+  s.near_list = nullptr;
+  s.near_bytes = 0;
+  const int rc = dalloc(&s.near_list, need);
+  if (rc == WAKE_OK) s.near_bytes = need;
   return rc;
 }
 
@@ -869,7 +889,7 @@ namespace {
 
 // Sort the beam of simulation s by xi cell (lost particles last) into the second copy and
 // swap the copies; bin_start then gives the range of each cell.
-int sort_beam(wake_sim *h, Sim &s) {
+int sort_beam(wake_sim *h, Sim &s, int *occ) {
   BeamDesc b = beam_desc(s, nullptr);
   BeamDesc d = b;
   d.x = s.bx2;
@@ -894,6 +914,13 @@ int sort_beam(wake_sim *h, Sim &s) {
     bin_scatter_kernel<float><<<blocks, 256, 0, h->stream>>>(b, d, s.bin_cursor);
   }
   CUDA_TRY(cudaGetLastError());
+  if (occ) {  // the densest cell (bins 0 .. nxi - 1) into the unused last count
+    bin_max_kernel<<<std::max(1, std::min(152, (nbins + 255) / 256)), 256, 0, h->stream>>>(s.bin_count, nbins - 1,
+                                                                                      s.bin_count + nbins);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(occ, s.bin_count + nbins, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
   std::swap(s.bx, s.bx2);
   std::swap(s.by, s.by2);
   std::swap(s.bux, s.bux2);
@@ -989,14 +1016,6 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
     const Sim &s = h->sims[i];
     if (4.0 * s.p.ds * rate > 0.5 * (s.p.ximax / s.p.nxi)) return 1;
   }
-  // list entries a simulation's particles make in L steps (each crossing into the next cell
-  // one; a particle that slips a cell in about 2^q steps crosses L / 2^q times)
-  auto crossings = [&](int i, int L) {
-    const int *hc = (const int *)&slip[(size_t)i * 33 + 1];
-    double p = 0.0;
-    for (int q = 0; q < 63; ++q) p += (double)hc[q] * (double)L / (double)(1LL << q);
-    return (int64_t)std::ceil(p);
-  };
   // steps per launch: the per-step density grids of all simulations within half the free memory
   size_t free_b = 0, total_b = 0;
   CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
@@ -1026,7 +1045,7 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
     for (int i = 0; i < h->n; ++i) {
       Sim &s = h->sims[i];
       const size_t gbytes = sizeof(float) * s.ng;
-      const int dcap = (int)std::min<int64_t>(s.p.n_beam, std::max<int64_t>(4096, 2 * crossings(i, ch) + 64));
+      const int dcap = (int)std::min<int64_t>(s.p.n_beam, 4096);
       if (s.pgrid_cap < ch + 1) {
         void *old[] = {s.pgrids, s.progress, s.defer_cnt};
         for (void *q : old)
@@ -1040,15 +1059,18 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
           return rc;
         s.pgrid_cap = ch + 1;
       }
-      if (s.defer_bytes < 2 * sizeof(int2) * (size_t)dcap * ch) {  // two lists per step
+      if (s.defer_bytes < sizeof(int2) * (size_t)dcap * ch) {
         if (s.defer_list) cudaFree(s.defer_list);
         s.defer_list = nullptr;
         s.defer_bytes = 0;
-        if ((rc = dalloc(&s.defer_list, 2 * sizeof(int2) * (size_t)dcap * ch))) return rc;
-        s.defer_bytes = 2 * sizeof(int2) * (size_t)dcap * ch;
+        if ((rc = dalloc(&s.defer_list, sizeof(int2) * (size_t)dcap * ch))) return rc;
+        s.defer_bytes = sizeof(int2) * (size_t)dcap * ch;
       }
       if ((rc = alloc_target(s))) return rc;
-      if ((rc = sort_beam(h, s))) return rc;
+      int occ = 0;
+      if ((rc = sort_beam(h, s, &occ))) return rc;
+      const int ncap = near_ring(s, occ);
+      if ((rc = alloc_near(s, ncap, ch))) return rc;
       BeamDesc b = beam_desc(s, nullptr);
       b.nb = s.pgrids;
       CUDA_TRY(cudaMemsetAsync(s.pgrids, 0, gbytes * (ch + 1), h->stream));
@@ -1103,6 +1125,8 @@ int step_batch_pipelined(wake_sim *h, int nsteps) {
       a.defer_cnt = s.defer_cnt;
       a.defer_list = s.defer_list;
       a.defer_cap = dcap;
+      a.near_list = s.near_list;
+      a.near_cap = ncap;
       a.target = s.target;
     }
     if ((rc = upload_beam_descs(h))) return rc;  // the sort swapped the beam copies
@@ -1229,12 +1253,11 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
     // count
     long long L = std::min<long long>(nsteps - done, chmax), dcap_l = 0;
     for (;;) {
-      // a particle that slips a cell in about 2^q steps crosses into the next cell L / 2^q
-      // times in L steps (a fraction: the chance that it does at all), each crossing one entry
-      double predf = 0.0;
-      for (int q = 0; q < 63; ++q) predf += (double)hist[q] * (double)L / (double)(1LL << q);
-      const long long pred = (long long)std::ceil(predf);
-      dcap_l = std::min<long long>(s.p.n_beam, (long long)(list_budget / (2 * sizeof(int2) * (size_t)L)));
+      // the second list holds the particles two or more cells past their sorted cell: at most
+      // those that slip a cell in fewer than L steps
+      long long pred = 0;
+      for (int q = 0; q < 64 && (1LL << q) < L; ++q) pred += hist[q];
+      dcap_l = std::min<long long>(s.p.n_beam, (long long)(list_budget / (sizeof(int2) * (size_t)L)));
       if (2 * pred <= dcap_l || L == 1) break;
       L = L > ctas_max ? (L - 1) / ctas_max * ctas_max : L / 2;
     }
@@ -1259,12 +1282,12 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
         return rc;
       s.pgrid_cap = cap + 1;
     }
-    if (s.defer_bytes < 2 * sizeof(int2) * (size_t)dcap * ch) {  // two lists per step
+    if (s.defer_bytes < sizeof(int2) * (size_t)dcap * ch) {
       if (s.defer_list) cudaFree(s.defer_list);
       s.defer_list = nullptr;
       s.defer_bytes = 0;
-      if ((rc = dalloc(&s.defer_list, 2 * sizeof(int2) * (size_t)dcap * ch))) return rc;
-      s.defer_bytes = 2 * sizeof(int2) * (size_t)dcap * ch;
+      if ((rc = dalloc(&s.defer_list, sizeof(int2) * (size_t)dcap * ch))) return rc;
+      s.defer_bytes = sizeof(int2) * (size_t)dcap * ch;
     }
     if ((rc = alloc_target(s))) return rc;
     const int ctas = std::min(ch, ctas_max);
@@ -1275,7 +1298,10 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
       if ((rc = dalloc(&s.pring, (rb + wb) * ctas))) return rc;
       s.pring_bytes = (rb + wb) * ctas;
     }
-    if ((rc = sort_beam(h, s))) return rc;
+    int occ = 0;
+    if ((rc = sort_beam(h, s, &occ))) return rc;
+    const int ncap = near_ring(s, occ);
+    if ((rc = alloc_near(s, ncap, ch))) return rc;
     const BeamDesc bd = beam_desc(s, nullptr);
     {  // beam density of the launch's first step
       BeamDesc b = bd;
@@ -1344,6 +1370,8 @@ int step_pipelined(wake_sim *h, int nsteps, int ctas_max, int wide_nt) {
     a.defer_cnt = s.defer_cnt;
     a.defer_list = s.defer_list;
     a.defer_cap = dcap;
+    a.near_list = s.near_list;
+    a.near_cap = ncap;
     a.target = s.target;
     if (h->ev_used == (int)h->ev.size()) {
       std::pair<cudaEvent_t, cudaEvent_t> q{};
@@ -1508,7 +1536,8 @@ int wake_status(wake_sim *h, int sim) {
   if (st & ST_NUMERIC) return fail(WAKE_ENUMERIC, "Gamma <= 0 or a non-finite field in the march");
   if (st & ST_ESCAPE) return fail(WAKE_EESCAPE, "a plasma ring left [0, rmax]");
   if (st & ST_TIMEOUT) return fail(WAKE_ETIMEOUT, "a bounded device wait gave up");
-  if (st & ST_DRIFT) return fail(WAKE_ESTATE, "a beam particle slipped more than one xi cell within a step");
+  if (st & ST_DRIFT) return fail(WAKE_ESTATE, "a beam particle was found behind the xi cell it was sorted into");
+  if (st & ST_LISTFULL) return fail(WAKE_ESTATE, "more beam particles slipped past their xi cells than a pipelined step's lists hold");
   return WAKE_OK;
 }
 
